@@ -1,0 +1,289 @@
+"""Seeded synthetic problem generators shared by the tests and the benchmark.
+
+This module only *builds* problems (data A, b, c and the cone list, plus the
+planted solution where there is one).  It contains none of the solver's
+arithmetic, so both the FP64 oracle and the CUDA path can be fed from it.
+
+Every problem is a dict with
+    A  : scipy.sparse.csr_matrix (m x n), rows ordered [f | l | q... | s...]
+    b, c : float64 arrays
+    f, l : ints;  q, s : lists of cone dimensions (SOC dims; PSD orders)
+plus optional planted ``xstar``, ``ystar``, ``sstar`` and ``meta``.
+
+Recipes (the paper measures on self-generated random families, Sec. 5; the
+shapes below follow those families and the workload sizes of the benchmark):
+  lasso()          l1-regularised least squares in epigraph form (Sec. 5.3)
+  planted()        random sparse cone program with a planted primal-dual pair
+  planted_sdp()    planted SDP blocks plus orthant rows
+  portfolio()      long-only mean-risk portfolio SOCP
+  infeasible() / unbounded()   planted certificates (Sec. 3, theorems of the alternative)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def _csr(rows, cols, vals, m, n):
+    A = sp.csr_matrix((np.asarray(vals, np.float64), (np.asarray(rows), np.asarray(cols))), shape=(m, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def random_pattern(rng, m, n, nnz_target):
+    """Uniform random sparsity pattern with about nnz_target distinct entries,
+    N(0,1) values, returned in CSR (row-major sorted) order."""
+    total = m * n
+    k = int(min(total, nnz_target))
+    if k == 0:
+        return sp.csr_matrix((m, n))
+    if total <= 4 * k:
+        lin = rng.choice(total, size=k, replace=False)
+    else:
+        lin = np.unique(rng.integers(0, total, size=int(k * 1.02) + 16, dtype=np.int64))
+        if lin.size > k:
+            lin = np.sort(rng.choice(lin, size=k, replace=False))
+    lin = np.sort(lin)
+    rows, cols = lin // n, lin % n
+    vals = rng.standard_normal(lin.size)
+    indptr = np.zeros(m + 1, np.int64)
+    np.add.at(indptr, rows + 1, 1)
+    indptr = np.cumsum(indptr)
+    return sp.csr_matrix((vals, cols.astype(np.int32), indptr), shape=(m, n))
+
+
+def lasso(seed=0, p=60, nvar=120, density=0.1, k_nz=12, noise=0.01, mu_frac=0.1, F=None, g=None):
+    """min 1/2 ||F x - g||^2 + mu ||x||_1 as a cone program.
+
+    Variables (x in R^nvar, t in R^nvar, r); c = (0, mu 1, 1).
+    Orthant rows: t - x >= 0, t + x >= 0.  One SOC (t last):
+    (sqrt2 (F x - g), r - 1, r + 1), which encodes 1/2 ||F x - g||^2 <= r.
+    Default: F 60 x 120 at 10% density, N(0, 1/60) values, planted x with 12
+    N(0,1) nonzeros, g = F x + 0.01 N(0,1), mu = 0.1 ||F^T g||_inf.
+    """
+    rng = np.random.default_rng(seed)
+    if F is None:
+        Fd = sp.random(p, nvar, density=density, random_state=rng, format="csr",
+                       data_rvs=lambda k: rng.standard_normal(k) / math.sqrt(p))
+    else:
+        Fd = sp.csr_matrix(F)
+        p, nvar = Fd.shape
+    if g is None:
+        xt = np.zeros(nvar)
+        idx = rng.choice(nvar, size=min(k_nz, nvar), replace=False)
+        xt[idx] = rng.standard_normal(idx.size)
+        g = Fd @ xt + noise * rng.standard_normal(p)
+    else:
+        xt = None
+    mu = mu_frac * np.max(np.abs(Fd.T @ g))
+    n = 2 * nvar + 1
+    I = sp.identity(nvar, format="csr")
+    Z = sp.csr_matrix((nvar, 1))
+    rows_l1 = sp.hstack([I, -I, Z])
+    rows_l2 = sp.hstack([-I, -I, Z])
+    er = sp.csr_matrix(([-1.0], ([0], [2 * nvar])), shape=(1, n))
+    soc_F = sp.hstack([-math.sqrt(2.0) * Fd, sp.csr_matrix((p, nvar)), sp.csr_matrix((p, 1))])
+    A = sp.vstack([rows_l1, rows_l2, soc_F, er, er]).tocsr()
+    A.sort_indices()
+    b = np.concatenate([np.zeros(2 * nvar), -math.sqrt(2.0) * g, [-1.0, 1.0]])
+    c = np.concatenate([np.zeros(nvar), mu * np.ones(nvar), [1.0]])
+    return dict(A=A, b=b, c=c, f=0, l=2 * nvar, q=[p + 2], s=[],
+                meta=dict(F=Fd, g=np.asarray(g), mu=mu, xtrue=xt, nvar=nvar))
+
+
+def _unit(rng, k):
+    v = rng.standard_normal(k)
+    nv = np.linalg.norm(v)
+    return v / nv if nv > 0 else np.eye(k)[0]
+
+
+def _svec(X):
+    d = X.shape[0]
+    out = np.empty(d * (d + 1) // 2)
+    o = 0
+    for j in range(d):
+        col = X[j:, j].copy()
+        col[1:] *= math.sqrt(2.0)
+        out[o:o + d - j] = col
+        o += d - j
+    return out
+
+
+def planted(seed=0, n=200, l=200, soc=(), psd=(), f=0, nnz=None, density=None, psd_rank=None):
+    """Random sparse cone program with a planted strictly complementary
+    primal-dual optimum (x*, y*, s*); b = A x* + s*, c = -A^T y*.
+
+    Orthant rows: with prob 1/2 s ~ U(0.1,1), y = 0, else y ~ U(0.1,1), s = 0.
+    SOC of dim k (t last), u uniform on the unit sphere of R^{k-1}, a, beta
+    ~ U(0.5,1.5), cycling over three cases: s = a(u,1), y = 0;  y = beta(-u,1),
+    s = 0;  s = a(u,1), y = beta(-u,1).  PSD of order d: V from the QR of a
+    Gaussian, S = V diag(lam_1..lam_k, 0..) V^T, Y = V diag(0.., lam_{k+1}..) V^T
+    with lam ~ U(0.5, 2) and k ~ U{d/4..3d/4}.  Zero-cone rows: s = 0, y ~ N(0,1).
+    A has N(0,1) values at uniform random positions.
+    """
+    rng = np.random.default_rng(seed)
+    soc, psd = list(soc), list(psd)
+    m = f + l + sum(soc) + sum(d * (d + 1) // 2 for d in psd)
+    if nnz is None:
+        nnz = int(round((density if density is not None else 0.05) * m * n))
+    A = random_pattern(rng, m, n, nnz)
+    xs = rng.standard_normal(n)
+    s = np.zeros(m)
+    y = np.zeros(m)
+    o = 0
+    y[o:o + f] = rng.standard_normal(f)
+    o += f
+    pick = rng.random(l) < 0.5
+    sv = rng.uniform(0.1, 1.0, l)
+    yv = rng.uniform(0.1, 1.0, l)
+    s[o:o + l] = np.where(pick, sv, 0.0)
+    y[o:o + l] = np.where(pick, 0.0, yv)
+    o += l
+    for i, k in enumerate(soc):
+        if k == 1:
+            if i % 2 == 0:
+                s[o] = rng.uniform(0.5, 1.5)
+            else:
+                y[o] = rng.uniform(0.5, 1.5)
+        else:
+            u = _unit(rng, k - 1)
+            a, be = rng.uniform(0.5, 1.5, 2)
+            case = i % 3
+            if case in (0, 2):
+                s[o:o + k - 1] = a * u
+                s[o + k - 1] = a
+            if case in (1, 2):
+                y[o:o + k - 1] = -be * u
+                y[o + k - 1] = be
+        o += k
+    for d in psd:
+        G = rng.standard_normal((d, d))
+        V, _ = np.linalg.qr(G)
+        lo, hi = (d // 4, (3 * d) // 4) if psd_rank is None else (psd_rank, psd_rank)
+        ks = int(rng.integers(max(lo, 0), hi + 1))
+        lam = rng.uniform(0.5, 2.0, d)
+        ls = np.where(np.arange(d) < ks, lam, 0.0)
+        ly = np.where(np.arange(d) >= ks, lam, 0.0)
+        S = (V * ls) @ V.T
+        Y = (V * ly) @ V.T
+        k = d * (d + 1) // 2
+        s[o:o + k] = _svec(S)
+        y[o:o + k] = _svec(Y)
+        o += k
+    assert o == m
+    b = A @ xs + s
+    c = -(A.T @ y)
+    return dict(A=A, b=b, c=c, f=f, l=l, q=soc, s=psd, xstar=xs, ystar=y, sstar=s)
+
+
+def c2_planted(seed=0, scale=1.0):
+    """Large planted sparse program: n = 100k, m = 200k (100k orthant rows plus
+    2000 SOCs of dim 50), A at 0.05% density (1e7 nonzeros).  ``scale`` shrinks
+    n, the orthant block and the SOC count together, keeping ~50 nnz per row."""
+    n = max(10, int(round(100_000 * scale)))
+    l = max(10, int(round(100_000 * scale)))
+    nq = max(1, int(round(2000 * scale)))
+    m = l + 50 * nq
+    nnz = int(round(50 * m))
+    return planted(seed, n=n, l=l, soc=[50] * nq, nnz=nnz)
+
+
+def c3_planted_sdp(seed=0, nblk=512, d=64, l=50_000, n=20_000, nnz=1_000_000):
+    """Planted SDP: nblk PSD blocks of order d plus l orthant rows, A with
+    about nnz N(0,1) entries at uniform random positions."""
+    return planted(seed, n=n, l=l, psd=[d] * nblk, nnz=nnz)
+
+
+def portfolio(seed=0, k=None, gamma=1.0):
+    """Long-only mean-risk portfolio SOCP with k assets and rank k//10 factors:
+    min -mu^T w + gamma t  s.t.  1^T w = 1,  w >= 0,  (F^T w, D^{1/2} w, t) in SOC.
+    k ~ U{20..400}, F ~ N(0, 1/k), D = diag U[0.01, 0.1], mu ~ N(0.05, 0.02)."""
+    rng = np.random.default_rng(seed)
+    if k is None:
+        k = int(rng.integers(20, 401))
+    r = max(1, k // 10)
+    F = rng.standard_normal((k, r)) / math.sqrt(k)
+    Dg = rng.uniform(0.01, 0.1, k)
+    mu = rng.normal(0.05, 0.02, k)
+    n = k + 1
+    rows, cols, vals = [], [], []
+    # zero cone: 1^T w = 1
+    rows += [0] * k; cols += list(range(k)); vals += [1.0] * k
+    # orthant: s = w
+    rows += list(range(1, k + 1)); cols += list(range(k)); vals += [-1.0] * k
+    o = k + 1
+    # SOC (F^T w, D^{1/2} w, t)
+    for j in range(r):
+        rows += [o + j] * k; cols += list(range(k)); vals += list(-F[:, j])
+    o += r
+    rows += list(range(o, o + k)); cols += list(range(k)); vals += list(-np.sqrt(Dg))
+    o += k
+    rows += [o]; cols += [k]; vals += [-1.0]
+    m = o + 1
+    A = _csr(rows, cols, vals, m, n)
+    b = np.zeros(m); b[0] = 1.0
+    c = np.concatenate([-mu, [gamma]])
+    return dict(A=A, b=b, c=c, f=1, l=k, q=[r + k + 1], s=[], meta=dict(k=k, r=r))
+
+
+def infeasible(seed=0, n=200, l=200, soc=(10,) * 4, nnz=None):
+    """Planted primal-infeasible program: the first two orthant rows are a and
+    -a with b_1 + b_2 = -1, so y = e_1 + e_2 certifies infeasibility."""
+    P = planted(seed, n=n, l=l, soc=soc, nnz=nnz)
+    rng = np.random.default_rng(seed + 7919)
+    A = P["A"].tolil()
+    a = rng.standard_normal(n) * (rng.random(n) < 0.1)
+    A[0, :] = a
+    A[1, :] = -a
+    A = A.tocsr()
+    A.eliminate_zeros()
+    A.sort_indices()
+    b = P["b"].copy()
+    b[0] = 0.3
+    b[1] = -1.3
+    return dict(A=A, b=b, c=P["c"], f=0, l=l, q=list(soc), s=[], ycert=np.eye(A.shape[0])[0] + np.eye(A.shape[0])[1])
+
+
+def unbounded(seed=0, n=200, l=200, soc=(10,) * 4, nnz=None):
+    """Planted dual-infeasible (unbounded) program: column 0 is replaced by
+    one with entries <= 0 in orthant rows only and c_0 = -1, so x = e_0 with
+    s = -A e_0 in K certifies unboundedness (a planted feasible x* keeps the
+    primal feasible)."""
+    P = planted(seed, n=n, l=l, soc=soc, nnz=nnz)
+    rng = np.random.default_rng(seed + 104729)
+    A = P["A"].tolil()
+    m = A.shape[0]
+    col = np.zeros(m)
+    sel = rng.random(l) < 0.2
+    col[:l] = -np.abs(rng.standard_normal(l)) * sel
+    A[:, 0] = col.reshape(-1, 1)
+    A = A.tocsr()
+    A.eliminate_zeros()
+    A.sort_indices()
+    xs = P["xstar"].copy()
+    b = A @ xs + P["sstar"]
+    c = P["c"].copy()
+    c[0] = -1.0
+    return dict(A=A, b=b, c=c, f=0, l=l, q=list(soc), s=[], xcert=np.eye(n)[0])
+
+
+def lasso_family_matrix(seed=0, p=2000, nvar=5000, density=0.01):
+    """Fixed F of the parametric LASSO family: p x nvar at the given density
+    with N(0, 1/p) values."""
+    rng = np.random.default_rng(seed)
+    return sp.random(p, nvar, density=density, random_state=rng, format="csr",
+                     data_rvs=lambda k: rng.standard_normal(k) / math.sqrt(p))
+
+
+def lasso_family_rhs(F, seed, frac_nz=0.05, noise=0.01):
+    """One instance parameter g = F x + 0.01 N(0,1) with x 5% sparse N(0,1)."""
+    rng = np.random.default_rng(seed)
+    nvar = F.shape[1]
+    x = np.zeros(nvar)
+    k = max(1, int(round(frac_nz * nvar)))
+    idx = rng.choice(nvar, size=k, replace=False)
+    x[idx] = rng.standard_normal(k)
+    return F @ x + noise * rng.standard_normal(F.shape[0])
