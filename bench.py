@@ -1,0 +1,341 @@
+"""Benchmark: SuperSCS time-to-tolerance on GB300 through the C ABI.
+
+Default workload (the large single-instance configuration): a planted sparse
+cone program with n = 100k, m = 200k (100k orthant rows + 2000 SOCs of dim
+50), A at 0.05% density (1e7 N(0,1) nonzeros), AA memory 10, eps = 1e-6.
+One step = one whole solve (all of Algorithm 1) of that instance in the
+chosen form (FP32 bulk + FP64 refinement, ``--precision mixed``), with the
+data resident in HBM.  A plain-FP64 solve of the same instance is timed once
+for comparison.
+
+JSON line keys follow the driver contract; ``roofline`` reports the solver
+kernel with the largest device time: algorithmic bytes (matrix streams of
+every SpMV pass plus the CG vector traffic) divided by its CUDA-event time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and time-to-1e-5 KKT residual: chosen form vs plain FP64, 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _bytes_per_pass(prob, sT):
+    m, n = prob["A"].shape
+    nnz = prob["A"].nnz
+    return nnz * (sT + 4) + ((m + n) / 2 + 1) * 4
+
+
+def algorithmic_bytes(prob, info, phase):
+    """Matrix streams of every SpMV pass (values + column indices + row
+    pointers of A or A^T) plus the CG vector traffic of the phase."""
+    m, n = prob["A"].shape
+    sT = 8 if phase == 0 else 4
+    passes = info["mat_passes"][phase]
+    cg = info["cg_iters"] - info["cg_iters_fp32"] if phase == 0 else info["cg_iters_fp32"]
+    return passes * _bytes_per_pass(prob, sT) + cg * (11 * n + 2 * m) * sT
+
+
+def build_workload(name, rank):
+    from paper_1903_06477_gb300 import workloads as W
+    if name == "c2":
+        prob = W.c2_planted(seed=0)
+        kw = dict(direction=0, mem=10, eps=1e-6, max_iters=20000, cg_rtol=1e-10)
+        cfg = {"workload": "planted sparse cone program n=100000 m=200000 (100000 orthant + 2000 SOC dim 50), "
+                           "nnz=1e7, AA mem 10, eps 1e-6", "n": prob["A"].shape[1], "m": prob["A"].shape[0],
+               "nnz": int(prob["A"].nnz)}
+    elif name == "c2_small":
+        prob = W.c2_planted(seed=0, scale=0.05)
+        kw = dict(direction=0, mem=10, eps=1e-6, max_iters=20000, cg_rtol=1e-10)
+        cfg = {"workload": "planted sparse cone program scaled 0.05", "n": prob["A"].shape[1],
+               "m": prob["A"].shape[0], "nnz": int(prob["A"].nnz)}
+    elif name == "c1":
+        prob = W.lasso(seed=0)
+        kw = dict(direction=1, mem=10, c0=0.1, eps=1e-5, max_iters=20000, cg_rtol=1e-10)
+        cfg = {"workload": "LASSO 60x120 epigraph (m=302, n=241), RB mem 10, eps 1e-5", "n": 241, "m": 302,
+               "nnz": int(prob["A"].nnz)}
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return prob, kw, cfg
+
+
+def oracle_baseline(prob, kw, small_prob):
+    """Times the FP64 oracle on a bounded sample: its setup (the g solve) and
+    one outer iteration of Algorithm 1 on the full instance; the iteration
+    count to eps is the oracle's own count on a 0.02-scaled instance of the
+    same family.  Returns (solves/s estimate, detail dict)."""
+    from oracle import oracle as O
+    okw = dict(kw)
+    okw["direction"] = {0: O.DIR_AA, 1: O.DIR_RB}[kw.get("direction", 0)]
+    t0 = time.perf_counter()
+    small = O.Oracle(small_prob, **okw).solve()
+    t_small = time.perf_counter() - t0
+    iters_needed = max(1, small["info"].iters)
+    okw1 = dict(okw, max_iters=1)
+    t0 = time.perf_counter()
+    orc = O.Oracle(prob, **okw1)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.solve()
+    t_iter = time.perf_counter() - t0
+    orc.close()
+    est = t_setup + t_iter * iters_needed
+    return 1.0 / est, {"t_setup_s": t_setup, "t_first_iteration_s": t_iter, "iters_to_eps_scaled": iters_needed,
+                       "t_scaled_solve_s": t_small, "est_time_to_eps_s": est}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1903_06477_gb300 import workloads as W
+    from oracle import oracle as O
+    prob, kw, cfg = build_workload(args.workload, 0)
+    small = W.c2_planted(seed=0, scale=0.02) if args.workload.startswith("c2") else prob
+    okw = dict(kw)
+    okw["direction"] = {0: O.DIR_AA, 1: O.DIR_RB}[kw.get("direction", 0)]
+    small_out = O.Oracle(small, **okw).solve()
+    iters_needed = max(1, small_out["info"].iters)
+    t0 = time.perf_counter()
+    orc = O.Oracle(prob, **dict(okw, max_iters=1))
+    t_setup = time.perf_counter() - t0
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        orc.solve()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t_iter = float(np.mean(times))
+    est = t_setup + t_iter * iters_needed
+    value = 1.0 / est
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step = 1 outer iteration of the FP64 oracle on the full instance; "
+                                   f"solves/s = 1/(setup {t_setup:.2f}s + mean step x {iters_needed} iterations, "
+                                   f"the oracle's count on the 0.02-scaled instance)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    from paper_1903_06477_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    prob, kw, cfg = build_workload(args.workload, rank)
+    prec = B.MIXED if args.precision == "mixed" else B.FP64
+    n, m = prob["A"].shape[1], prob["A"].shape[0]
+    work = B.Work(prob, stream=stream, precision=prec, **kw)
+    xd = torch.empty(n, dtype=torch.float64, device="cuda")
+    yd = torch.empty(m, dtype=torch.float64, device="cuda")
+    sd = torch.empty(m, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        work.solve(xd, yd, sd)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    infos = []
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            _, _, _, info = work.solve(xd, yd, sd)
+            ev1[k].record(stream)
+            infos.append(info)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    last = infos[-1]
+    # plain FP64 solve of the same instance, for the chosen-form comparison
+    fp64_ms = None
+    fp64_info = None
+    if prec == B.MIXED:
+        work64 = B.Work(prob, stream=stream, precision=B.FP64, **kw)
+        work64.solve(xd, yd, sd)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        x64, _, _, fp64_info = work64.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+        xm = xd.cpu().numpy()
+        last["err_vs_fp64"] = float(np.linalg.norm(xm - x64) / max(1e-300, np.linalg.norm(x64)))
+        work64.close()
+    # roofline of the dominant solver kernel
+    peak, peak_kind = _peaks()
+    phase = 1 if (prec == B.MIXED and last["kernel_s"][1] >= last["kernel_s"][0]) else 0
+    ks = float(np.mean([i["kernel_s"][phase] for i in infos]))
+    abytes = algorithmic_bytes(prob, last, phase)
+    achieved = abytes / ks / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "k_grid<float> (FP32 phase)" if phase == 1 else "k_grid<double> (FP64 phase)",
+                "kernel_ms": ks * 1e3, "algorithmic_bytes": abytes}
+    # e2e through the public API with host buffers: setup (H2D of A,b,c) + solve + D2H of x,y,s
+    e2e = None
+    if args.e2e_steps > 0:
+        times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            w2 = B.Work(prob, stream=stream, precision=prec, **kw)
+            w2.solve()
+            w2.close()
+            times.append(time.perf_counter() - t0)
+        A = prob["A"]
+        h2d = A.nnz * 12 + (m + 1) * 8 + (m + n) * 8
+        d2h = (n + 2 * m) * 8
+        e2e = {"value": 1.0 / float(np.mean(times)), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "includes": "scs_setup (validation, A^T build, H2D, g solve) + "
+                                                            "scs_solve + D2H, host buffers"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("c2"):
+        val, det = oracle_baseline(prob, kw, W.c2_planted(seed=0, scale=0.02))
+        cpu = {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, 1 thread: setup + 1 outer iteration on the full instance, scaled by the "
+                         "oracle's iteration count on the 0.02-scaled instance", **det}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == B.MIXED else "f64", "data": "synthetic",
+            "config": dict(cfg, precision=args.precision, l2="flushed (256 MB write) before every step; "
+                                                               "the matrix streams exceed L2 as well",
+                           parallelism="replicas" if world > 1 else "single"),
+            "time_to_eps_s": total_ms / args.steps / 1e3,
+            "status": last["status"], "iters": last["iters"], "iters_fp32": last["iters_fp32"],
+            "cg_iters": last["cg_iters"], "kkt": max(last["pr"], last["dr"], last["gap"]),
+            "pobj": last["pobj"], "err_vs_fp64": last.get("err_vs_fp64"),
+            "fp64_time_to_eps_s": None if fp64_ms is None else fp64_ms / 1e3,
+            "fp64_iters": None if fp64_info is None else fp64_info["iters"],
+            "speedup_vs_fp64": None if fp64_ms is None else fp64_ms / (total_ms / args.steps),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (4 if prec == B.MIXED else 1),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    work.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

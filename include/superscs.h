@@ -1,0 +1,190 @@
+/*
+ * superscs.h -- C ABI of the GB300-native SuperSCS solver (libsuperscs.so).
+ *
+ * Method: Sopasakis, Menounou, Patrinos, "SuperSCS: fast and accurate
+ * large-scale conic optimization", arXiv 1903.06477.
+ *
+ * Problem (Sec. 3, primal (P)):   minimize <c,x>  s.t.  b - A x = s,  s in K
+ * Dual    (Sec. 3, (D)):          minimize <b,y>  s.t.  y in K*,  A^T y + c = 0
+ * The solver applies Douglas-Rachford splitting to the homogeneous self-dual
+ * embedding (Sec. 3.1, Eq. drs) and globalises it with SuperMann
+ * (Algorithm 1) using restarted Broyden (Algorithm 2) or Anderson directions
+ * (Sec. 4.4).  Every step runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Cone rows of s are ordered [ f zero | l orthant | q SOCs | s PSDs ].
+ *    An SOC block (x, t) stores t LAST (Sec. 2, cone (iii)).  A PSD block of
+ *    order d occupies d(d+1)/2 rows holding svec(X): lower triangle, column
+ *    by column, off-diagonal entries multiplied by sqrt(2) (Sec. 2, map mat).
+ *  - A is CSR with m rows: Ap[m+1] (int64, Ap[0] = 0), Ai[nnz] (int32 column
+ *    indices in [0,n)), Ax[nnz].  nnz must be below 2^31.
+ *  - HSDE vectors u = (chi, psi, tau) have N = n + m + 1 entries (Sec. 3.1).
+ *  - All input arrays are caller-owned and only read.  scs_setup copies them
+ *    to the device.  Output and vector arguments may be host or device
+ *    pointers (unified addressing decides the copy direction).
+ *  - Every function returns SCS_OK (0) or a negative error code and never
+ *    aborts; the algorithmic outcome is reported in scs_info.status.
+ */
+#ifndef SUPERSCS_H
+#define SUPERSCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SCS_OK 0
+#define SCS_EINVAL (-1)   /* bad sizes, cone dims not summing to m, non-finite data, bad settings */
+#define SCS_ENOMEM (-2)   /* device or host allocation failed */
+#define SCS_ECUDA (-3)    /* a CUDA call failed; see scs_last_error */
+#define SCS_ETIMEOUT (-4) /* a device-wide barrier waited more than 10 s; the solve was abandoned */
+
+/* scs_info.status (Sec. 3.1 recovery rules and Sec. 4.3 certificates) */
+#define SCS_SOLVED 1
+#define SCS_INFEASIBLE (-1)
+#define SCS_UNBOUNDED (-2)
+#define SCS_MAX_ITERS (-3)
+#define SCS_TIME_LIMIT (-4)
+#define SCS_NUMERICAL (-5)
+
+/* directions (Sec. 4.4) */
+#define SCS_DIR_AA 0   /* Anderson's acceleration */
+#define SCS_DIR_RB 1   /* restarted Broyden, Algorithm 2 */
+#define SCS_DIR_NONE 2 /* d = 0: with c0 = 0 every step is the KM step of Eq. (km) */
+
+/* precision */
+#define SCS_FP64 0  /* every vector and the matrix in FP64 */
+#define SCS_MIXED 1 /* FP32 bulk (matrix, vectors, CG, projections), FP64 scalars and
+                       reductions, then an FP64 refinement phase that confirms eps */
+
+/* execution team */
+#define SCS_TEAM_AUTO 0
+#define SCS_TEAM_BLOCK 1 /* one thread block per instance */
+#define SCS_TEAM_GRID 2  /* every SM on one instance (cooperative launch) */
+
+typedef struct {
+    int32_t f, l;        /* zero-cone rows, orthant rows (Sec. 2 cones (i), (iv)) */
+    int32_t nq;          /* number of SOCs */
+    const int32_t *q;    /* SOC dimensions, each >= 1 (Sec. 2 cone (iii)) */
+    int32_t ns;          /* number of PSD blocks */
+    const int32_t *s;    /* PSD orders d, each 1..64 (Sec. 2 cone (ii)) */
+} scs_cone;
+
+typedef struct {
+    int32_t m, n;
+    const int64_t *Ap;
+    const int32_t *Ai;
+    const double *Ax;
+    const double *b; /* m */
+    const double *c; /* n */
+} scs_data;
+
+typedef struct {
+    int32_t direction;   /* SCS_DIR_AA | SCS_DIR_RB | SCS_DIR_NONE */
+    int32_t mem;         /* memory of the direction (AA: 1..32, RB: 0..64) */
+    double eps;          /* tolerance of Sec. 4.3 on pr, dr, gap, ic, uc */
+    double c0, c1, q, sigma, lambda; /* Algorithm 1 parameters */
+    double thetabar;     /* Powell safeguard of Algorithm 2 */
+    int32_t max_iters;   /* outer iterations of Algorithm 1 */
+    int32_t ls_max;      /* backtracking halvings before the KM fallback (alpha = 0) */
+    int32_t cg_max;      /* CG iterations per linear solve */
+    int32_t check_every; /* termination test period */
+    double cg_rtol;      /* CG stops when ||res|| <= cg_rtol ||rhs|| */
+    double time_limit_s; /* <= 0: none */
+    int32_t precision;   /* SCS_FP64 | SCS_MIXED */
+    int32_t warm;        /* 0: u0 = (0,0,1);  1: u0 = warm_u */
+    const double *warm_u;/* N values (host or device) when warm = 1 */
+    int32_t verbose;
+    double aa_reg;       /* Tikhonov factor of the AA normal equations */
+    int32_t team;        /* SCS_TEAM_* */
+    int32_t threads;     /* threads per block, 0 = automatic */
+    double mixed_cg_rtol;   /* CG tolerance of the FP32 phase (SCS_MIXED) */
+    int32_t mixed_stall;    /* FP32 phase ends after this many iterations without a
+                               10% drop of max(pr,dr,gap) (SCS_MIXED) */
+    int32_t mixed_max_iters;/* cap on FP32-phase iterations (SCS_MIXED) */
+} scs_settings;
+
+typedef struct {
+    int32_t status;      /* SCS_SOLVED ... SCS_NUMERICAL */
+    int32_t iters;       /* outer iterations (all phases) */
+    int32_t k0, k1, k2, backtracks;
+    int64_t cg_iters;
+    double pr, dr, gap, ic, uc; /* Sec. 4.3, evaluated in FP64 on the final iterate */
+    double pobj, dobj;   /* <c,x> and -<b,y> */
+    double setup_s, solve_s;
+    double err_vs_fp64;  /* unused by the library (0); benchmarks fill it */
+    int32_t iters_fp32;  /* outer iterations of the FP32 phase (SCS_MIXED) */
+    int32_t device_error;/* nonzero if a device barrier timed out */
+    double kernel_s[2];  /* device time of the solver launch of the FP64 [0] and FP32 [1] phase
+                            (CUDA events on the work's stream) */
+    int64_t mat_passes[2]; /* passes over A or A^T (one SpMV each) in the FP64 [0] / FP32 [1] phase */
+    int64_t cg_iters_fp32; /* CG iterations of the FP32 phase */
+} scs_info;
+
+typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
+typedef struct scs_batch scs_batch; /* opaque; owns all device memory of a batch */
+
+/* Fills *out with the defaults: AA, mem 10, eps 1e-5, c0 0.99, c1 0.99,
+ * q 0.99, sigma 1e-2, lambda 1, thetabar 0.1, max_iters 10000, ls_max 20,
+ * cg_max 1000, check_every 1, cg_rtol 1e-10, FP64, cold start, auto team. */
+int scs_default_settings(scs_settings *out);
+
+/* Validates the data, copies A, b, c to the device, builds the transposed
+ * copy of A (CSR of A^T) and precomputes g = M^{-1}(c, b) (one CG solve; the
+ * block elimination of (I+Q)^{-1}, Sec. 4.1).  cuda_stream may be NULL (the
+ * legacy default stream).  On success *out owns the device memory. */
+int scs_setup(const scs_data *data, const scs_cone *cone, const scs_settings *settings,
+              void *cuda_stream, scs_work **out);
+
+/* Runs Algorithm 1 to the settings' tolerance.  x (n), y (m), s (m) receive
+ * the solution (Sec. 3.1 recovery: (chi, psi, sigma)/tau); for INFEASIBLE,
+ * y holds the certificate scaled to <b,y> = -1 and x, s are NaN; for
+ * UNBOUNDED, x and s hold the certificate scaled to <c,x> = -1 and y is NaN.
+ * Any of x, y, s, info may be NULL.  Synchronises the work's stream. */
+int scs_solve(scs_work *work, double *x, double *y, double *s, scs_info *info);
+
+/* Replaces b (m) and/or c (n) of a set-up problem (NULL keeps the old one)
+ * and recomputes g; A and the cones stay.  For parametric families. */
+int scs_update_bc(scs_work *work, const double *b, const double *c);
+
+/* The final HSDE iterate u (N values) of the last scs_solve, for warm starts
+ * and checkpoint/resume (any u0 converges, Sec. 4.5). */
+int scs_get_u(scs_work *work, double *u);
+
+/* --- single operators of Eq. (drs), for checking one step at a time ------ */
+/* out = (I+Q)^{-1} r on N-vectors (Sec. 4.1, linear-system step of Eq. drs).
+ * Uses and updates the work's CG warm start of slot 0 (u~) or 1 (d~). */
+int scs_linsys(scs_work *work, const double *r, double *out, int32_t slot);
+/* out = Pi_C(v), C = R^n x K* x R_+ (Sec. 3.1; projection step of Eq. drs). */
+int scs_project_cone(scs_work *work, const double *v, double *out);
+/* Tu = u + Pi_C(2u~ - u) - u~ and Ru = u - Tu (Sec. 4.1-4.2); either may be NULL. */
+int scs_apply_T(scs_work *work, const double *u, double *Tu, double *Ru);
+
+/* Frees everything owned by work; NULL-safe. */
+void scs_finish(scs_work *work);
+
+/* Message of the last error on work, or of the calling thread when work is NULL. */
+const char *scs_last_error(const scs_work *work);
+
+/* --- batched solves ------------------------------------------------------ */
+/* B independent instances of any sizes, solved by one persistent launch in
+ * which each thread block takes instances from a queue, largest first.
+ * The settings apply to every instance (team is ignored: one block each). */
+int scs_batch_setup(int32_t B, const scs_data *const *data, const scs_cone *const *cones,
+                    const scs_settings *settings, void *cuda_stream, scs_batch **out);
+/* x[i], y[i], s[i] (any may be NULL, as may the arrays) receive instance i's
+ * result as in scs_solve; infos may be NULL or hold B entries. */
+int scs_batch_solve(scs_batch *batch, double *const *x, double *const *y, double *const *s,
+                    scs_info *infos);
+void scs_batch_finish(scs_batch *batch);
+/* One-shot: setup, solve, finish. */
+int scs_solve_batch(int32_t B, const scs_data *const *data, const scs_cone *const *cones,
+                    const scs_settings *settings, void *cuda_stream, double *const *x,
+                    double *const *y, double *const *s, scs_info *infos);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUPERSCS_H */

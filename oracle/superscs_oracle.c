@@ -673,6 +673,9 @@ int orc_solve(orc_work *W, double *x, double *y, double *s, double *u_out, orc_i
     double *wb = buf + 8 * N, *Rw = buf + 9 * N, *zp = buf + 10 * N, *xip = buf + 11 * N;
     int64_t cg0 = W->cg_total;
     if (trace) trace->len = 0;
+    /* every solve starts both CG warm starts from zero */
+    memset(W->ws[0], 0, sizeof(double) * (size_t)W->P.n);
+    memset(W->ws[1], 0, sizeof(double) * (size_t)W->P.n);
 
     if (S->warm_u) memcpy(u, S->warm_u, sizeof(double) * (size_t)N);
     else u[N - 1] = 1.0;

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libsuperscs.so (include/superscs.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Loading fails loudly if the library has not been built; there
+is no CPU fallback.  Vectors may be numpy arrays (host) or CUDA torch tensors
+(device); the library copies with unified addressing either way.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsuperscs.so")
+
+SCS_OK, SCS_EINVAL, SCS_ENOMEM, SCS_ECUDA, SCS_ETIMEOUT = 0, -1, -2, -3, -4
+SOLVED, INFEASIBLE, UNBOUNDED, MAX_ITERS, TIME_LIMIT, NUMERICAL = 1, -1, -2, -3, -4, -5
+DIR_AA, DIR_RB, DIR_NONE = 0, 1, 2
+FP64, MIXED = 0, 1
+TEAM_AUTO, TEAM_BLOCK, TEAM_GRID = 0, 1, 2
+
+
+class Cone(C.Structure):
+    _fields_ = [("f", C.c_int32), ("l", C.c_int32), ("nq", C.c_int32), ("q", C.POINTER(C.c_int32)),
+                ("ns", C.c_int32), ("s", C.POINTER(C.c_int32))]
+
+
+class Data(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("Ap", C.POINTER(C.c_int64)), ("Ai", C.POINTER(C.c_int32)),
+                ("Ax", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)), ("c", C.POINTER(C.c_double))]
+
+
+class Settings(C.Structure):
+    _fields_ = [
+        ("direction", C.c_int32), ("mem", C.c_int32), ("eps", C.c_double),
+        ("c0", C.c_double), ("c1", C.c_double), ("q", C.c_double), ("sigma", C.c_double),
+        ("lam", C.c_double), ("thetabar", C.c_double),
+        ("max_iters", C.c_int32), ("ls_max", C.c_int32), ("cg_max", C.c_int32), ("check_every", C.c_int32),
+        ("cg_rtol", C.c_double), ("time_limit_s", C.c_double),
+        ("precision", C.c_int32), ("warm", C.c_int32), ("warm_u", C.c_void_p), ("verbose", C.c_int32),
+        ("aa_reg", C.c_double), ("team", C.c_int32), ("threads", C.c_int32),
+        ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("iters", C.c_int32), ("k0", C.c_int32), ("k1", C.c_int32), ("k2", C.c_int32),
+        ("backtracks", C.c_int32), ("cg_iters", C.c_int64),
+        ("pr", C.c_double), ("dr", C.c_double), ("gap", C.c_double), ("ic", C.c_double), ("uc", C.c_double),
+        ("pobj", C.c_double), ("dobj", C.c_double), ("setup_s", C.c_double), ("solve_s", C.c_double),
+        ("err_vs_fp64", C.c_double), ("iters_fp32", C.c_int32), ("device_error", C.c_int32),
+        ("kernel_s", C.c_double * 2), ("mat_passes", C.c_int64 * 2), ("cg_iters_fp32", C.c_int64),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        for k in ("kernel_s", "mat_passes"):
+            d[k] = list(d[k])
+        return d
+
+
+class SCSError(RuntimeError):
+    pass
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point of include/superscs.h
+_SIGS = [
+    ("scs_default_settings", C.c_int, [C.POINTER(Settings)]),
+    ("scs_setup", C.c_int, [C.POINTER(Data), C.POINTER(Cone), C.POINTER(Settings), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("scs_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+    ("scs_update_bc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_get_u", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("scs_linsys", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_finish", None, [C.c_void_p]),
+    ("scs_last_error", C.c_char_p, [C.c_void_p]),
+    ("scs_batch_setup", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    ("scs_batch_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+    ("scs_batch_finish", None, [C.c_void_p]),
+    ("scs_solve_batch", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+]
+
+
+def lib():
+    """Load libsuperscs.so; raise if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise SCSError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error(work=None) -> str:
+    msg = lib().scs_last_error(work)
+    return msg.decode() if msg else ""
+
+
+def _check(rc, work=None):
+    if rc != SCS_OK:
+        raise SCSError(f"superscs error {rc}: {last_error(work)}")
+
+
+def default_settings(**kw) -> Settings:
+    s = Settings()
+    _check(lib().scs_default_settings(C.byref(s)))
+    for k, v in kw.items():
+        if k == "lambda":
+            k = "lam"
+        if not hasattr(s, k):
+            raise KeyError(k)
+        setattr(s, k, v)
+    return s
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (host or CUDA)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class _Keep:
+    """Holds the numpy buffers behind a Data/Cone pair."""
+
+    def __init__(self, prob):
+        A = prob["A"]
+        self.m, self.n = A.shape
+        self.Ap = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        self.Ai = np.ascontiguousarray(A.indices, dtype=np.int32)
+        self.Ax = np.ascontiguousarray(A.data, dtype=np.float64)
+        self.b = np.ascontiguousarray(prob["b"], dtype=np.float64)
+        self.c = np.ascontiguousarray(prob["c"], dtype=np.float64)
+        self.q = np.ascontiguousarray(list(prob.get("q", [])) or [0], dtype=np.int32)
+        self.s = np.ascontiguousarray(list(prob.get("s", [])) or [0], dtype=np.int32)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        self.data = Data(self.m, self.n, self.Ap.ctypes.data_as(C.POINTER(C.c_int64)), ip(self.Ai), dp(self.Ax),
+                         dp(self.b), dp(self.c))
+        self.cone = Cone(int(prob.get("f", 0)), int(prob.get("l", 0)), len(prob.get("q", [])), ip(self.q),
+                         len(prob.get("s", [])), ip(self.s))
+
+
+class Work:
+    """One problem set up on the device (scs_setup ... scs_finish)."""
+
+    def __init__(self, prob, settings: Settings | None = None, stream=None, **kw):
+        L = lib()
+        self._keep = _Keep(prob)
+        self.n, self.m = self._keep.n, self._keep.m
+        self.N = self.n + self.m + 1
+        self.settings = settings if settings is not None else default_settings(**kw)
+        self._warm = None
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if isinstance(stream, int) else (C.c_void_p(stream.cuda_stream) if stream is not None else None)
+        _check(L.scs_setup(C.byref(self._keep.data), C.byref(self._keep.cone), C.byref(self.settings), st,
+                           C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scs_finish(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_warm(self, u):
+        """Warm start from an HSDE iterate u (N values); None for a cold start."""
+        if u is None:
+            self.settings.warm = 0
+            self.settings.warm_u = None
+            self._warm = None
+        else:
+            self._warm = u if hasattr(u, "data_ptr") else np.ascontiguousarray(u, dtype=np.float64)
+            self.settings.warm = 1
+            self.settings.warm_u = _ptr(self._warm).value
+
+    def solve(self, x=None, y=None, s=None):
+        """Returns (x, y, s, info dict); outputs may be preallocated host or device buffers."""
+        x = np.empty(self.n) if x is None else x
+        y = np.empty(self.m) if y is None else y
+        s = np.empty(self.m) if s is None else s
+        info = Info()
+        _check(lib().scs_solve(self.h, _ptr(x), _ptr(y), _ptr(s), C.byref(info)), self.h)
+        return x, y, s, info.as_dict()
+
+    def update_bc(self, b=None, c=None):
+        bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        cc = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+        _check(lib().scs_update_bc(self.h, _ptr(bb), _ptr(cc)), self.h)
+
+    def get_u(self):
+        u = np.empty(self.N)
+        _check(lib().scs_get_u(self.h, _ptr(u)), self.h)
+        return u
+
+    def linsys(self, r, slot=0):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        out = np.empty(self.N)
+        _check(lib().scs_linsys(self.h, _ptr(r), _ptr(out), slot), self.h)
+        return out
+
+    def project_cone(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty(self.N)
+        _check(lib().scs_project_cone(self.h, _ptr(v), _ptr(out)), self.h)
+        return out
+
+    def apply_T(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        Tu, Ru = np.empty(self.N), np.empty(self.N)
+        _check(lib().scs_apply_T(self.h, _ptr(u), _ptr(Tu), _ptr(Ru)), self.h)
+        return Tu, Ru
+
+
+class Batch:
+    """B independent problems solved by one persistent launch."""
+
+    def __init__(self, probs, settings: Settings | None = None, stream=None, **kw):
+        L = lib()
+        self.keeps = [_Keep(p) for p in probs]
+        self.B = len(probs)
+        self.settings = settings if settings is not None else default_settings(**kw)
+        self._dp = (C.POINTER(Data) * self.B)(*[C.pointer(k.data) for k in self.keeps])
+        self._cp = (C.POINTER(Cone) * self.B)(*[C.pointer(k.cone) for k in self.keeps])
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if isinstance(stream, int) else (C.c_void_p(stream.cuda_stream) if stream is not None else None)
+        _check(L.scs_batch_setup(self.B, self._dp, self._cp, C.byref(self.settings), st, C.byref(h)))
+        self.h = h
+
+    def solve(self):
+        xs = [np.empty(k.n) for k in self.keeps]
+        ys = [np.empty(k.m) for k in self.keeps]
+        ss = [np.empty(k.m) for k in self.keeps]
+        arr = lambda lst: (C.c_void_p * self.B)(*[a.ctypes.data for a in lst])
+        infos = (Info * self.B)()
+        _check(lib().scs_batch_solve(self.h, arr(xs), arr(ys), arr(ss), infos))
+        return xs, ys, ss, [infos[i].as_dict() for i in range(self.B)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scs_batch_finish(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1282 @@
+// solver.cuh -- device-resident SuperSCS (Sopasakis, Menounou, Patrinos,
+// arXiv 1903.06477), generic over the bulk precision T (double or float)
+// and over the execution team (one CTA, or every CTA of a cooperative grid).
+//
+// Structure of one outer iteration (Algorithm 1):
+//   termination test (Sec. 4.3)       2 SpMVs + 1 reduction
+//   direction d (Sec. 4.4, AA or RB)   passes over the N x mem buffers
+//   d~ = (I+Q)^{-1} d                  CG on I + A^T A (Sec. 4.1)
+//   K0 | line search with K1/K2        fused projection + residual passes
+// HSDE vectors keep their tau entry in FP64 whatever T is.
+#pragma once
+
+#include "common.cuh"
+#include "team.cuh"
+
+namespace sscs {
+
+constexpr int MAXMEM = 64;   // direction memory cap (RB)
+constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared memory)
+constexpr int PSD_MAX = 64;  // largest PSD order
+
+enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4 };
+enum { ST_SOLVED = 1, ST_INFEASIBLE = -1, ST_UNBOUNDED = -2, ST_MAX_ITERS = -3, ST_TIME_LIMIT = -4,
+       ST_NUMERICAL = -5, ST_STALLED = -6 };
+
+template <typename T>
+struct HV {  // HSDE vector: (chi, psi) bulk of n+m entries in T, tau in FP64
+    T* v;
+    double* t;
+};
+
+struct DevSettings {
+    int direction, mem;
+    double eps, c0, c1, q, sigma, lambda, thetabar;
+    int max_iters, ls_max, cg_max, check_every;
+    double cg_rtol, aa_reg;
+    double time_limit_ns;  // <= 0: none
+    int stall_iters;       // > 0: stop when max(pr,dr,gap) has not dropped 10% for this many iterations
+    int use_warm;
+};
+
+struct DevState {
+    int status, iters, k0, k1, k2, backtracks;
+    long long cg_iters;
+    double pr, dr, gap, ic, uc, pobj, dobj, nRu, hg;
+    int setup_cg, pad;
+    long long mat_passes;  // SpMV passes over A or A^T
+};
+
+template <typename T>
+struct DevProb {
+    int n, m;
+    const int *Ap, *Ai;
+    const T* Ax;  // CSR of A (m rows)
+    const int *Tp, *Ti;
+    const T* Tx;  // CSR of A^T (n rows)
+    const T *b, *c;
+    double nb, nc;
+    int f, l, nq, ns;
+    const int* q_off;  // nq+1 row offsets of the SOCs inside s
+    const int* s_dim;  // ns PSD orders
+    const int* s_off;  // ns row offsets of the PSD blocks inside s
+    int vecA, vecT;    // SpMV sub-warp widths
+};
+
+template <typename T>
+struct DevWork {
+    HV<T> u, ut, ub, Ru, d, dt, wb, Rw, zp, xip, zt;
+    T* g;       // n+m: g = M^{-1}(c, b)
+    T* ws[2];   // CG warm starts (n) for the u~ and d~ systems
+    T *cr, *cp, *cq, *tn;  // n
+    T *tm, *py;            // m
+    T* Zv;
+    double* Zt;  // mem columns (AA: z^i; RB: z^i)
+    T* Xv;
+    double* Xt;  // mem columns (AA: xi^i; RB: z~^i)
+    double *io_in, *io_out, *io_out2;      // N-vectors of the single-operator entries
+    double* warm;                          // N: warm start (FP64)
+    double *x_out, *y_out, *s_out, *u_out; // results (FP64)
+    double* partials;
+    unsigned* bar;
+    int* abort_flag;
+    DevState* st;
+};
+
+template <typename T>
+struct Args {
+    DevProb<T> P;
+    DevWork<T> W;
+    DevSettings S;
+    int mode;
+    int slot;
+};
+
+// ---------------------------------------------------------------------------
+// sparse products: sub-warp groups of V lanes per row (V = 1..32)
+// ---------------------------------------------------------------------------
+template <int V>
+__device__ __forceinline__ unsigned group_mask()
+{
+    if constexpr (V == 32) return FULL_MASK;
+    else return ((1u << V) - 1u) << ((threadIdx.x & 31) & ~(V - 1));
+}
+
+template <int V, typename T, class Team, class Epi>
+__device__ __forceinline__ void spmv_v(const Team& tm, int rows, const int* rp, const int* ci, const T* val,
+                                       const T* x, Epi& epi)
+{
+    const int r = tm.rank();
+    const int lane = r & (V - 1);
+    const int ng = tm.size() / V;
+    const unsigned mask = group_mask<V>();
+    for (int row = r / V; row < rows; row += ng) {
+        const int s = ro(rp + row), e = ro(rp + row + 1);
+        T a0 = 0, a1 = 0;
+        int k = s + lane;
+        for (; k + V < e; k += 2 * V) {
+            const int c0 = ro(ci + k), c1 = ro(ci + k + V);
+            const T v0 = ro(val + k), v1 = ro(val + k + V);
+            a0 += v0 * x[c0];
+            a1 += v1 * x[c1];
+        }
+        if (k < e) a0 += ro(val + k) * x[ro(ci + k)];
+        T acc = a0 + a1;
+#pragma unroll
+        for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+        if (lane == 0) epi(row, acc);
+    }
+}
+
+template <int V, typename T, class Team, class Epi>
+__device__ __forceinline__ void spmv2_v(const Team& tm, int rows, const int* rp, const int* ci, const T* val,
+                                        const T* x1, const T* x2, Epi& epi)
+{
+    const int r = tm.rank();
+    const int lane = r & (V - 1);
+    const int ng = tm.size() / V;
+    const unsigned mask = group_mask<V>();
+    for (int row = r / V; row < rows; row += ng) {
+        const int s = ro(rp + row), e = ro(rp + row + 1);
+        T a1 = 0, a2 = 0;
+        for (int k = s + lane; k < e; k += V) {
+            const int c = ro(ci + k);
+            const T v = ro(val + k);
+            a1 += v * x1[c];
+            a2 += v * x2[c];
+        }
+#pragma unroll
+        for (int o = V / 2; o > 0; o >>= 1) {
+            a1 += __shfl_xor_sync(mask, a1, o);
+            a2 += __shfl_xor_sync(mask, a2, o);
+        }
+        if (lane == 0) epi(row, a1, a2);
+    }
+}
+
+template <typename T, class Team, class Epi>
+__device__ void spmv(const Team& tm, int V, int rows, const int* rp, const int* ci, const T* val, const T* x, Epi epi)
+{
+    switch (V) {
+        case 1: spmv_v<1>(tm, rows, rp, ci, val, x, epi); break;
+        case 2: spmv_v<2>(tm, rows, rp, ci, val, x, epi); break;
+        case 4: spmv_v<4>(tm, rows, rp, ci, val, x, epi); break;
+        case 8: spmv_v<8>(tm, rows, rp, ci, val, x, epi); break;
+        case 16: spmv_v<16>(tm, rows, rp, ci, val, x, epi); break;
+        default: spmv_v<32>(tm, rows, rp, ci, val, x, epi); break;
+    }
+}
+
+template <typename T, class Team, class Epi>
+__device__ void spmv2(const Team& tm, int V, int rows, const int* rp, const int* ci, const T* val, const T* x1,
+                      const T* x2, Epi epi)
+{
+    switch (V) {
+        case 1: spmv2_v<1>(tm, rows, rp, ci, val, x1, x2, epi); break;
+        case 2: spmv2_v<2>(tm, rows, rp, ci, val, x1, x2, epi); break;
+        case 4: spmv2_v<4>(tm, rows, rp, ci, val, x1, x2, epi); break;
+        case 8: spmv2_v<8>(tm, rows, rp, ci, val, x1, x2, epi); break;
+        case 16: spmv2_v<16>(tm, rows, rp, ci, val, x1, x2, epi); break;
+        default: spmv2_v<32>(tm, rows, rp, ci, val, x1, x2, epi); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M^{-1}(a, e) for M = [I A^T; -A I]: x = (I + A^T A)^{-1}(a - A^T e) by CG
+// warm-started from x (in place), y = e + A x written to W.py.  Returns the CG
+// iterations; htp = <c, x> + <b, y>.  CG stops when ||res|| <= rtol ||rhs||.
+// (Block elimination of the linear-system step of Eq. drs; Sec. 4.1 names CG.)
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T* a, const T* e, T* x, double rtol,
+                    int cg_max, double& htp)
+{
+    const int n = P.n, m = P.m;
+    T* tmv = W.tm;
+    T* r = W.cr;
+    T* p = W.cp;
+    T* q = W.cq;
+    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, x, [&](int i, T s) { tmv[i] = s; });
+    tm.sync();
+    T acc_b = 0, acc_r = 0;
+    spmv2(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, e, tmv, [&](int j, T s1, T s2) {
+        const T rhs = a[j] - s1;
+        const T res = rhs - x[j] - s2;
+        r[j] = res;
+        p[j] = res;
+        acc_b += rhs * rhs;
+        acc_r += res * res;
+    });
+    double red2[2] = {(double)acc_b, (double)acc_r};
+    tm.reduce(red2);
+    const double rhs2 = red2[0];
+    double rr = red2[1];
+    const double tol = rtol * sqrt(rhs2);
+    int it = 0;
+    if (rhs2 == 0.0) {
+        for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
+        tm.sync();
+    } else if (sqrt(rr) > tol) {
+        while (it < cg_max) {
+            if (tm.aborted()) break;
+            spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, p, [&](int i, T s) { tmv[i] = s; });
+            tm.sync();
+            T pq = 0;
+            spmv(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, tmv, [&](int j, T s) {
+                const T qj = p[j] + s;
+                q[j] = qj;
+                pq += p[j] * qj;
+            });
+            double red1[1] = {(double)pq};
+            tm.reduce(red1);
+            const double alpha = rr / red1[0];
+            const T ta = (T)alpha;
+            T rn = 0;
+            for (int j = tm.rank(); j < n; j += tm.size()) {
+                x[j] += ta * p[j];
+                const T rj = r[j] - ta * q[j];
+                r[j] = rj;
+                rn += rj * rj;
+            }
+            double red3[1] = {(double)rn};
+            tm.reduce(red3);
+            ++it;
+            if (!(sqrt(red3[0]) > tol)) break;
+            const T tb = (T)(red3[0] / rr);
+            rr = red3[0];
+            for (int j = tm.rank(); j < n; j += tm.size()) p[j] = r[j] + tb * p[j];
+            tm.sync();
+        }
+    }
+    T hb = 0, hc = 0;
+    T* py = W.py;
+    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, x, [&](int i, T s) {
+        const T yi = e[i] + s;
+        py[i] = yi;
+        hb += ro(P.b + i) * yi;
+    });
+    for (int j = tm.rank(); j < n; j += tm.size()) hc += ro(P.c + j) * x[j];
+    double red4[2] = {(double)hb, (double)hc};
+    tm.reduce(red4);
+    htp = red4[0] + red4[1];
+    if (tm.leader()) W.st->mat_passes += 3 + 2 * it;
+    return it;
+}
+
+// out = (I+Q)^{-1} r via tau = (r_tau + h^T M^{-1} r) / (1 + h^T g), (x,y) = M^{-1} r - tau g.
+// r and out must not share storage of the bulk part.
+template <typename T, class Team>
+__device__ int linsys(Team& tm, const DevProb<T>& P, const DevWork<T>& W, HV<T> r, HV<T> out, int slot,
+                      double rtol, int cg_max, double hg)
+{
+    const int n = P.n, m = P.m;
+    const double rtau = *r.t;
+    T* x = W.ws[slot];
+    double htp;
+    const int it = minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp);
+    const double tau = (rtau + htp) / (1.0 + hg);
+    const T tt = (T)tau;
+    for (int i = tm.rank(); i < n; i += tm.size()) out.v[i] = x[i] - tt * W.g[i];
+    for (int i = tm.rank(); i < m; i += tm.size()) out.v[n + i] = W.py[i] - tt * W.g[n + i];
+    if (tm.leader()) *out.t = tau;
+    tm.sync();
+    return it;
+}
+
+// ---------------------------------------------------------------------------
+// Projection on C = R^n x K* x R_+ fused with the DRS residual (Eq. drs):
+// for each element the op supplies (w, w~), the pass forms v = 2 w~ - w,
+// projects it (identity on chi and zero-cone rows, max(0,.) on the orthant,
+// closed form per SOC with one warp per cone, eigen-decomposition per PSD
+// block with one CTA per block) and hands (w, w~, w_) back to the op.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int svec_index(int d, int i, int j)  // i >= j
+{
+    return j * d - j * (j - 1) / 2 + (i - j);
+}
+
+__device__ __forceinline__ double block_sum(double x, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// Parallel two-sided Jacobi (round-robin pairing, d/2 disjoint rotations per
+// round) on the dp x dp matrix X in shared memory; V receives the
+// eigenvectors as columns.  Rotation formula as in the textbook cyclic method.
+template <typename T>
+__device__ void jacobi_block(T* X, T* V, int dp, int* pp, int* qq, T* cs, T* sn, double* red, double tol2, int max_sweeps)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int idx = tid; idx < dp * dp; idx += nt) V[idx] = (idx / dp == idx % dp) ? T(1) : T(0);
+    double total = 0.0;
+    for (int idx = tid; idx < dp * dp; idx += nt) total += (double)X[idx] * (double)X[idx];
+    __syncthreads();
+    total = block_sum(total, red);
+    const int half = dp / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double off = 0.0;
+        for (int idx = tid; idx < dp * dp; idx += nt)
+            if (idx / dp != idx % dp) off += (double)X[idx] * (double)X[idx];
+        off = block_sum(off, red);
+        if (off <= tol2 * total || off == 0.0) break;
+        for (int rnd = 0; rnd < dp - 1; ++rnd) {
+            for (int k = tid; k < half; k += nt) {
+                int a, b;
+                if (k == 0) {
+                    a = rnd;
+                    b = dp - 1;
+                } else {
+                    a = (rnd + k) % (dp - 1);
+                    b = (rnd - k + dp - 1) % (dp - 1);
+                }
+                const int p = a < b ? a : b, qd = a < b ? b : a;
+                const T apq = X[p * dp + qd];
+                T c = 1, s = 0;
+                if (apq != T(0)) {
+                    const T theta = (X[qd * dp + qd] - X[p * dp + p]) / (T(2) * apq);
+                    const T at = theta < T(0) ? -theta : theta;
+                    T t;
+                    if (at > T(1e18))
+                        t = T(0.5) / theta;
+                    else
+                        t = (theta >= T(0) ? T(1) : T(-1)) / (at + sqrt(theta * theta + T(1)));
+                    c = T(1) / sqrt(t * t + T(1));
+                    s = t * c;
+                }
+                pp[k] = p;
+                qq[k] = qd;
+                cs[k] = c;
+                sn[k] = s;
+            }
+            __syncthreads();
+            // columns: X <- X J and V <- V J
+            for (int idx = tid; idx < half * dp; idx += nt) {
+                const int k = idx / dp, i = idx % dp;
+                const int p = pp[k], qd = qq[k];
+                const T c = cs[k], s = sn[k];
+                const T xp = X[i * dp + p], xq = X[i * dp + qd];
+                X[i * dp + p] = c * xp - s * xq;
+                X[i * dp + qd] = s * xp + c * xq;
+                const T vp = V[i * dp + p], vq = V[i * dp + qd];
+                V[i * dp + p] = c * vp - s * vq;
+                V[i * dp + qd] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // rows: X <- J^T X
+            for (int idx = tid; idx < half * dp; idx += nt) {
+                const int k = idx / dp, j = idx % dp;
+                const int p = pp[k], qd = qq[k];
+                const T c = cs[k], s = sn[k];
+                const T xp = X[p * dp + j], xq = X[qd * dp + j];
+                X[p * dp + j] = c * xp - s * xq;
+                X[qd * dp + j] = s * xp + c * xq;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+struct PsdSmem {
+    T* X;
+    T* V;
+    int* pp;
+    int* qq;
+    T* cs;
+    T* sn;
+    T* lam;
+    double* red;
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t psd_smem_bytes()
+{
+    return sizeof(T) * (2 * PSD_MAX * PSD_MAX + 3 * PSD_MAX) + sizeof(int) * PSD_MAX + 64 * sizeof(double);
+}
+
+template <typename T>
+__device__ PsdSmem<T> psd_smem(unsigned char* base)
+{
+    PsdSmem<T> s;
+    s.X = (T*)base;
+    s.V = s.X + PSD_MAX * PSD_MAX;
+    s.cs = s.V + PSD_MAX * PSD_MAX;
+    s.sn = s.cs + PSD_MAX / 2;
+    s.lam = s.sn + PSD_MAX / 2;
+    s.red = (double*)(s.lam + 2 * PSD_MAX);
+    s.pp = (int*)(s.red + 32);
+    s.qq = s.pp + PSD_MAX / 2;
+    return s;
+}
+
+template <typename T, class Team, class Op>
+__device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned char* psd_base)
+{
+    const int n = P.n;
+    const int lin = n + P.f + P.l;
+    const int fz = n + P.f;
+    for (int i = tm.rank(); i < lin; i += tm.size()) {
+        T w, wt;
+        op.load(i, w, wt);
+        const T v = T(2) * wt - w;
+        const T wb = (i >= fz) ? (v > T(0) ? v : T(0)) : v;
+        op.store(i, w, wt, wb);
+    }
+    // second-order cones, t last: one warp per cone
+    const int lane = threadIdx.x & 31;
+    const int nw = tm.size() >> 5;
+    for (int k = tm.rank() >> 5; k < P.nq; k += nw) {
+        const int o = n + ro(P.q_off + k);
+        const int dim = ro(P.q_off + k + 1) - ro(P.q_off + k);
+        T ss = 0;
+        for (int j = lane; j < dim - 1; j += 32) {
+            T w, wt;
+            op.load(o + j, w, wt);
+            const T v = T(2) * wt - w;
+            ss += v * v;
+        }
+        T wT, wtT;
+        op.load(o + dim - 1, wT, wtT);
+        const T tv = T(2) * wtT - wT;
+        const double nx = sqrt((double)warp_sum(ss));
+        const double t = (double)tv;
+        int mode;
+        double a = 0.0, tb = 0.0;
+        if (nx <= t) mode = 0;
+        else if (nx <= -t) mode = 1;
+        else {
+            mode = 2;
+            a = (nx + t) / (2.0 * nx);
+            tb = a * nx;
+        }
+        for (int j = lane; j < dim - 1; j += 32) {
+            T w, wt;
+            op.load(o + j, w, wt);
+            const T v = T(2) * wt - w;
+            const T wb = mode == 0 ? v : (mode == 1 ? T(0) : (T)(a * (double)v));
+            op.store(o + j, w, wt, wb);
+        }
+        if (lane == 0) op.store(o + dim - 1, wT, wtT, mode == 0 ? tv : (mode == 1 ? T(0) : (T)tb));
+        __syncwarp();
+    }
+    // PSD blocks: one CTA per block, Jacobi eigen-decomposition in shared memory
+    if (P.ns > 0) {
+        PsdSmem<T> sm = psd_smem<T>(psd_base);
+        for (int k = tm.block(); k < P.ns; k += tm.nblocks()) {
+            const int d = ro(P.s_dim + k);
+            const int o = n + ro(P.s_off + k);
+            const int dp = d + (d & 1);
+            const double isq2 = 0.70710678118654752440;
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
+                const int i = idx / dp, j = idx % dp;
+                T val = 0;
+                if (i < d && j < d) {
+                    const int ii = i > j ? i : j, jj = i > j ? j : i;
+                    T w, wt;
+                    op.load(o + svec_index(d, ii, jj), w, wt);
+                    const T v = T(2) * wt - w;
+                    val = (ii == jj) ? v : (T)((double)v * isq2);
+                }
+                sm.X[idx] = val;
+            }
+            __syncthreads();
+            const double tol2 = sizeof(T) == 8 ? 1e-26 : 1e-11;
+            jacobi_block<T>(sm.X, sm.V, dp, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2, sizeof(T) == 8 ? 20 : 15);
+            for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+                const T l = sm.X[i * dp + i];
+                sm.lam[i] = l > T(0) ? l : T(0);
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+                const int i = idx / d, j = idx % d;
+                if (i < j) continue;
+                T s = 0;
+                for (int kk = 0; kk < dp; ++kk) s += sm.V[i * dp + kk] * sm.lam[kk] * sm.V[j * dp + kk];
+                const int e = o + svec_index(d, i, j);
+                T w, wt;
+                op.load(e, w, wt);
+                op.store(e, w, wt, i == j ? s : (T)((double)s * 1.41421356237309504880));
+            }
+            __syncthreads();
+        }
+    }
+    if (tm.leader()) {
+        double w, wt;
+        op.load_tau(w, wt);
+        const double v = 2.0 * wt - w;
+        op.store_tau(w, wt, v > 0.0 ? v : 0.0);
+    }
+}
+
+// ---- ops of the projection pass ----
+// residual at (u, u~): u_ = Pi(2u~ - u), R = u~ - u_;  acc0 = ||R||^2
+template <typename T>
+struct OpResidual {
+    HV<T> u, ut, ub, R;
+    T acc0;
+    __device__ void load(int i, T& w, T& wt) const { w = u.v[i]; wt = ut.v[i]; }
+    __device__ void store(int i, T, T wt, T wb)
+    {
+        ub.v[i] = wb;
+        const T r = wt - wb;
+        R.v[i] = r;
+        acc0 += r * r;
+    }
+    __device__ void load_tau(double& w, double& wt) const { w = *u.t; wt = *ut.t; }
+    __device__ void store_tau(double, double wt, double wb)
+    {
+        *ub.t = wb;
+        const double r = wt - wb;
+        *R.t = r;
+        acc0 += (T)(r * r);
+    }
+};
+
+// K0 (blind step): u <- u + d, u~ <- u~ + d~, then the residual of the new
+// point; secant pair z = d, xi = R_new - R_old; acc0 = ||R_new||^2, acc1 = ||d||^2
+template <typename T>
+struct OpK0 {
+    HV<T> u, ut, ub, Ru, d, dt, zp, xip;
+    T acc0, acc1;
+    __device__ void load(int i, T& w, T& wt) const { w = u.v[i] + d.v[i]; wt = ut.v[i] + dt.v[i]; }
+    __device__ void store(int i, T w, T wt, T wb)
+    {
+        const T di = d.v[i];
+        u.v[i] = w;
+        ut.v[i] = wt;
+        ub.v[i] = wb;
+        const T r = wt - wb;
+        xip.v[i] = r - Ru.v[i];
+        zp.v[i] = di;
+        Ru.v[i] = r;
+        acc0 += r * r;
+        acc1 += di * di;
+    }
+    __device__ void load_tau(double& w, double& wt) const { w = *u.t + *d.t; wt = *ut.t + *dt.t; }
+    __device__ void store_tau(double w, double wt, double wb)
+    {
+        const double di = *d.t;
+        *u.t = w;
+        *ut.t = wt;
+        *ub.t = wb;
+        const double r = wt - wb;
+        *xip.t = r - *Ru.t;
+        *zp.t = di;
+        *Ru.t = r;
+        acc0 += (T)(r * r);
+        acc1 += (T)(di * di);
+    }
+};
+
+// line-search trial at w = u + alpha d, w~ = u~ + alpha d~ (linearity trick,
+// Sec. 4.2): stores w_ and Rw; acc0 = ||Rw||^2, acc1 = <Rw, Rw - alpha d>
+template <typename T>
+struct OpTrial {
+    HV<T> u, ut, d, dt, wb, Rw;
+    double alpha;
+    T acc0, acc1;
+    __device__ void load(int i, T& w, T& wt) const
+    {
+        const T a = (T)alpha;
+        w = u.v[i] + a * d.v[i];
+        wt = ut.v[i] + a * dt.v[i];
+    }
+    __device__ void store(int i, T, T wt, T wbv)
+    {
+        wb.v[i] = wbv;
+        const T r = wt - wbv;
+        Rw.v[i] = r;
+        acc0 += r * r;
+        acc1 += r * (r - (T)alpha * d.v[i]);
+    }
+    __device__ void load_tau(double& w, double& wt) const
+    {
+        w = *u.t + alpha * *d.t;
+        wt = *ut.t + alpha * *dt.t;
+    }
+    __device__ void store_tau(double, double wt, double wbv)
+    {
+        *wb.t = wbv;
+        const double r = wt - wbv;
+        *Rw.t = r;
+        acc0 += (T)(r * r);
+        acc1 += (T)(r * (r - alpha * *d.t));
+    }
+};
+
+// plain projection: v -> Pi_C(v) (as w = -v, w~ = 0)
+template <typename T>
+struct OpProject {
+    const T* vin;
+    const double* tin;
+    T* out;
+    double* tout;
+    __device__ void load(int i, T& w, T& wt) const { w = -vin[i]; wt = 0; }
+    __device__ void store(int i, T, T, T wb) { out[i] = wb; }
+    __device__ void load_tau(double& w, double& wt) const { w = -*tin; wt = 0.0; }
+    __device__ void store_tau(double, double, double wb) { *tout = wb; }
+};
+
+// ---------------------------------------------------------------------------
+// elementwise helpers on HSDE vectors
+// ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// Termination (Sec. 4.3) on (u, u~, u_).  Returns a status (0 = continue).
+// Certificates use the reading ic = ||b|| ||A^T psi_|| / (-<b, psi_>) and
+// uc = ||c|| ||A chi_ + sigma_|| / (-<c, chi_>) on unscaled vectors.
+// ---------------------------------------------------------------------------
+struct TermOut {
+    double pr, dr, gap, ic, uc, pobj, dobj, bpsi, cchi;
+    bool time_up;
+};
+
+template <typename T, class Team>
+__device__ int termination(Team& tm, const DevProb<T>& P, const DevWork<T>& W, double eps, double deadline_ns,
+                           TermOut& o)
+{
+    const int n = P.n, m = P.m;
+    const T* chib = W.ub.v;
+    const T* psib = W.ub.v + n;
+    const T* psit = W.ut.v + n;
+    const T* psi = W.u.v + n;
+    const double taub = *W.ub.t;
+    T* tmv = W.tm;
+    T* tnv = W.tn;
+    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, chib, [&](int i, T s) { tmv[i] = s; });
+    spmv(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, psib, [&](int j, T s) { tnv[j] = s; });
+    tm.sync();
+    if (tm.leader()) W.st->mat_passes += 2;
+    const bool pos = taub > 0.0;
+    const T inv = pos ? (T)(1.0 / taub) : T(0);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    for (int i = tm.rank(); i < m; i += tm.size()) {
+        const T sig = psib[i] - T(2) * psit[i] + psi[i];
+        const T bi = ro(P.b + i);
+        if (pos) {
+            const T e = tmv[i] * inv + sig * inv - bi;
+            a0 += e * e;
+        }
+        const T f = tmv[i] + sig;
+        a4 += f * f;
+        a3 += bi * psib[i];
+    }
+    for (int j = tm.rank(); j < n; j += tm.size()) {
+        const T cj = ro(P.c + j);
+        if (pos) {
+            const T gq = tnv[j] * inv + cj;
+            a1 += gq * gq;
+        }
+        a2 += cj * chib[j];
+        a5 += tnv[j] * tnv[j];
+    }
+    double tflag = 0.0;
+    if (tm.leader() && deadline_ns > 0.0 && (double)gtimer() > deadline_ns) tflag = 1.0;
+    double red[7] = {(double)a0, (double)a1, (double)a2, (double)a3, (double)a4, (double)a5, tflag};
+    tm.reduce(red);
+    o.time_up = red[6] > 0.0;
+    o.cchi = red[2];
+    o.bpsi = red[3];
+    o.pr = o.dr = o.gap = INFINITY;
+    o.pobj = o.dobj = NAN;
+    int status = 0;
+    if (pos) {
+        o.pr = sqrt(red[0]) / (1.0 + P.nb);
+        o.dr = sqrt(red[1]) / (1.0 + P.nc);
+        const double cx = red[2] / taub, by = red[3] / taub;
+        o.gap = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
+        o.pobj = cx;
+        o.dobj = -by;
+        if (o.pr <= eps && o.dr <= eps && o.gap <= eps) status = ST_SOLVED;
+    }
+    o.ic = red[3] < 0.0 ? P.nb * sqrt(red[5]) / (-red[3]) : INFINITY;
+    o.uc = red[2] < 0.0 ? P.nc * sqrt(red[4]) / (-red[2]) : INFINITY;
+    if (!status) {
+        if (o.ic < eps) status = ST_INFEASIBLE;
+        else if (o.uc < eps) status = ST_UNBOUNDED;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// directions (Sec. 4.4)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ HV<T> col(T* base, double* tb, int k, int nm)
+{
+    return HV<T>{base + (size_t)k * nm, tb + k};
+}
+
+// small dense Cholesky solve by warp 0 of every block (k <= 32):
+// (G + reg I) t = rhs with reg raised tenfold up to 8 times; false on failure
+static __device__ bool small_chol(const double* G, const double* rhs, double* L, double* t, int k, double reg0)
+{
+    __shared__ int ok_s;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        bool ok = false;
+        double reg = reg0;
+        for (int attempt = 0; attempt < 8 && !ok; ++attempt, reg *= 10.0) {
+            ok = true;
+            for (int j = 0; j < k; ++j) {
+                double s = (lane < j) ? L[j * AAMAX + lane] * L[j * AAMAX + lane] : 0.0;
+                s = warp_sum(s);
+                const double dj = G[j * AAMAX + j] + reg - s;
+                if (!(dj > 0.0)) {
+                    ok = false;
+                    break;
+                }
+                const double ljj = sqrt(dj);
+                if (lane > j && lane < k) {
+                    double e = G[lane * AAMAX + j];
+                    for (int p = 0; p < j; ++p) e -= L[lane * AAMAX + p] * L[j * AAMAX + p];
+                    L[lane * AAMAX + j] = e / ljj;
+                }
+                if (lane == 0) L[j * AAMAX + j] = ljj;
+                __syncwarp();
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (ok) {
+                for (int i = 0; i < k; ++i) {
+                    double e = rhs[i];
+                    for (int p = 0; p < i; ++p) e -= L[i * AAMAX + p] * t[p];
+                    t[i] = e / L[i * AAMAX + i];
+                }
+                for (int i = k - 1; i >= 0; --i) {
+                    double e = t[i];
+                    for (int p = i + 1; p < k; ++p) e -= L[p * AAMAX + i] * t[p];
+                    t[i] = e / L[i * AAMAX + i];
+                }
+            }
+            ok_s = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct DirState {
+    int count;     // stored pairs
+    long long inserted;
+};
+
+// Anderson's acceleration: d = -Ru - (Z - Xi) t, t = argmin ||Xi t - Ru|| by
+// regularised normal equations; ring buffer of the last mem pairs.
+template <typename T, class Team>
+__device__ void aa_direction(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S,
+                             bool have_pair, double nz2, DirState& ds, double* G, double* sm_rhs, double* sm_L,
+                             double* sm_t)
+{
+    const int nm = P.n + P.m;
+    const int mem = S.mem;
+    if (have_pair && mem > 0 && nz2 > 0.0) {
+        const int slot = (int)(ds.inserted % mem);
+        HV<T> Zs = col(W.Zv, W.Zt, slot, nm), Xs = col(W.Xv, W.Xt, slot, nm);
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            Zs.v[i] = W.zp.v[i];
+            Xs.v[i] = W.xip.v[i];
+        }
+        if (tm.leader()) {
+            *Zs.t = *W.zp.t;
+            *Xs.t = *W.xip.t;
+        }
+        ds.inserted++;
+        if (ds.count < mem) ds.count++;
+        tm.sync();
+        // new Gram row: <xi_slot, xi_j> for all stored j, in chunks of 8
+        for (int j0 = 0; j0 < ds.count; j0 += 8) {
+            T a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = 0;
+            for (int i = tm.rank(); i < nm; i += tm.size()) {
+                const T xs = Xs.v[i];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (j0 + q < ds.count) a[q] += xs * W.Xv[(size_t)(j0 + q) * nm + i];
+            }
+            double red[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[q] = (double)a[q];
+            if (tm.leader()) {
+                const double xt = *Xs.t;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (j0 + q < ds.count) red[q] += xt * W.Xt[j0 + q];
+            }
+            tm.reduce(red);
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < 8 && j0 + q < ds.count; ++q) {
+                    G[slot * AAMAX + j0 + q] = red[q];
+                    G[(j0 + q) * AAMAX + slot] = red[q];
+                }
+            }
+        }
+    }
+    const int k = ds.count;
+    if (k == 0) {
+        for (int i = tm.rank(); i < nm; i += tm.size()) W.d.v[i] = -W.Ru.v[i];
+        if (tm.leader()) *W.d.t = -*W.Ru.t;
+        tm.sync();
+        return;
+    }
+    // rhs_j = <xi_j, Ru>
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        T a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = 0;
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            const T r = W.Ru.v[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < k) a[q] += r * W.Xv[(size_t)(j0 + q) * nm + i];
+        }
+        double red[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[q] = (double)a[q];
+        if (tm.leader()) {
+            const double rt = *W.Ru.t;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < k) red[q] += rt * W.Xt[j0 + q];
+        }
+        tm.reduce(red);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 8 && j0 + q < k; ++q) sm_rhs[j0 + q] = red[q];
+    }
+    __syncthreads();
+    double tr = 0.0;
+    for (int j = 0; j < k; ++j) tr += G[j * AAMAX + j];
+    bool ok = false;
+    if (tr > 0.0) ok = small_chol(G, sm_rhs, sm_L, sm_t, k, S.aa_reg * tr / k);
+    // d = -Ru - sum_j t_j (Z_j - Xi_j)
+    for (int i = tm.rank(); i < nm; i += tm.size()) {
+        T di = -W.Ru.v[i];
+        if (ok)
+            for (int j = 0; j < k; ++j) di -= (T)sm_t[j] * (W.Zv[(size_t)j * nm + i] - W.Xv[(size_t)j * nm + i]);
+        W.d.v[i] = di;
+    }
+    if (tm.leader()) {
+        double di = -*W.Ru.t;
+        if (ok)
+            for (int j = 0; j < k; ++j) di -= sm_t[j] * (W.Zt[j] - W.Xt[j]);
+        *W.d.t = di;
+    }
+    tm.sync();
+}
+
+// Restarted Broyden, Algorithm 2 (readings: m' = stored pairs; restart when
+// m' = mem empties the buffers without storing the current pair; the
+// denominator of z~ is <z, H xi~>; sgn(0) = 1).
+template <typename T, class Team>
+__device__ void rb_direction(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S,
+                             bool have_pair, double nz2, DirState& ds)
+{
+    const int nm = P.n + P.m;
+    HV<T> d = W.d, zt = W.zt, Ru = W.Ru, z = W.zp, xi = W.xip;
+    if (!have_pair || !(nz2 > 0.0)) {
+        for (int i = tm.rank(); i < nm; i += tm.size()) d.v[i] = -Ru.v[i];
+        if (tm.leader()) *d.t = -*Ru.t;
+        tm.sync();
+        return;
+    }
+    const int cnt = ds.count;
+    // pass 0: d = -Ru, zt = xi; dots with the first stored z (or with z when none)
+    {
+        const T* z0 = cnt > 0 ? W.Zv : z.v;
+        const double z0t = cnt > 0 ? W.Zt[0] : *z.t;
+        T a = 0, b = 0;
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            const T di = -Ru.v[i], zi = xi.v[i];
+            d.v[i] = di;
+            zt.v[i] = zi;
+            a += z0[i] * zi;
+            b += z0[i] * di;
+        }
+        double red[2] = {(double)a, (double)b};
+        if (tm.leader()) {
+            *d.t = -*Ru.t;
+            *zt.t = *xi.t;
+            red[0] += z0t * *xi.t;
+            red[1] += z0t * (-*Ru.t);
+        }
+        tm.reduce(red);
+        double ca = red[0], cb = red[1];
+        // stored pairs: zt += <z^k, zt> z~^k ; d += <z^k, d> z~^k, dots for the next pair fused
+        for (int k = 0; k < cnt; ++k) {
+            const T* zk1 = (k + 1 < cnt) ? W.Zv + (size_t)(k + 1) * nm : z.v;
+            const double zk1t = (k + 1 < cnt) ? W.Zt[k + 1] : *z.t;
+            const T* ztk = W.Xv + (size_t)k * nm;
+            const T ta = (T)ca, tb = (T)cb;
+            T a2 = 0, b2 = 0;
+            for (int i = tm.rank(); i < nm; i += tm.size()) {
+                const T zti = zt.v[i] + ta * ztk[i];
+                const T di = d.v[i] + tb * ztk[i];
+                zt.v[i] = zti;
+                d.v[i] = di;
+                a2 += zk1[i] * zti;
+                b2 += zk1[i] * di;
+            }
+            double red2[2] = {(double)a2, (double)b2};
+            if (tm.leader()) {
+                const double zti = *zt.t + ca * W.Xt[k];
+                const double di = *d.t + cb * W.Xt[k];
+                *zt.t = zti;
+                *d.t = di;
+                red2[0] += zk1t * zti;
+                red2[1] += zk1t * di;
+            }
+            tm.reduce(red2);
+            ca = red2[0];
+            cb = red2[1];
+        }
+        // now ca = <z, H xi>, cb = <z, H(-r)>
+        const double gamma = ca / nz2;
+        const double sg = gamma >= 0.0 ? 1.0 : -1.0;
+        const double theta = fabs(gamma) >= S.thetabar ? 1.0 : (1.0 - sg * S.thetabar) / (1.0 - gamma);
+        // z~ = (z - ((1-theta) z + theta H xi)) / <z, (1-theta) z + theta H xi>
+        const double den = (1.0 - theta) * nz2 + theta * ca;
+        const bool store = cnt < S.mem;
+        T* ztn = W.Xv + (size_t)cnt * nm;  // used only when storing
+        T* zsn = W.Zv + (size_t)cnt * nm;
+        const T f1 = (T)(theta / den);
+        const T tcb = (T)cb;
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            const T zi = z.v[i];
+            const T zn = f1 * (zi - zt.v[i]);
+            d.v[i] += tcb * zn;
+            if (store) {
+                ztn[i] = zn;
+                zsn[i] = zi;
+            }
+        }
+        if (tm.leader()) {
+            const double zi = *z.t;
+            const double zn = (theta / den) * (zi - *zt.t);
+            *d.t += cb * zn;
+            if (store) {
+                W.Xt[cnt] = zn;
+                W.Zt[cnt] = zi;
+            }
+        }
+        tm.sync();
+        ds.count = store ? cnt + 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// outputs (Sec. 3.1 recovery rules)
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ void write_outputs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, int status, const TermOut& o)
+{
+    const int n = P.n, m = P.m;
+    const double taub = *W.ub.t;
+    const T* chib = W.ub.v;
+    const T* psib = W.ub.v + n;
+    for (int i = tm.rank(); i < m; i += tm.size()) {
+        const double sig = (double)psib[i] - 2.0 * (double)W.ut.v[n + i] + (double)W.u.v[n + i];
+        double yv, sv;
+        if (status == ST_INFEASIBLE) {
+            yv = (double)psib[i] / (-o.bpsi);
+            sv = NAN;
+        } else if (status == ST_UNBOUNDED) {
+            yv = NAN;
+            sv = sig / (-o.cchi);
+        } else if (taub > 0.0) {
+            yv = (double)psib[i] / taub;
+            sv = sig / taub;
+        } else {
+            yv = NAN;
+            sv = NAN;
+        }
+        W.y_out[i] = yv;
+        W.s_out[i] = sv;
+    }
+    for (int j = tm.rank(); j < n; j += tm.size()) {
+        double xv;
+        if (status == ST_INFEASIBLE) xv = NAN;
+        else if (status == ST_UNBOUNDED) xv = (double)chib[j] / (-o.cchi);
+        else if (taub > 0.0) xv = (double)chib[j] / taub;
+        else xv = NAN;
+        W.x_out[j] = xv;
+    }
+    for (int i = tm.rank(); i < n + m; i += tm.size()) W.u_out[i] = (double)W.u.v[i];
+    if (tm.leader()) W.u_out[n + m] = *W.u.t;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 with the linearity trick (Sec. 4.2).  Readings where the paper
+// is silent: u0 = (0,0,1) unless warm; q^nu with nu the outer index; at most
+// ls_max halvings, then alpha = 0 (the KM step); ||Rw|| = 0 is accepted as
+// K1; secant pair z = w - u, xi = Rw - Ru of the last evaluated w; after K2
+// the new u~ is solved from the new u; termination before the direction.
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, double* G,
+                         double* sm_rhs, double* sm_L, double* sm_t, unsigned char* psd)
+{
+    const int n = P.n, m = P.m, nm = n + m;
+    const double hg = W.st->hg;
+    long long cg_total = 0;
+    int k0 = 0, k1 = 0, k2 = 0, bt = 0;
+    const double deadline = S.time_limit_ns > 0.0 ? (double)gtimer() + S.time_limit_ns : 0.0;
+    // u0
+    for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = S.use_warm ? (T)W.warm[i] : T(0);
+    if (tm.leader()) *W.u.t = S.use_warm ? W.warm[nm] : 1.0;
+    tm.sync();
+    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+    double nRu;
+    {
+        OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
+        project_pass(tm, P, op, psd);
+        double red[1] = {(double)op.acc0};
+        tm.reduce(red);
+        nRu = sqrt(red[0]);
+    }
+    const double eta0 = nRu;
+    double r_safe = eta0, eta = eta0, nz2 = 0.0;
+    bool have_pair = false;
+    DirState ds{0, 0};
+    int status = ST_MAX_ITERS;
+    TermOut to;
+    to.pr = to.dr = to.gap = to.ic = to.uc = INFINITY;
+    to.pobj = to.dobj = NAN;
+    to.bpsi = to.cchi = 0.0;
+    double best_kkt = INFINITY;
+    int best_it = 0;
+    const int check_every = S.check_every > 0 ? S.check_every : 1;
+    bool need_final_check = true;
+    int nu;
+    for (nu = 0; nu < S.max_iters; ++nu) {
+        if (tm.aborted()) break;
+        if (!isfinite(nRu)) {
+            status = ST_NUMERICAL;
+            break;
+        }
+        if (nu % check_every == 0) {
+            const int st = termination(tm, P, W, S.eps, deadline, to);
+            if (st != 0) {
+                status = st;
+                need_final_check = false;
+                break;
+            }
+            if (to.time_up) {
+                status = ST_TIME_LIMIT;
+                need_final_check = false;
+                break;
+            }
+            if (S.stall_iters > 0) {
+                const double kkt = fmax(to.pr, fmax(to.dr, to.gap));
+                if (kkt < 0.9 * best_kkt) {
+                    best_kkt = kkt;
+                    best_it = nu;
+                } else if (nu - best_it >= S.stall_iters) {
+                    status = ST_STALLED;
+                    need_final_check = false;
+                    break;
+                }
+            }
+        }
+        // direction d (Sec. 4.4)
+        if (S.direction == 0)
+            aa_direction(tm, P, W, S, have_pair, nz2, ds, G, sm_rhs, sm_L, sm_t);
+        else if (S.direction == 1)
+            rb_direction(tm, P, W, S, have_pair, nz2, ds);
+        else {
+            for (int i = tm.rank(); i < nm; i += tm.size()) W.d.v[i] = T(0);
+            if (tm.leader()) *W.d.t = 0.0;
+            tm.sync();
+        }
+        cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg);
+        if (nRu <= S.c0 * eta) {
+            // K0
+            eta = nRu;
+            OpK0<T> op{W.u, W.ut, W.ub, W.Ru, W.d, W.dt, W.zp, W.xip, T(0), T(0)};
+            project_pass(tm, P, op, psd);
+            double red[2] = {(double)op.acc0, (double)op.acc1};
+            tm.reduce(red);
+            nRu = sqrt(red[0]);
+            nz2 = red[1];
+            ++k0;
+        } else {
+            double alpha = 1.0;
+            for (int ls = 0; ls <= S.ls_max; ++ls) {
+                if (ls == S.ls_max) alpha = 0.0;
+                OpTrial<T> op{W.u, W.ut, W.d, W.dt, W.wb, W.Rw, alpha, T(0), T(0)};
+                project_pass(tm, P, op, psd);
+                double red[2] = {(double)op.acc0, (double)op.acc1};
+                tm.reduce(red);
+                const double nRw = sqrt(red[0]);
+                const double rho = red[1];
+                if ((nRu <= r_safe && nRw <= S.c1 * nRu) || nRw == 0.0) {
+                    // K1: u <- w, reuse w~, w_, Rw
+                    r_safe = nRw + pow(S.q, (double)nu) * eta0;
+                    const T ta = (T)alpha;
+                    T zz = 0;
+                    for (int i = tm.rank(); i < nm; i += tm.size()) {
+                        const T di = ta * W.d.v[i];
+                        W.u.v[i] += di;
+                        W.ut.v[i] += ta * W.dt.v[i];
+                        W.ub.v[i] = W.wb.v[i];
+                        W.zp.v[i] = di;
+                        W.xip.v[i] = W.Rw.v[i] - W.Ru.v[i];
+                        W.Ru.v[i] = W.Rw.v[i];
+                        zz += di * di;
+                    }
+                    double red2[1] = {(double)zz};
+                    if (tm.leader()) {
+                        const double di = alpha * *W.d.t;
+                        *W.u.t += di;
+                        *W.ut.t += alpha * *W.dt.t;
+                        *W.ub.t = *W.wb.t;
+                        *W.zp.t = di;
+                        *W.xip.t = *W.Rw.t - *W.Ru.t;
+                        *W.Ru.t = *W.Rw.t;
+                        red2[0] += di * di;
+                    }
+                    tm.reduce(red2);
+                    nz2 = red2[0];
+                    nRu = nRw;
+                    ++k1;
+                    break;
+                } else if (rho >= S.sigma * nRu * nRw) {
+                    // K2: u <- u - lambda rho / ||Rw||^2 Rw, then a fresh u~ solve
+                    const double coef = S.lambda * rho / (nRw * nRw);
+                    const T ta = (T)alpha, tc = (T)coef;
+                    T zz = 0;
+                    for (int i = tm.rank(); i < nm; i += tm.size()) {
+                        const T di = ta * W.d.v[i];
+                        W.zp.v[i] = di;
+                        W.xip.v[i] = W.Rw.v[i] - W.Ru.v[i];
+                        W.u.v[i] -= tc * W.Rw.v[i];
+                        zz += di * di;
+                    }
+                    double red2[1] = {(double)zz};
+                    if (tm.leader()) {
+                        const double di = alpha * *W.d.t;
+                        *W.zp.t = di;
+                        *W.xip.t = *W.Rw.t - *W.Ru.t;
+                        *W.u.t -= coef * *W.Rw.t;
+                        red2[0] += di * di;
+                    }
+                    tm.reduce(red2);
+                    nz2 = red2[0];
+                    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+                    OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
+                    project_pass(tm, P, opr, psd);
+                    double red3[1] = {(double)opr.acc0};
+                    tm.reduce(red3);
+                    nRu = sqrt(red3[0]);
+                    ++k2;
+                    break;
+                }
+                alpha *= 0.5;
+                ++bt;
+            }
+        }
+        have_pair = true;
+    }
+    if (need_final_check && !tm.aborted()) {
+        const int st = termination(tm, P, W, S.eps, 0.0, to);
+        if (st != 0 && status != ST_NUMERICAL) status = st;
+    }
+    write_outputs(tm, P, W, status, to);
+    if (tm.leader()) {
+        DevState* st = W.st;
+        st->status = status;
+        st->iters = nu;
+        st->k0 = k0;
+        st->k1 = k1;
+        st->k2 = k2;
+        st->backtracks = bt;
+        st->cg_iters = cg_total;
+        st->pr = to.pr;
+        st->dr = to.dr;
+        st->gap = to.gap;
+        st->ic = to.ic;
+        st->uc = to.uc;
+        st->nRu = nRu;
+        if (status == ST_SOLVED || status == ST_MAX_ITERS || status == ST_TIME_LIMIT || status == ST_STALLED) {
+            st->pobj = to.pobj;
+            st->dobj = to.dobj;
+        } else {
+            st->pobj = NAN;
+            st->dobj = NAN;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one entry for every mode
+// ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, double* sm_L, double* sm_t,
+                         unsigned char* psd)
+{
+    const DevProb<T>& P = a.P;
+    const DevWork<T>& W = a.W;
+    const int n = P.n, m = P.m, nm = n + m;
+    if (a.mode == MODE_SETUP) {
+        // g = M^{-1}(c, b) from a zero start; ws[0] is zero on entry and left zero
+        T* x = W.ws[0];
+        double htp;
+        const int it = minv(tm, P, W, P.c, P.b, x, a.S.cg_rtol, a.S.cg_max, htp);
+        for (int i = tm.rank(); i < n; i += tm.size()) {
+            W.g[i] = x[i];
+            x[i] = T(0);
+        }
+        for (int i = tm.rank(); i < m; i += tm.size()) W.g[n + i] = W.py[i];
+        if (tm.leader()) {
+            W.st->hg = htp;
+            W.st->setup_cg = it;
+        }
+        tm.sync();
+        return;
+    }
+    if (a.mode == MODE_SOLVE) {
+        superscs(tm, P, W, a.S, G, sm_rhs, sm_L, sm_t, psd);
+        return;
+    }
+    // single operators: io_in (FP64, N) -> u (T), results to io_out / io_out2
+    for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = (T)W.io_in[i];
+    if (tm.leader()) *W.u.t = W.io_in[nm];
+    tm.sync();
+    if (a.mode == MODE_LINSYS) {
+        linsys(tm, P, W, W.u, W.ut, a.slot, a.S.cg_rtol, a.S.cg_max, W.st->hg);
+        for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ut.v[i];
+        if (tm.leader()) W.io_out[nm] = *W.ut.t;
+    } else if (a.mode == MODE_PROJECT) {
+        OpProject<T> op{W.u.v, W.u.t, W.ub.v, W.ub.t};
+        project_pass(tm, P, op, psd);
+        tm.sync();
+        for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ub.v[i];
+        if (tm.leader()) W.io_out[nm] = *W.ub.t;
+    } else if (a.mode == MODE_APPLY_T) {
+        linsys(tm, P, W, W.u, W.ut, 0, a.S.cg_rtol, a.S.cg_max, W.st->hg);
+        OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
+        project_pass(tm, P, op, psd);
+        tm.sync();
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            W.io_out[i] = (double)W.u.v[i] - (double)W.Ru.v[i];
+            W.io_out2[i] = (double)W.Ru.v[i];
+        }
+        if (tm.leader()) {
+            W.io_out[nm] = *W.u.t - *W.Ru.t;
+            W.io_out2[nm] = *W.Ru.t;
+        }
+    }
+    tm.sync();
+}
+
+}  // namespace sscs

@@ -1,0 +1,947 @@
+// superscs.cu -- host side of the C ABI declared in include/superscs.h:
+// validation, the CSR transpose of A built once at setup, one device arena
+// per problem (or per batch), and the launches of the device-resident solver.
+//
+// Launch shapes
+//   GridTeam : one cooperative launch of (SMs x resident blocks) CTAs that
+//              runs the whole of Algorithm 1 for one large instance.
+//   BlockTeam: persistent CTAs that take instances from an atomic queue
+//              (largest first) and run Algorithm 1 on each.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/superscs.h"
+#include "solver.cuh"
+
+using namespace sscs;
+
+#include "launch.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static void set_err(char* dst, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    if (dst != g_err) memcpy(g_err, dst, 512);
+}
+
+#define CU(call, errbuf)                                                                                    \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) {                                                                            \
+            set_err(errbuf, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
+            return SCS_ECUDA;                                                                               \
+        }                                                                                                   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// host problem preparation
+// ---------------------------------------------------------------------------
+struct HostProb {
+    int n = 0, m = 0;
+    long long nnz = 0;
+    std::vector<int> Ap, Ai, Tp, Ti;
+    std::vector<double> Ax, Tx, b, c;
+    int f = 0, l = 0;
+    std::vector<int> q, s, q_off, s_off;
+    double nb = 0, nc = 0;
+    int vecA = 32, vecT = 32;
+};
+
+static int pick_vec(long long nnz, int rows)
+{
+    const double avg = rows > 0 ? (double)nnz / rows : 0.0;
+    int v = 1;
+    while (v < 32 && v < avg / 2.0) v <<= 1;
+    return v;
+}
+
+static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err)
+{
+    if (!d || !k) { set_err(err, "data and cone must not be NULL"); return SCS_EINVAL; }
+    if (d->m <= 0 || d->n <= 0) { set_err(err, "m and n must be positive (m=%d n=%d)", d->m, d->n); return SCS_EINVAL; }
+    if (!d->Ap || !d->Ai || !d->Ax || !d->b || !d->c) { set_err(err, "data arrays must not be NULL"); return SCS_EINVAL; }
+    const int m = d->m, n = d->n;
+    if (d->Ap[0] != 0) { set_err(err, "Ap[0] must be 0"); return SCS_EINVAL; }
+    for (int i = 0; i < m; ++i)
+        if (d->Ap[i + 1] < d->Ap[i]) { set_err(err, "Ap is not nondecreasing at row %d", i); return SCS_EINVAL; }
+    const long long nnz = d->Ap[m];
+    if (nnz >= (1ll << 31)) { set_err(err, "nnz = %lld is not below 2^31", nnz); return SCS_EINVAL; }
+    if (k->f < 0 || k->l < 0 || k->nq < 0 || k->ns < 0) { set_err(err, "negative cone counts"); return SCS_EINVAL; }
+    if ((k->nq > 0 && !k->q) || (k->ns > 0 && !k->s)) { set_err(err, "cone arrays must not be NULL"); return SCS_EINVAL; }
+    long long rows = (long long)k->f + k->l;
+    H.q_off.assign(1, 0);
+    for (int i = 0; i < k->nq; ++i) {
+        if (k->q[i] < 1) { set_err(err, "SOC %d has dimension %d < 1", i, k->q[i]); return SCS_EINVAL; }
+        H.q.push_back(k->q[i]);
+    }
+    for (int i = 0; i < k->ns; ++i) {
+        if (k->s[i] < 1 || k->s[i] > PSD_MAX) {
+            set_err(err, "PSD block %d has order %d outside 1..%d", i, k->s[i], PSD_MAX);
+            return SCS_EINVAL;
+        }
+        H.s.push_back(k->s[i]);
+    }
+    long long o = (long long)k->f + k->l;
+    for (int i = 0; i < k->nq; ++i) { o += k->q[i]; }
+    for (int i = 0; i < k->ns; ++i) { o += (long long)k->s[i] * (k->s[i] + 1) / 2; }
+    rows = o;
+    if (rows != m) { set_err(err, "cone rows (%lld) do not sum to m (%d)", rows, m); return SCS_EINVAL; }
+    H.n = n;
+    H.m = m;
+    H.nnz = nnz;
+    H.f = k->f;
+    H.l = k->l;
+    long long qo = (long long)k->f + k->l;
+    for (int i = 0; i < k->nq; ++i) { H.q_off.push_back(0); }
+    H.q_off[0] = (int)qo;
+    for (int i = 0; i < k->nq; ++i) H.q_off[i + 1] = H.q_off[i] + k->q[i];
+    long long so = qo;
+    for (int i = 0; i < k->nq; ++i) so += k->q[i];
+    for (int i = 0; i < k->ns; ++i) {
+        H.s_off.push_back((int)so);
+        so += (long long)k->s[i] * (k->s[i] + 1) / 2;
+    }
+    H.Ap.resize(m + 1);
+    for (int i = 0; i <= m; ++i) H.Ap[i] = (int)d->Ap[i];
+    H.Ai.assign(d->Ai, d->Ai + nnz);
+    H.Ax.assign(d->Ax, d->Ax + nnz);
+    for (long long e = 0; e < nnz; ++e) {
+        if (H.Ai[e] < 0 || H.Ai[e] >= n) { set_err(err, "column index %d out of range at %lld", H.Ai[e], e); return SCS_EINVAL; }
+        if (!std::isfinite(H.Ax[e])) { set_err(err, "non-finite A value at %lld", e); return SCS_EINVAL; }
+    }
+    H.b.assign(d->b, d->b + m);
+    H.c.assign(d->c, d->c + n);
+    for (int i = 0; i < m; ++i)
+        if (!std::isfinite(H.b[i])) { set_err(err, "non-finite b[%d]", i); return SCS_EINVAL; }
+    for (int j = 0; j < n; ++j)
+        if (!std::isfinite(H.c[j])) { set_err(err, "non-finite c[%d]", j); return SCS_EINVAL; }
+    // CSR of A^T: counting sort by column, rows ascending inside each column
+    H.Tp.assign(n + 1, 0);
+    for (long long e = 0; e < nnz; ++e) H.Tp[H.Ai[e] + 1]++;
+    for (int j = 0; j < n; ++j) H.Tp[j + 1] += H.Tp[j];
+    H.Ti.resize(nnz);
+    H.Tx.resize(nnz);
+    std::vector<int> pos(H.Tp.begin(), H.Tp.end() - 1);
+    for (int i = 0; i < m; ++i)
+        for (int e = H.Ap[i]; e < H.Ap[i + 1]; ++e) {
+            const int j = H.Ai[e];
+            H.Ti[pos[j]] = i;
+            H.Tx[pos[j]] = H.Ax[e];
+            pos[j]++;
+        }
+    double s = 0;
+    for (int i = 0; i < m; ++i) s += H.b[i] * H.b[i];
+    H.nb = std::sqrt(s);
+    s = 0;
+    for (int j = 0; j < n; ++j) s += H.c[j] * H.c[j];
+    H.nc = std::sqrt(s);
+    H.vecA = pick_vec(nnz, m);
+    H.vecT = pick_vec(nnz, n);
+    return SCS_OK;
+}
+
+static int check_settings(const scs_settings* S, char* err)
+{
+    if (!S) { set_err(err, "settings must not be NULL"); return SCS_EINVAL; }
+    if (S->direction < 0 || S->direction > 2) { set_err(err, "bad direction %d", S->direction); return SCS_EINVAL; }
+    if (S->direction == SCS_DIR_AA && (S->mem < 0 || S->mem > AAMAX)) { set_err(err, "AA mem must be in 0..%d", AAMAX); return SCS_EINVAL; }
+    if (S->direction == SCS_DIR_RB && (S->mem < 0 || S->mem > MAXMEM)) { set_err(err, "RB mem must be in 0..%d", MAXMEM); return SCS_EINVAL; }
+    if (!(S->eps > 0) || S->max_iters < 0 || S->ls_max < 0 || S->cg_max < 0) { set_err(err, "bad tolerances or caps"); return SCS_EINVAL; }
+    if (!(S->lambda > 0 && S->lambda < 2)) { set_err(err, "lambda must lie in (0,2)"); return SCS_EINVAL; }
+    if (!(S->sigma > 0 && S->sigma < 1)) { set_err(err, "sigma must lie in (0,1)"); return SCS_EINVAL; }
+    if (S->precision != SCS_FP64 && S->precision != SCS_MIXED) { set_err(err, "bad precision"); return SCS_EINVAL; }
+    if (S->threads != 0 && (S->threads < 32 || S->threads > 1024 || S->threads % 32)) { set_err(err, "threads must be a multiple of 32 in 32..1024"); return SCS_EINVAL; }
+    return SCS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device arena
+// ---------------------------------------------------------------------------
+struct Arena {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename X>
+    X* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        X* p = (X*)(base + off);
+        off += sizeof(X) * std::max<size_t>(count, 1);
+        return p;
+    }
+};
+
+// layout of one instance's data and work in precision T; base == nullptr only measures
+template <typename T>
+static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevProb<T>& P, DevWork<T>& W,
+                    const int* shared_idx /* Ap,Ai,Tp,Ti,q_off,s_dim,s_off from another precision or null */)
+{
+    const int n = H.n, m = H.m, nm = n + m;
+    const long long nnz = H.nnz;
+    P.n = n;
+    P.m = m;
+    if (shared_idx == nullptr) {
+        P.Ap = A.take<int>(m + 1);
+        P.Ai = A.take<int>(nnz);
+        P.Tp = A.take<int>(n + 1);
+        P.Ti = A.take<int>(nnz);
+        P.q_off = A.take<int>(H.q_off.size());
+        P.s_dim = A.take<int>(H.s.size());
+        P.s_off = A.take<int>(H.s_off.size());
+    }
+    P.Ax = A.take<T>(nnz);
+    P.Tx = A.take<T>(nnz);
+    P.b = A.take<T>(m);
+    P.c = A.take<T>(n);
+    P.nb = H.nb;
+    P.nc = H.nc;
+    P.f = H.f;
+    P.l = H.l;
+    P.nq = (int)H.q.size();
+    P.ns = (int)H.s.size();
+    P.vecA = H.vecA;
+    P.vecT = H.vecT;
+    double* taus = A.take<double>(16);
+    HV<T>* hvs[] = {&W.u, &W.ut, &W.ub, &W.Ru, &W.d, &W.dt, &W.wb, &W.Rw, &W.zp, &W.xip, &W.zt};
+    for (int i = 0; i < 11; ++i) {
+        hvs[i]->v = A.take<T>(nm);
+        hvs[i]->t = taus + i;
+    }
+    W.g = A.take<T>(nm);
+    W.ws[0] = A.take<T>(n);
+    W.ws[1] = A.take<T>(n);
+    W.cr = A.take<T>(n);
+    W.cp = A.take<T>(n);
+    W.cq = A.take<T>(n);
+    W.tn = A.take<T>(n);
+    W.tm = A.take<T>(m);
+    W.py = A.take<T>(m);
+    const int mm = std::max(mem, 1);
+    W.Zv = A.take<T>((size_t)mm * nm);
+    W.Xv = A.take<T>((size_t)mm * nm);
+    W.Zt = A.take<double>(mm);
+    W.Xt = A.take<double>(mm);
+    W.io_in = A.take<double>(nm + 1);
+    W.io_out = A.take<double>(nm + 1);
+    W.io_out2 = A.take<double>(nm + 1);
+    W.warm = A.take<double>(nm + 1);
+    W.x_out = A.take<double>(n);
+    W.y_out = A.take<double>(m);
+    W.s_out = A.take<double>(m);
+    W.u_out = A.take<double>(nm + 1);
+    W.partials = A.take<double>((size_t)2 * KMAX * std::max(max_blocks, 1));
+    W.bar = A.take<unsigned>(4);
+    W.abort_flag = A.take<int>(4);
+    W.st = A.take<DevState>(1);
+}
+
+template <typename T>
+static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t st, char* err)
+{
+    if (idx) {
+        CU(cudaMemcpyAsync((void*)P.Ap, H.Ap.data(), sizeof(int) * H.Ap.size(), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.Ai, H.Ai.data(), sizeof(int) * H.Ai.size(), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.Tp, H.Tp.data(), sizeof(int) * H.Tp.size(), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.Ti, H.Ti.data(), sizeof(int) * H.Ti.size(), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.q_off, H.q_off.data(), sizeof(int) * H.q_off.size(), cudaMemcpyHostToDevice, st), err);
+        if (!H.s.empty()) {
+            CU(cudaMemcpyAsync((void*)P.s_dim, H.s.data(), sizeof(int) * H.s.size(), cudaMemcpyHostToDevice, st), err);
+            CU(cudaMemcpyAsync((void*)P.s_off, H.s_off.data(), sizeof(int) * H.s_off.size(), cudaMemcpyHostToDevice, st), err);
+        }
+    }
+    if (sizeof(T) == sizeof(double)) {
+        CU(cudaMemcpyAsync((void*)P.Ax, H.Ax.data(), sizeof(double) * H.nnz, cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.Tx, H.Tx.data(), sizeof(double) * H.nnz, cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.b, H.b.data(), sizeof(double) * H.m, cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync((void*)P.c, H.c.data(), sizeof(double) * H.n, cudaMemcpyHostToDevice, st), err);
+    } else {
+        std::vector<float> tmp;
+        auto put = [&](const std::vector<double>& v, const T* dst) -> int {
+            tmp.resize(v.size());
+            for (size_t i = 0; i < v.size(); ++i) tmp[i] = (float)v[i];
+            CU(cudaMemcpyAsync((void*)dst, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice, st), err);
+            CU(cudaStreamSynchronize(st), err);  // tmp is reused
+            return SCS_OK;
+        };
+        int rc;
+        if ((rc = put(H.Ax, P.Ax)) || (rc = put(H.Tx, P.Tx)) || (rc = put(H.b, P.b)) || (rc = put(H.c, P.c))) return rc;
+    }
+    return SCS_OK;
+}
+
+static DevSettings dev_settings(const scs_settings* S)
+{
+    DevSettings D;
+    D.direction = S->direction;
+    D.mem = S->mem;
+    D.eps = S->eps;
+    D.c0 = S->c0;
+    D.c1 = S->c1;
+    D.q = S->q;
+    D.sigma = S->sigma;
+    D.lambda = S->lambda;
+    D.thetabar = S->thetabar;
+    D.max_iters = S->max_iters;
+    D.ls_max = S->ls_max;
+    D.cg_max = S->cg_max;
+    D.check_every = S->check_every;
+    D.cg_rtol = S->cg_rtol;
+    D.aa_reg = S->aa_reg;
+    D.time_limit_ns = S->time_limit_s > 0 ? S->time_limit_s * 1e9 : 0.0;
+    D.stall_iters = 0;
+    D.use_warm = 0;
+    return D;
+}
+
+struct DevInfo {
+    int team = SCS_TEAM_GRID;
+    int threads = 512;
+    int grid = 0;
+    int sms = 0;
+    size_t dyn64 = 0, dyn32 = 0;
+};
+
+template <typename T>
+static size_t dyn_smem(const HostProb& H)
+{
+    return H.s.empty() ? 0 : psd_smem_bytes<T>();
+}
+
+template <typename T>
+static int config_kernels(size_t dyn, char* err)
+{
+    if (dyn > 48 * 1024) {
+        CU(cudaFuncSetAttribute(kgrid_ptr<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn), err);
+        CU(cudaFuncSetAttribute(kblock_ptr<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn), err);
+    }
+    return SCS_OK;
+}
+
+template <typename T>
+static int launch(int team, int threads, int grid, size_t dyn, const Args<T>& a, Args<T>* dev_args, int* queue,
+                  cudaStream_t st, char* err)
+{
+    if (team == SCS_TEAM_GRID) {
+        CU(cudaMemsetAsync(a.W.bar, 0, 4 * sizeof(unsigned), st), err);
+        CU(cudaMemsetAsync(a.W.abort_flag, 0, 4 * sizeof(int), st), err);
+        void* kargs[] = {(void*)&a};
+        CU(cudaLaunchCooperativeKernel(kgrid_ptr<T>(), dim3(grid), dim3(threads), kargs, dyn, st), err);
+    } else {
+        CU(cudaMemcpyAsync(dev_args, &a, sizeof(Args<T>), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemsetAsync(queue, 0, sizeof(int), st), err);
+        CU(launch_block<T>(1, threads, dyn, st, dev_args, 1, queue), err);
+    }
+    return SCS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// scs_work
+// ---------------------------------------------------------------------------
+struct scs_work {
+    HostProb H;
+    scs_settings S;
+    cudaStream_t stream = nullptr;
+    DevInfo D;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    DevProb<double> P64;
+    DevWork<double> W64;
+    DevProb<float> P32;
+    DevWork<float> W32;
+    bool has32 = false;
+    Args<double>* dargs64 = nullptr;
+    Args<float>* dargs32 = nullptr;
+    int* queue = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    char err[512];
+    double setup_s = 0;
+};
+
+static double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+extern "C" int scs_default_settings(scs_settings* o)
+{
+    if (!o) return SCS_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->direction = SCS_DIR_AA;
+    o->mem = 10;
+    o->eps = 1e-5;
+    o->c0 = 0.99;
+    o->c1 = 0.99;
+    o->q = 0.99;
+    o->sigma = 1e-2;
+    o->lambda = 1.0;
+    o->thetabar = 0.1;
+    o->max_iters = 10000;
+    o->ls_max = 20;
+    o->cg_max = 1000;
+    o->check_every = 1;
+    o->cg_rtol = 1e-10;
+    o->time_limit_s = 0;
+    o->precision = SCS_FP64;
+    o->aa_reg = 1e-10;
+    o->team = SCS_TEAM_AUTO;
+    o->threads = 0;
+    o->mixed_cg_rtol = 1e-6;
+    o->mixed_stall = 50;
+    o->mixed_max_iters = 10000;
+    return SCS_OK;
+}
+
+template <typename T>
+static Args<T> make_args(const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, int mode, int slot = 0)
+{
+    Args<T> a;
+    a.P = P;
+    a.W = W;
+    a.S = S;
+    a.mode = mode;
+    a.slot = slot;
+    return a;
+}
+
+template <typename T>
+static int run_setup_g(scs_work* w, const DevProb<T>& P, const DevWork<T>& W, Args<T>* dargs, size_t dyn)
+{
+    DevSettings S = dev_settings(&w->S);
+    S.cg_max = std::max(10 * w->S.cg_max, 10000);
+    S.cg_rtol = std::min(w->S.cg_rtol, sizeof(T) == 8 ? 1e-12 : 1e-7);
+    Args<T> a = make_args(P, W, S, MODE_SETUP);
+    return launch<T>(w->D.team, w->D.threads, w->D.grid, dyn, a, dargs, w->queue, w->stream, w->err);
+}
+
+extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_settings* settings, void* cuda_stream,
+                         scs_work** out)
+{
+    if (!out) { set_err(g_err, "out must not be NULL"); return SCS_EINVAL; }
+    *out = nullptr;
+    const double t0 = now_s();
+    scs_work* w = new (std::nothrow) scs_work();
+    if (!w) { set_err(g_err, "host allocation failed"); return SCS_ENOMEM; }
+    w->err[0] = 0;
+    int rc = check_settings(settings, w->err);
+    if (!rc) rc = prepare(data, cone, w->H, w->err);
+    if (rc) { memcpy(g_err, w->err, 512); delete w; return rc; }
+    w->S = *settings;
+    w->stream = (cudaStream_t)cuda_stream;
+    const HostProb& H = w->H;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) { set_err(g_err, "no CUDA device: %s", cudaGetErrorString(ce)); delete w; return SCS_ECUDA; }
+    cudaDeviceGetAttribute(&w->D.sms, cudaDevAttrMultiProcessorCount, dev);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const long long work_size = H.nnz + (long long)H.n + H.m;
+    int team = settings->team;
+    if (team == SCS_TEAM_AUTO) team = (work_size < 150000 || !coop) ? SCS_TEAM_BLOCK : SCS_TEAM_GRID;
+    if (team == SCS_TEAM_GRID && !coop) { set_err(w->err, "device lacks cooperative launch"); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
+    w->D.team = team;
+    w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? 512 : 256);
+    w->has32 = settings->precision == SCS_MIXED;
+    w->D.dyn64 = dyn_smem<double>(H);
+    w->D.dyn32 = w->has32 ? dyn_smem<float>(H) : 0;
+    int rc2 = config_kernels<double>(w->D.dyn64, w->err);
+    if (!rc2 && w->has32) rc2 = config_kernels<float>(w->D.dyn32, w->err);
+    if (rc2) { memcpy(g_err, w->err, 512); delete w; return rc2; }
+    if (team == SCS_TEAM_GRID) {
+        int nb64 = 0, nb32 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb64, kgrid_ptr<double>(), w->D.threads, w->D.dyn64);
+        int nb = nb64;
+        if (w->has32) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb32, kgrid_ptr<float>(), w->D.threads, w->D.dyn32);
+            nb = std::min(nb64, nb32);
+        }
+        if (nb < 1) { set_err(w->err, "solver kernel cannot be resident with %d threads", w->D.threads); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
+        w->D.grid = w->D.sms * std::min(nb, 4);
+    } else {
+        w->D.grid = 1;
+    }
+    // measure and allocate one arena
+    Arena A;
+    DevProb<double> P64{};
+    DevWork<double> W64{};
+    DevProb<float> P32{};
+    DevWork<float> W32{};
+    const int mem = std::max(settings->mem, 1);
+    lay_out<double>(A, H, mem, w->D.grid, P64, W64, nullptr);
+    if (w->has32) lay_out<float>(A, H, mem, w->D.grid, P32, W32, (const int*)1);
+    size_t bytes = A.off + sizeof(Args<double>) + sizeof(Args<float>) + 1024;
+    ce = cudaMalloc((void**)&w->arena, bytes);
+    if (ce != cudaSuccess) { set_err(w->err, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(ce)); memcpy(g_err, w->err, 512); delete w; return SCS_ENOMEM; }
+    w->arena_bytes = bytes;
+    A.off = 0;
+    A.base = w->arena;
+    lay_out<double>(A, H, mem, w->D.grid, w->P64, w->W64, nullptr);
+    if (w->has32) {
+        lay_out<float>(A, H, mem, w->D.grid, w->P32, w->W32, (const int*)1);
+        w->P32.Ap = w->P64.Ap;
+        w->P32.Ai = w->P64.Ai;
+        w->P32.Tp = w->P64.Tp;
+        w->P32.Ti = w->P64.Ti;
+        w->P32.q_off = w->P64.q_off;
+        w->P32.s_dim = w->P64.s_dim;
+        w->P32.s_off = w->P64.s_off;
+    }
+    w->dargs64 = A.take<Args<double>>(1);
+    w->dargs32 = A.take<Args<float>>(1);
+    w->queue = A.take<int>(4);
+    if (A.off > bytes) { set_err(w->err, "arena overflow"); memcpy(g_err, w->err, 512); scs_finish(w); return SCS_ECUDA; }
+    auto fail = [&](int r) { memcpy(g_err, w->err, 512); scs_finish(w); return r; };
+    if (cudaMemsetAsync(w->arena, 0, bytes, w->stream) != cudaSuccess) { set_err(w->err, "memset failed"); return fail(SCS_ECUDA); }
+    if ((rc = upload<double>(H, w->P64, true, w->stream, w->err))) return fail(rc);
+    if (w->has32 && (rc = upload<float>(H, w->P32, false, w->stream, w->err))) return fail(rc);
+    if ((rc = run_setup_g<double>(w, w->P64, w->W64, w->dargs64, w->D.dyn64))) return fail(rc);
+    if (w->has32 && (rc = run_setup_g<float>(w, w->P32, w->W32, w->dargs32, w->D.dyn32))) return fail(rc);
+    if (cudaStreamSynchronize(w->stream) != cudaSuccess) {
+        set_err(w->err, "setup kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SCS_ECUDA);
+    }
+    int abort_flag = 0;
+    cudaMemcpy(&abort_flag, w->W64.abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (abort_flag) { set_err(w->err, "device barrier timed out in setup"); return fail(SCS_ETIMEOUT); }
+    for (auto& e : w->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { set_err(w->err, "cudaEventCreate failed"); return fail(SCS_ECUDA); }
+    w->setup_s = now_s() - t0;
+    *out = w;
+    return SCS_OK;
+}
+
+extern "C" void scs_finish(scs_work* w)
+{
+    if (!w) return;
+    for (auto& e : w->ev)
+        if (e) cudaEventDestroy(e);
+    if (w->arena) cudaFree(w->arena);
+    delete w;
+}
+
+extern "C" const char* scs_last_error(const scs_work* w) { return w ? w->err : g_err; }
+
+static void fill_info(scs_info* info, const DevState& s)
+{
+    info->status = s.status;
+    info->iters = s.iters;
+    info->k0 = s.k0;
+    info->k1 = s.k1;
+    info->k2 = s.k2;
+    info->backtracks = s.backtracks;
+    info->cg_iters = s.cg_iters;
+    info->pr = s.pr;
+    info->dr = s.dr;
+    info->gap = s.gap;
+    info->ic = s.ic;
+    info->uc = s.uc;
+    info->pobj = s.pobj;
+    info->dobj = s.dobj;
+}
+
+template <typename T>
+static int reset_solve_state(scs_work* w, const DevWork<T>& W, const HostProb& H)
+{
+    CU(cudaMemsetAsync(W.ws[0], 0, sizeof(T) * H.n, w->stream), w->err);
+    CU(cudaMemsetAsync(W.ws[1], 0, sizeof(T) * H.n, w->stream), w->err);
+    CU(cudaMemsetAsync(&W.st->mat_passes, 0, sizeof(long long), w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info* info)
+{
+    if (!w) { set_err(g_err, "work is NULL"); return SCS_EINVAL; }
+    const double t0 = now_s();
+    const HostProb& H = w->H;
+    const int N = H.n + H.m + 1;
+    int rc;
+    DevSettings S = dev_settings(&w->S);
+    if (w->S.warm == 1) {
+        if (!w->S.warm_u) { set_err(w->err, "warm = 1 needs warm_u"); return SCS_EINVAL; }
+        CU(cudaMemcpyAsync(w->W64.warm, w->S.warm_u, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+        S.use_warm = 1;
+    }
+    if ((rc = reset_solve_state<double>(w, w->W64, H))) return rc;
+    DevState st32{};
+    if (w->has32) {
+        if ((rc = reset_solve_state<float>(w, w->W32, H))) return rc;
+        DevSettings S32 = S;
+        S32.cg_rtol = w->S.mixed_cg_rtol > 0 ? w->S.mixed_cg_rtol : 1e-6;
+        S32.stall_iters = w->S.mixed_stall;
+        S32.max_iters = w->S.mixed_max_iters > 0 ? std::min(w->S.mixed_max_iters, w->S.max_iters) : w->S.max_iters;
+        if (S.use_warm) CU(cudaMemcpyAsync(w->W32.warm, w->W64.warm, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
+        Args<float> a32 = make_args(w->P32, w->W32, S32, MODE_SOLVE);
+        CU(cudaEventRecord(w->ev[2], w->stream), w->err);
+        if ((rc = launch<float>(w->D.team, w->D.threads, w->D.grid, w->D.dyn32, a32, w->dargs32, w->queue, w->stream, w->err))) return rc;
+        CU(cudaEventRecord(w->ev[3], w->stream), w->err);
+        // FP64 phase starts from the FP32 iterate and CG warm starts
+        CU(cudaMemcpyAsync(w->W64.warm, w->W32.u_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
+        for (int k = 0; k < 2; ++k) {
+            CU(launch_f2d(w->W32.ws[k], w->W64.ws[k], H.n, w->stream), w->err);
+        }
+        S.use_warm = 1;
+        CU(cudaMemcpyAsync(&st32, w->W32.st, sizeof(DevState), cudaMemcpyDeviceToHost, w->stream), w->err);
+    }
+    Args<double> a = make_args(w->P64, w->W64, S, MODE_SOLVE);
+    CU(cudaEventRecord(w->ev[0], w->stream), w->err);
+    if ((rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
+    CU(cudaEventRecord(w->ev[1], w->stream), w->err);
+    DevState st{};
+    int abort_flag = 0;
+    CU(cudaMemcpyAsync(&st, w->W64.st, sizeof(DevState), cudaMemcpyDeviceToHost, w->stream), w->err);
+    CU(cudaMemcpyAsync(&abort_flag, w->W64.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, w->stream), w->err);
+    if (x) CU(cudaMemcpyAsync(x, w->W64.x_out, sizeof(double) * H.n, cudaMemcpyDefault, w->stream), w->err);
+    if (y) CU(cudaMemcpyAsync(y, w->W64.y_out, sizeof(double) * H.m, cudaMemcpyDefault, w->stream), w->err);
+    if (s) CU(cudaMemcpyAsync(s, w->W64.s_out, sizeof(double) * H.m, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    int abort32 = 0;
+    if (w->has32) CU(cudaMemcpy(&abort32, w->W32.abort_flag, sizeof(int), cudaMemcpyDeviceToHost), w->err);
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        fill_info(info, st);
+        if (w->has32) {
+            info->iters += st32.iters;
+            info->iters_fp32 = st32.iters;
+            info->k0 += st32.k0;
+            info->k1 += st32.k1;
+            info->k2 += st32.k2;
+            info->backtracks += st32.backtracks;
+            info->cg_iters += st32.cg_iters;
+        }
+        info->setup_s = w->setup_s;
+        info->solve_s = now_s() - t0;
+        info->device_error = abort_flag | abort32;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, w->ev[0], w->ev[1]) == cudaSuccess) info->kernel_s[0] = ms * 1e-3;
+        info->mat_passes[0] = st.mat_passes;
+        if (w->has32) {
+            if (cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]) == cudaSuccess) info->kernel_s[1] = ms * 1e-3;
+            info->mat_passes[1] = st32.mat_passes;
+            info->cg_iters_fp32 = st32.cg_iters;
+        }
+    }
+    if (abort_flag || abort32) { set_err(w->err, "device barrier timed out"); return SCS_ETIMEOUT; }
+    return SCS_OK;
+}
+
+extern "C" int scs_get_u(scs_work* w, double* u)
+{
+    if (!w || !u) { set_err(w ? w->err : g_err, "NULL argument"); return SCS_EINVAL; }
+    const int N = w->H.n + w->H.m + 1;
+    CU(cudaMemcpyAsync(u, w->W64.u_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_update_bc(scs_work* w, const double* b, const double* c)
+{
+    if (!w) { set_err(g_err, "work is NULL"); return SCS_EINVAL; }
+    HostProb& H = w->H;
+    if (b) {
+        for (int i = 0; i < H.m; ++i)
+            if (!std::isfinite(b[i])) { set_err(w->err, "non-finite b[%d]", i); return SCS_EINVAL; }
+        H.b.assign(b, b + H.m);
+    }
+    if (c) {
+        for (int j = 0; j < H.n; ++j)
+            if (!std::isfinite(c[j])) { set_err(w->err, "non-finite c[%d]", j); return SCS_EINVAL; }
+        H.c.assign(c, c + H.n);
+    }
+    double s2 = 0;
+    for (double v : H.b) s2 += v * v;
+    H.nb = std::sqrt(s2);
+    s2 = 0;
+    for (double v : H.c) s2 += v * v;
+    H.nc = std::sqrt(s2);
+    w->P64.nb = w->P32.nb = H.nb;
+    w->P64.nc = w->P32.nc = H.nc;
+    int rc;
+    CU(cudaMemcpyAsync((void*)w->P64.b, H.b.data(), sizeof(double) * H.m, cudaMemcpyHostToDevice, w->stream), w->err);
+    CU(cudaMemcpyAsync((void*)w->P64.c, H.c.data(), sizeof(double) * H.n, cudaMemcpyHostToDevice, w->stream), w->err);
+    CU(cudaMemsetAsync(w->W64.ws[0], 0, sizeof(double) * H.n, w->stream), w->err);
+    if ((rc = run_setup_g<double>(w, w->P64, w->W64, w->dargs64, w->D.dyn64))) return rc;
+    if (w->has32) {
+        std::vector<float> tb(H.b.begin(), H.b.end()), tc(H.c.begin(), H.c.end());
+        CU(cudaMemcpyAsync((void*)w->P32.b, tb.data(), sizeof(float) * H.m, cudaMemcpyHostToDevice, w->stream), w->err);
+        CU(cudaMemcpyAsync((void*)w->P32.c, tc.data(), sizeof(float) * H.n, cudaMemcpyHostToDevice, w->stream), w->err);
+        CU(cudaMemsetAsync(w->W32.ws[0], 0, sizeof(float) * H.n, w->stream), w->err);
+        if ((rc = run_setup_g<float>(w, w->P32, w->W32, w->dargs32, w->D.dyn32))) return rc;
+        CU(cudaStreamSynchronize(w->stream), w->err);
+    }
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+static int single_op(scs_work* w, int mode, int slot, const double* in, double* out, double* out2)
+{
+    if (!w || !in) { set_err(w ? w->err : g_err, "NULL argument"); return SCS_EINVAL; }
+    const int N = w->H.n + w->H.m + 1;
+    CU(cudaMemcpyAsync(w->W64.io_in, in, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    DevSettings S = dev_settings(&w->S);
+    Args<double> a = make_args(w->P64, w->W64, S, mode, slot);
+    int rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
+    if (rc) return rc;
+    if (out) CU(cudaMemcpyAsync(out, w->W64.io_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    if (out2) CU(cudaMemcpyAsync(out2, w->W64.io_out2, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_linsys(scs_work* w, const double* r, double* out, int32_t slot)
+{
+    return single_op(w, MODE_LINSYS, slot ? 1 : 0, r, out, nullptr);
+}
+extern "C" int scs_project_cone(scs_work* w, const double* v, double* out)
+{
+    return single_op(w, MODE_PROJECT, 0, v, out, nullptr);
+}
+extern "C" int scs_apply_T(scs_work* w, const double* u, double* Tu, double* Ru)
+{
+    return single_op(w, MODE_APPLY_T, 0, u, Tu, Ru);
+}
+
+// ---------------------------------------------------------------------------
+// batches: one arena, one descriptor per instance, persistent CTAs
+// ---------------------------------------------------------------------------
+struct scs_batch {
+    int B = 0;
+    std::vector<HostProb> H;
+    std::vector<int> order;  // queue position -> instance
+    scs_settings S;
+    cudaStream_t stream = nullptr;
+    char* arena = nullptr;
+    int threads = 256, grid = 1;
+    bool has32 = false;
+    size_t dyn64 = 0, dyn32 = 0;
+    std::vector<Args<double>> a64;
+    std::vector<Args<float>> a32;
+    Args<double>* d64 = nullptr;
+    Args<float>* d32 = nullptr;
+    int* queue = nullptr;
+    char err[512];
+    double setup_s = 0;
+};
+
+static int pick_threads(const std::vector<HostProb>& H)
+{
+    long long tot = 0;
+    for (const auto& h : H) tot += h.n + h.m;
+    const double avg = H.empty() ? 0 : (double)tot / H.size();
+    return avg < 600 ? 128 : (avg < 3000 ? 256 : 512);
+}
+
+template <typename T>
+static int batch_launch(scs_batch* b, int mode, const DevSettings& S, Args<T>* dargs, std::vector<Args<T>>& host_args,
+                        size_t dyn)
+{
+    for (auto& a : host_args) {
+        a.S = S;
+        a.mode = mode;
+    }
+    CU(cudaMemcpyAsync(dargs, host_args.data(), sizeof(Args<T>) * host_args.size(), cudaMemcpyHostToDevice, b->stream), b->err);
+    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+    CU(launch_block<T>(b->grid, b->threads, dyn, b->stream, dargs, b->B, b->queue), b->err);
+    CU(cudaStreamSynchronize(b->stream), b->err);  // host_args may change before the next launch
+    return SCS_OK;
+}
+
+extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs_cone* const* cones,
+                               const scs_settings* settings, void* cuda_stream, scs_batch** out)
+{
+    if (!out) { set_err(g_err, "out must not be NULL"); return SCS_EINVAL; }
+    *out = nullptr;
+    if (B <= 0 || !data || !cones) { set_err(g_err, "bad batch arguments"); return SCS_EINVAL; }
+    const double t0 = now_s();
+    scs_batch* b = new (std::nothrow) scs_batch();
+    if (!b) return SCS_ENOMEM;
+    b->err[0] = 0;
+    int rc = check_settings(settings, b->err);
+    if (rc) { memcpy(g_err, b->err, 512); delete b; return rc; }
+    b->B = B;
+    b->S = *settings;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->H.resize(B);
+    for (int i = 0; i < B; ++i) {
+        if ((rc = prepare(data[i], cones[i], b->H[i], b->err))) {
+            char tmp[512];
+            snprintf(tmp, sizeof tmp, "instance %d: %.480s", i, b->err);
+            memcpy(b->err, tmp, 512);
+            memcpy(g_err, b->err, 512);
+            delete b;
+            return rc;
+        }
+    }
+    b->order.resize(B);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        return b->H[x].nnz + b->H[x].n + b->H[x].m > b->H[y].nnz + b->H[y].n + b->H[y].m;
+    });
+    b->has32 = settings->precision == SCS_MIXED;
+    bool any_psd = false;
+    for (auto& h : b->H) any_psd |= !h.s.empty();
+    b->dyn64 = any_psd ? psd_smem_bytes<double>() : 0;
+    b->dyn32 = any_psd && b->has32 ? psd_smem_bytes<float>() : 0;
+    if ((rc = config_kernels<double>(b->dyn64, b->err)) || (b->has32 && (rc = config_kernels<float>(b->dyn32, b->err)))) {
+        memcpy(g_err, b->err, 512);
+        delete b;
+        return rc;
+    }
+    b->threads = settings->threads ? settings->threads : pick_threads(b->H);
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kblock_ptr<double>(), b->threads, b->dyn64);
+    b->grid = std::max(1, std::min(B, sms * std::max(nb, 1)));
+    const int mem = std::max(settings->mem, 1);
+    Arena A;
+    b->a64.resize(B);
+    if (b->has32) b->a32.resize(B);
+    for (int qi = 0; qi < B; ++qi) {
+        const HostProb& h = b->H[b->order[qi]];
+        lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr);
+        if (b->has32) lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1);
+    }
+    A.take<Args<double>>(B);
+    A.take<Args<float>>(B);
+    A.take<int>(4);
+    const size_t bytes = A.off + 1024;
+    if (cudaMalloc((void**)&b->arena, bytes) != cudaSuccess) {
+        set_err(b->err, "cudaMalloc(%zu) failed", bytes);
+        memcpy(g_err, b->err, 512);
+        delete b;
+        return SCS_ENOMEM;
+    }
+    auto fail = [&](int r) { memcpy(g_err, b->err, 512); scs_batch_finish(b); return r; };
+    A.off = 0;
+    A.base = b->arena;
+    for (int qi = 0; qi < B; ++qi) {
+        const HostProb& h = b->H[b->order[qi]];
+        lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr);
+        if (b->has32) {
+            lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1);
+            DevProb<float>& p = b->a32[qi].P;
+            const DevProb<double>& q = b->a64[qi].P;
+            p.Ap = q.Ap; p.Ai = q.Ai; p.Tp = q.Tp; p.Ti = q.Ti; p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
+        }
+    }
+    b->d64 = A.take<Args<double>>(B);
+    b->d32 = A.take<Args<float>>(B);
+    b->queue = A.take<int>(4);
+    if (cudaMemsetAsync(b->arena, 0, bytes, b->stream) != cudaSuccess) { set_err(b->err, "memset failed"); return fail(SCS_ECUDA); }
+    for (int qi = 0; qi < B; ++qi) {
+        const HostProb& h = b->H[b->order[qi]];
+        if ((rc = upload<double>(h, b->a64[qi].P, true, b->stream, b->err))) return fail(rc);
+        if (b->has32 && (rc = upload<float>(h, b->a32[qi].P, false, b->stream, b->err))) return fail(rc);
+    }
+    DevSettings S = dev_settings(settings);
+    S.cg_max = std::max(10 * settings->cg_max, 10000);
+    DevSettings S64 = S, S32 = S;
+    S64.cg_rtol = std::min(settings->cg_rtol, 1e-12);
+    S32.cg_rtol = std::min(settings->cg_rtol, 1e-7);
+    if ((rc = batch_launch<double>(b, MODE_SETUP, S64, b->d64, b->a64, b->dyn64))) return fail(rc);
+    if (b->has32 && (rc = batch_launch<float>(b, MODE_SETUP, S32, b->d32, b->a32, b->dyn32))) return fail(rc);
+    b->setup_s = now_s() - t0;
+    *out = b;
+    return SCS_OK;
+}
+
+extern "C" void scs_batch_finish(scs_batch* b)
+{
+    if (!b) return;
+    if (b->arena) cudaFree(b->arena);
+    delete b;
+}
+
+extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y, double* const* s, scs_info* infos)
+{
+    if (!b) { set_err(g_err, "batch is NULL"); return SCS_EINVAL; }
+    const double t0 = now_s();
+    int rc;
+    for (int qi = 0; qi < b->B; ++qi) {
+        const HostProb& h = b->H[b->order[qi]];
+        CU(cudaMemsetAsync(b->a64[qi].W.ws[0], 0, sizeof(double) * h.n, b->stream), b->err);
+        CU(cudaMemsetAsync(b->a64[qi].W.ws[1], 0, sizeof(double) * h.n, b->stream), b->err);
+        if (b->has32) {
+            CU(cudaMemsetAsync(b->a32[qi].W.ws[0], 0, sizeof(float) * h.n, b->stream), b->err);
+            CU(cudaMemsetAsync(b->a32[qi].W.ws[1], 0, sizeof(float) * h.n, b->stream), b->err);
+        }
+    }
+    DevSettings S = dev_settings(&b->S);
+    std::vector<DevState> st32(b->B);
+    if (b->has32) {
+        DevSettings S32 = S;
+        S32.cg_rtol = b->S.mixed_cg_rtol > 0 ? b->S.mixed_cg_rtol : 1e-6;
+        S32.stall_iters = b->S.mixed_stall;
+        S32.max_iters = b->S.mixed_max_iters > 0 ? std::min(b->S.mixed_max_iters, b->S.max_iters) : b->S.max_iters;
+        if ((rc = batch_launch<float>(b, MODE_SOLVE, S32, b->d32, b->a32, b->dyn32))) return rc;
+        for (int qi = 0; qi < b->B; ++qi) {
+            const HostProb& h = b->H[b->order[qi]];
+            const int N = h.n + h.m + 1;
+            CU(cudaMemcpyAsync(b->a64[qi].W.warm, b->a32[qi].W.u_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, b->stream), b->err);
+            for (int k = 0; k < 2; ++k)
+                CU(launch_f2d(b->a32[qi].W.ws[k], b->a64[qi].W.ws[k], h.n, b->stream), b->err);
+            CU(cudaMemcpyAsync(&st32[qi], b->a32[qi].W.st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), b->err);
+        }
+        S.use_warm = 1;
+    }
+    if ((rc = batch_launch<double>(b, MODE_SOLVE, S, b->d64, b->a64, b->dyn64))) return rc;
+    std::vector<DevState> st(b->B);
+    for (int qi = 0; qi < b->B; ++qi) {
+        const int i = b->order[qi];
+        const HostProb& h = b->H[i];
+        CU(cudaMemcpyAsync(&st[qi], b->a64[qi].W.st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), b->err);
+        if (x && x[i]) CU(cudaMemcpyAsync(x[i], b->a64[qi].W.x_out, sizeof(double) * h.n, cudaMemcpyDefault, b->stream), b->err);
+        if (y && y[i]) CU(cudaMemcpyAsync(y[i], b->a64[qi].W.y_out, sizeof(double) * h.m, cudaMemcpyDefault, b->stream), b->err);
+        if (s && s[i]) CU(cudaMemcpyAsync(s[i], b->a64[qi].W.s_out, sizeof(double) * h.m, cudaMemcpyDefault, b->stream), b->err);
+    }
+    CU(cudaStreamSynchronize(b->stream), b->err);
+    const double el = now_s() - t0;
+    if (infos) {
+        for (int qi = 0; qi < b->B; ++qi) {
+            const int i = b->order[qi];
+            scs_info* info = &infos[i];
+            memset(info, 0, sizeof(*info));
+            fill_info(info, st[qi]);
+            if (b->has32) {
+                info->iters += st32[qi].iters;
+                info->iters_fp32 = st32[qi].iters;
+                info->k0 += st32[qi].k0;
+                info->k1 += st32[qi].k1;
+                info->k2 += st32[qi].k2;
+                info->backtracks += st32[qi].backtracks;
+                info->cg_iters += st32[qi].cg_iters;
+            }
+            info->setup_s = b->setup_s;
+            info->solve_s = el;
+        }
+    }
+    return SCS_OK;
+}
+
+extern "C" int scs_solve_batch(int32_t B, const scs_data* const* data, const scs_cone* const* cones,
+                               const scs_settings* settings, void* cuda_stream, double* const* x, double* const* y,
+                               double* const* s, scs_info* infos)
+{
+    scs_batch* b = nullptr;
+    int rc = scs_batch_setup(B, data, cones, settings, cuda_stream, &b);
+    if (rc) return rc;
+    rc = scs_batch_solve(b, x, y, s, infos);
+    scs_batch_finish(b);
+    return rc;
+}

@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle.
+
+Single operators of Eq. (drs) are compared element by element:
+  Pi_C            identical arithmetic up to rounding      -> 1e-12 relative
+  (I+Q)^{-1}      both CG to 1e-14 relative residual       -> 1e-9 relative
+  T, R            composition of the two                   -> 1e-9 relative
+Whole solves are iterations whose paths diverge with rounding, so parity is
+judged on what is unique: the status, the GPU's own KKT residuals (<= eps,
+recomputed here in FP64 from the returned x, y, s), the objective within
+10 eps (1 + |p*|), and x itself where the solution is unique.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1903_06477_gb300 import binding as B
+from paper_1903_06477_gb300 import workloads as W
+from tests.helpers import check_in_cone
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    return {
+        "lasso": W.lasso(seed=0),
+        "planted_mixed_cones": W.planted(seed=2, n=70, l=50, soc=[1, 2, 3, 7, 40], psd=[1, 2, 3, 5], f=3, nnz=1500),
+        "portfolio": W.portfolio(seed=3, k=60),
+        "planted_c2_small": W.c2_planted(seed=1, scale=0.01),
+    }
+
+
+PROBS = _problems()
+TEAMS = [B.TEAM_BLOCK, B.TEAM_GRID]
+
+
+def _kkt(prob, x, y, s):
+    A, b, c = prob["A"], prob["b"], prob["c"]
+    pr = np.linalg.norm(A @ x + s - b) / (1 + np.linalg.norm(b))
+    dr = np.linalg.norm(A.T @ y + c) / (1 + np.linalg.norm(c))
+    cx, by = c @ x, b @ y
+    gap = abs(cx + by) / (1 + abs(cx) + abs(by))
+    return pr, dr, gap
+
+
+@pytest.mark.parametrize("team", TEAMS)
+@pytest.mark.parametrize("name", list(PROBS))
+def test_project_cone_parity(name, team):
+    prob = PROBS[name]
+    work = B.Work(prob, team=team, cg_rtol=1e-14)
+    orc = O.Oracle(prob, cg_rtol=1e-14)
+    rng = np.random.default_rng(0)
+    for scale in (0.1, 1.0, 30.0):
+        v = rng.standard_normal(work.N) * scale
+        v[-1] = -abs(v[-1]) if scale == 1.0 else v[-1]
+        out = work.project_cone(v)
+        ref = orc.proj_C(v)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * (1 + np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("team", TEAMS)
+@pytest.mark.parametrize("name", list(PROBS))
+def test_linsys_and_T_parity(name, team):
+    prob = PROBS[name]
+    work = B.Work(prob, team=team, cg_rtol=1e-14, cg_max=5000)
+    orc = O.Oracle(prob, cg_rtol=1e-14, cg_max=5000)
+    rng = np.random.default_rng(1)
+    for slot in (0, 1, 0):
+        r = rng.standard_normal(work.N) * 3
+        out = work.linsys(r, slot=slot)
+        ref = orc.linsys(r, slot=slot)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-9 * (1 + np.abs(ref).max()))
+    u = rng.standard_normal(work.N)
+    Tu, Ru = work.apply_T(u)
+    Tr, Rr = orc.apply_T(u)
+    np.testing.assert_allclose(Tu, Tr, rtol=0, atol=1e-9 * (1 + np.abs(Tr).max()))
+    np.testing.assert_allclose(Ru, Rr, rtol=0, atol=1e-9 * (1 + np.abs(Tr).max()))
+
+
+@pytest.mark.parametrize("team", TEAMS)
+@pytest.mark.parametrize("direction", [B.DIR_AA, B.DIR_RB])
+@pytest.mark.parametrize("name", list(PROBS))
+def test_solve_parity_fp64(name, direction, team):
+    prob = PROBS[name]
+    eps = 1e-6
+    c0 = 0.99 if direction == B.DIR_AA else 0.1
+    kw = dict(direction=direction, mem=10, c0=c0, eps=eps, max_iters=20000, cg_rtol=1e-12)
+    work = B.Work(prob, team=team, **kw)
+    x, y, s, info = work.solve()
+    okw = dict(kw)
+    okw["cg_rtol"] = 1e-12
+    ref = O.Oracle(prob, **okw).solve()
+    assert info["status"] == B.SOLVED == ref["info"].status, (info, ref["info"])
+    assert max(info["pr"], info["dr"], info["gap"]) <= eps
+    pr, dr, gap = _kkt(prob, x, y, s)
+    assert max(pr, dr, gap) <= eps * 1.01, (pr, dr, gap)
+    check_in_cone(prob, s, dual=False, tol=1e-7 * (1 + np.abs(s).max()))
+    check_in_cone(prob, y, dual=True, tol=1e-7 * (1 + np.abs(y).max()))
+    p_ref = ref["info"].pobj
+    assert abs(info["pobj"] - p_ref) <= 10 * eps * (1 + abs(p_ref))
+    if "xstar" in prob:
+        pstar = prob["c"] @ prob["xstar"]
+        assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+    if name == "lasso":
+        nv = prob["meta"]["nvar"]
+        np.testing.assert_allclose(x[:nv], ref["x"][:nv], atol=5e-4)
+
+
+def test_km_iterates_match_oracle():
+    """d = 0 and K0 off: both sides run the KM iteration (Eq. km); the iterates
+    agree to CG accuracy after a fixed number of steps."""
+    prob = PROBS["planted_mixed_cones"]
+    kw = dict(direction=B.DIR_NONE, c0=0.0, eps=1e-30, max_iters=30, cg_rtol=1e-14, cg_max=5000)
+    for team in TEAMS:
+        work = B.Work(prob, team=team, **kw)
+        work.solve()
+        u = work.get_u()
+        okw = dict(kw)
+        okw["direction"] = O.DIR_NONE
+        ref = O.Oracle(prob, **okw).solve()
+        np.testing.assert_allclose(u, ref["u"], rtol=0, atol=1e-8 * (1 + np.abs(ref["u"]).max()))
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_infeasible_and_unbounded(team):
+    eps = 1e-7
+    for kind, prob in (("inf", W.infeasible(seed=3, n=80, l=80, nnz=1500)),
+                       ("unb", W.unbounded(seed=4, n=80, l=80, nnz=1500))):
+        work = B.Work(prob, team=team, eps=eps, max_iters=20000, cg_rtol=1e-12)
+        x, y, s, info = work.solve()
+        if kind == "inf":
+            assert info["status"] == B.INFEASIBLE, info
+            assert abs(prob["b"] @ y + 1) <= 1e-8
+            assert np.linalg.norm(prob["A"].T @ y) * np.linalg.norm(prob["b"]) <= eps * 1.01
+            check_in_cone(prob, y, dual=True, tol=1e-9)
+            assert np.all(np.isnan(x))
+        else:
+            assert info["status"] == B.UNBOUNDED, info
+            assert abs(prob["c"] @ x + 1) <= 1e-8
+            assert np.linalg.norm(prob["A"] @ x + s) * np.linalg.norm(prob["c"]) <= eps * 1.01
+            check_in_cone(prob, s, dual=False, tol=1e-9)
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_mixed_precision_reaches_fp64_tolerance(team):
+    prob = W.c2_planted(seed=2, scale=0.02)
+    eps = 1e-6
+    work = B.Work(prob, team=team, precision=B.MIXED, eps=eps, max_iters=20000)
+    x, y, s, info = work.solve()
+    assert info["status"] == B.SOLVED, info
+    assert info["iters_fp32"] > 0
+    pr, dr, gap = _kkt(prob, x, y, s)
+    assert max(pr, dr, gap) <= eps * 1.01
+    pstar = prob["c"] @ prob["xstar"]
+    assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+
+
+def test_edge_cases():
+    # zero-cone only rows, dimension-1 SOCs, an empty row, PSD of order 1
+    rng = np.random.default_rng(9)
+    prob = W.planted(seed=9, n=15, l=4, soc=[1, 1, 2], psd=[1], f=3, nnz=60)
+    A = prob["A"].tolil()
+    A[4, :] = 0  # an empty orthant row: s_4 = b_4
+    A = A.tocsr()
+    A.eliminate_zeros()
+    prob = dict(prob, A=A, b=A @ prob["xstar"] + prob["sstar"])
+    ycheck = prob["ystar"].copy()
+    prob["c"] = -(A.T @ ycheck)
+    for team in TEAMS:
+        work = B.Work(prob, team=team, eps=1e-7, max_iters=50000, cg_rtol=1e-12)
+        x, y, s, info = work.solve()
+        assert info["status"] == B.SOLVED, info
+        pr, dr, gap = _kkt(prob, x, y, s)
+        assert max(pr, dr, gap) <= 1.01e-7
+        v = rng.standard_normal(work.N)
+        np.testing.assert_allclose(work.project_cone(v), O.Oracle(prob).proj_C(v), atol=1e-12)
+
+
+def test_invalid_inputs_rejected():
+    prob = W.lasso(seed=0)
+    bad = dict(prob)
+    bad["b"] = prob["b"].copy()
+    bad["b"][3] = np.nan
+    with pytest.raises(B.SCSError):
+        B.Work(bad)
+    bad = dict(prob, l=prob["l"] + 1)
+    with pytest.raises(B.SCSError):
+        B.Work(bad)
+    with pytest.raises(B.SCSError):
+        B.Work(prob, mem=99)
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+def test_batch_parity(precision):
+    probs = [W.portfolio(seed=100 + i, k=int(k)) for i, k in enumerate(np.linspace(20, 140, 24))]
+    eps = 1e-6
+    batch = B.Batch(probs, precision=precision, eps=eps, max_iters=20000, cg_rtol=1e-12)
+    xs, ys, ss, infos = batch.solve()
+    for p, x, y, s, info in zip(probs, xs, ys, ss, infos):
+        assert info["status"] == B.SOLVED, info
+        pr, dr, gap = _kkt(p, x, y, s)
+        assert max(pr, dr, gap) <= eps * 1.01
+        ref = O.Oracle(p, eps=eps, max_iters=20000).solve()
+        assert abs(info["pobj"] - ref["info"].pobj) <= 10 * eps * (1 + abs(ref["info"].pobj))
+
+
+def test_device_pointers_roundtrip():
+    torch = pytest.importorskip("torch")
+    prob = PROBS["lasso"]
+    work = B.Work(prob, eps=1e-6)
+    xd = torch.empty(work.n, dtype=torch.float64, device="cuda")
+    yd = torch.empty(work.m, dtype=torch.float64, device="cuda")
+    sd = torch.empty(work.m, dtype=torch.float64, device="cuda")
+    _, _, _, info = work.solve(xd, yd, sd)
+    x2, y2, s2, info2 = work.solve()
+    assert info["status"] == info2["status"] == B.SOLVED
+    np.testing.assert_array_equal(xd.cpu().numpy(), x2)
+    np.testing.assert_array_equal(sd.cpu().numpy(), s2)
+
+
+def test_repeat_solves_are_deterministic():
+    prob = PROBS["planted_c2_small"]
+    work = B.Work(prob, team=B.TEAM_GRID, eps=1e-6)
+    a = work.solve()
+    b = work.solve()
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[3]["iters"] == b[3]["iters"]
