@@ -208,6 +208,11 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--max-iters", type=int, default=0, help="cap outer iterations (profiling only)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
+    ap.add_argument("--cg-adapt", type=float, default=None)
+    ap.add_argument("--mixed-switch", type=float, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -226,6 +231,15 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     prob, kw, cfg = build_workload(args.workload, rank)
+    if args.max_iters > 0:
+        kw["max_iters"] = args.max_iters
+        kw["mixed_max_iters"] = args.max_iters
+    if args.threads > 0:
+        kw["threads"] = args.threads
+    if args.cg_adapt is not None:
+        kw["cg_adapt"] = args.cg_adapt
+    if args.mixed_switch is not None:
+        kw["mixed_switch"] = args.mixed_switch
     prec = B.MIXED if args.precision == "mixed" else B.FP64
     n, m = prob["A"].shape[1], prob["A"].shape[0]
     work = B.Work(prob, stream=stream, precision=prec, **kw)
@@ -263,7 +277,8 @@ def main():
     # plain FP64 solve of the same instance, for the chosen-form comparison
     fp64_ms = None
     fp64_info = None
-    if prec == B.MIXED:
+    if prec == B.MIXED and not args.no_fp64:
+        xm = xd.cpu().numpy().copy()
         work64 = B.Work(prob, stream=stream, precision=B.FP64, **kw)
         work64.solve(xd, yd, sd)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -273,7 +288,6 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         fp64_ms = e0.elapsed_time(e1)
-        xm = xd.cpu().numpy()
         last["err_vs_fp64"] = float(np.linalg.norm(xm - x64) / max(1e-300, np.linalg.norm(x64)))
         work64.close()
     # roofline of the dominant solver kernel

@@ -104,6 +104,9 @@ typedef struct {
     int32_t mixed_stall;    /* FP32 phase ends after this many iterations without a
                                10% drop of max(pr,dr,gap) (SCS_MIXED) */
     int32_t mixed_max_iters;/* cap on FP32-phase iterations (SCS_MIXED) */
+    double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
+    double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
+                               (not in the paper; 0 keeps the fixed relative tolerance) */
 } scs_settings;
 
 typedef struct {

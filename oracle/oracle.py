@@ -59,6 +59,7 @@ class _Settings(C.Structure):
         ("check_every", C.c_int32),
         ("cg_rtol", C.c_double), ("aa_reg", C.c_double),
         ("warm_u", C.POINTER(C.c_double)),
+        ("cg_adapt", C.c_double),
     ]
 
 
@@ -122,7 +123,7 @@ def _ip(a):
 
 DEFAULTS = dict(direction=DIR_AA, mem=10, eps=1e-5, c0=0.99, c1=0.99, q=0.99, sigma=1e-2, lam=1.0,
                 thetabar=0.1, max_iters=2000, ls_max=20, cg_max=1000, check_every=1,
-                cg_rtol=1e-12, aa_reg=1e-10)
+                cg_rtol=1e-12, aa_reg=1e-10, cg_adapt=0.0)
 
 
 @dataclass

@@ -238,6 +238,7 @@ struct orc_work {
     double *ws[2];    /* CG warm starts (n) for the u~ and d~ systems */
     double *tm, *tn, *r, *p, *q, *rhs; /* scratch */
     int64_t cg_total;
+    double atol; /* absolute CG tolerance of the next solves (0 = rtol only) */
 };
 
 /* CG on (I + A^T A) x = rhs, x holds the warm start on entry */
@@ -257,6 +258,7 @@ static int cg_solve(orc_work *W, const double *rhs, double *x, double rtol, int3
     for (int32_t j = 0; j < n; ++j) { r[j] = rhs[j] - x[j] - q[j]; p[j] = r[j]; }
     double rr = vdot(r, r, n);
     double tol = rtol * bnorm;
+    if (W->atol > tol) tol = W->atol;
     int32_t it = 0;
     if (sqrt(rr) <= tol) return 0;
     for (it = 0; it < cg_max; ++it) {
@@ -683,6 +685,7 @@ int orc_solve(orc_work *W, double *x, double *y, double *s, double *u_out, orc_i
     eval_R(W, u, ut, ub, Ru);
     double nRu = vnorm(Ru, N);
     double eta0 = nRu, r_safe = eta0, eta = eta0;
+    W->atol = 0.0;
     int have_pair = 0;
     int status = ORC_MAX_ITERS;
     int check_every = S->check_every > 0 ? S->check_every : 1;
@@ -694,6 +697,9 @@ int orc_solve(orc_work *W, double *x, double *y, double *s, double *u_out, orc_i
             if (st != 0) { status = st; break; }
         }
         orc_dir_compute(D, Ru, zp, xip, have_pair, d);
+        /* reading taken for cg_adapt (not in the paper): inside the loop the CG
+         * solves may stop at an absolute residual cg_adapt * ||Ru|| */
+        W->atol = S->cg_adapt > 0.0 ? S->cg_adapt * nRu : 0.0;
         orc_linsys(W, d, dt, 1, NULL);
         int step;
         double alpha = 1.0;
@@ -780,6 +786,7 @@ int orc_solve(orc_work *W, double *x, double *y, double *s, double *u_out, orc_i
         info->dobj = -by;
     }
     if (u_out) memcpy(u_out, u, sizeof(double) * (size_t)N);
+    W->atol = 0.0;
     free(buf);
     orc_dir_free(D);
     return status;

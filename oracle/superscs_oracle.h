@@ -57,6 +57,7 @@ typedef struct {
     double cg_rtol;
     double aa_reg;
     const double *warm_u; /* N = n+m+1 values or NULL for u0 = (0,0,1) */
+    double cg_adapt;      /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru|| */
 } orc_settings;
 
 enum {

@@ -42,6 +42,7 @@ class Settings(C.Structure):
         ("precision", C.c_int32), ("warm", C.c_int32), ("warm_u", C.c_void_p), ("verbose", C.c_int32),
         ("aa_reg", C.c_double), ("team", C.c_int32), ("threads", C.c_int32),
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
+        ("mixed_switch", C.c_double), ("cg_adapt", C.c_double),
     ]
 
 

@@ -1,7 +1,7 @@
 """Builds libsuperscs.so in-tree from csrc/ with nvcc for sm_103a.
 
-The three translation units (FP64 kernels, FP32 kernels, host ABI) are
-compiled in parallel and linked against the shared CUDA runtime.
+The translation units (grid and block kernels in each precision, host ABI)
+are compiled in parallel and linked against the shared CUDA runtime.
 """
 from __future__ import annotations
 
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsuperscs.so")
-UNITS = ["kernels_f64.cu", "kernels_f32.cu", "superscs.cu"]
+UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_block_f64.cu", "kernels_block_f32.cu", "superscs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177"]

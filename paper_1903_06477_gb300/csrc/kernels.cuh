@@ -9,6 +9,8 @@
 namespace sscs {
 
 struct SmemFixed {
+    unsigned long long mbar[2 * MAX_WARPS];
+    unsigned ph[MAX_WARPS];
     double red[(MAX_WARPS + 1) * KMAX];
     double G[AAMAX * AAMAX];
     double L[AAMAX * AAMAX];
@@ -20,8 +22,17 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_grid(const __grid_constant__ Args<T> a)
 {
     __shared__ SmemFixed sf;
-    extern __shared__ __align__(16) unsigned char dyn[];
-    GridTeam tm{sf.red, a.W.partials, a.W.bar, a.W.abort_flag, 0};
+    extern __shared__ __align__(128) unsigned char dyn[];
+    const bool tma = a.P.A.wbnd != nullptr;
+    if (tma && (threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        mbar_init(smem_addr(&sf.mbar[2 * w]), 1);
+        mbar_init(smem_addr(&sf.mbar[2 * w + 1]), 1);
+        sf.ph[w] = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    GridTeam tm{sf.red, tma ? dyn : nullptr, sf.mbar, sf.ph, a.W.partials, a.W.bar, a.W.abort_flag, 0};
     run_mode<T>(tm, a, sf.G, sf.rhs, sf.L, sf.t, dyn);
 }
 
@@ -30,8 +41,8 @@ __global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int
 {
     __shared__ SmemFixed sf;
     __shared__ int sidx;
-    extern __shared__ __align__(16) unsigned char dyn[];
-    BlockTeam tm{sf.red};
+    extern __shared__ __align__(128) unsigned char dyn[];
+    BlockTeam tm{sf.red, nullptr, sf.mbar, sf.ph, nullptr};
     for (;;) {
         if (threadIdx.x == 0) sidx = atomicAdd(queue, 1);
         __syncthreads();

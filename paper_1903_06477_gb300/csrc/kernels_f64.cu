@@ -1,10 +1,8 @@
-// kernels_f64.cu -- FP64 instantiation of the solver kernels.
+// kernels_f64.cu -- FP64 instantiation of the grid-team solver kernel.
 #include "kernels.cuh"
 
 namespace sscs {
 template const void* kgrid_ptr<double>();
-template const void* kblock_ptr<double>();
-template cudaError_t launch_block<double>(int, int, size_t, cudaStream_t, const Args<double>*, int, int*);
 
 cudaError_t launch_f2d(const float* in, double* out, long long n, cudaStream_t st)
 {

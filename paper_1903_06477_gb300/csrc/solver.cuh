@@ -35,8 +35,10 @@ struct DevSettings {
     int max_iters, ls_max, cg_max, check_every;
     double cg_rtol, aa_reg;
     double time_limit_ns;  // <= 0: none
-    int stall_iters;       // > 0: stop when max(pr,dr,gap) has not dropped 10% for this many iterations
+    int stall_iters;       // > 0: stop when ||Ru|| has not dropped 10% below its best for this many iterations
     int use_warm;
+    double switch_kkt;     // > 0: stop (hand over) once max(pr,dr,gap) <= switch_kkt
+    double cg_adapt;       // > 0: CG inside the loop also stops at ||res|| <= cg_adapt ||Ru||
 };
 
 struct DevState {
@@ -47,20 +49,39 @@ struct DevState {
     long long mat_passes;  // SpMV passes over A or A^T
 };
 
+// Sliced ELL with row sorting (SELL-H-sigma) and V lanes per row, H = 32 / V
+// rows per slice: element j of the slice's row r sits at ptr[s] + j*H + r,
+// so lane q*H + r of a warp reads element t*V + q of row r at
+// ptr[s] + 32 t + lane -- every load of a warp is one coalesced 32-element
+// segment, and each lane streams its own run of independent loads.
+template <typename T>
+struct Sell {
+    int rows, V, nslices;
+    const int* ptr;    // nslices + 1 offsets (multiples of 32)
+    const int* col;    // padded column indices
+    const T* val;      // padded values (0 in padding)
+    const int* perm;   // sorted position -> original row (nslices * H entries, -1 past the end)
+    const int* wbnd;   // grid team only: warp w owns slices [wbnd[w], wbnd[w+1]) (nnz-balanced), else null
+};
+
+constexpr int TMA_CH = 8;  // t-steps (of 32 elements) per staged chunk
+template <typename T>
+__host__ __device__ constexpr int tma_stage_bytes()
+{
+    return TMA_CH * 32 * (4 + (int)sizeof(T));
+}
+
 template <typename T>
 struct DevProb {
     int n, m;
-    const int *Ap, *Ai;
-    const T* Ax;  // CSR of A (m rows)
-    const int *Tp, *Ti;
-    const T* Tx;  // CSR of A^T (n rows)
+    Sell<T> A;   // A   (m rows)
+    Sell<T> AT;  // A^T (n rows)
     const T *b, *c;
     double nb, nc;
     int f, l, nq, ns;
     const int* q_off;  // nq+1 row offsets of the SOCs inside s
     const int* s_dim;  // ns PSD orders
     const int* s_off;  // ns row offsets of the PSD blocks inside s
-    int vecA, vecT;    // SpMV sub-warp widths
 };
 
 template <typename T>
@@ -77,7 +98,7 @@ struct DevWork {
     double *io_in, *io_out, *io_out2;      // N-vectors of the single-operator entries
     double* warm;                          // N: warm start (FP64)
     double *x_out, *y_out, *s_out, *u_out; // results (FP64)
-    double* partials;
+    double* partials;      // [2][KMAX][blocks] block partials, then [2][KMAX] results
     unsigned* bar;
     int* abort_flag;
     DevState* st;
@@ -93,93 +114,205 @@ struct Args {
 };
 
 // ---------------------------------------------------------------------------
-// sparse products: sub-warp groups of V lanes per row (V = 1..32)
+// sparse products on the sliced-ELL layout: warps of the team take slices in
+// turn; xf(c) supplies the gathered vector entry, epi(row, sum) consumes the
+// row result (only lanes q = 0 call it)
 // ---------------------------------------------------------------------------
-template <int V>
-__device__ __forceinline__ unsigned group_mask()
+template <typename T, class Team, class XF, class Epi>
+__device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf, Epi& epi)
 {
-    if constexpr (V == 32) return FULL_MASK;
-    else return ((1u << V) - 1u) << ((threadIdx.x & 31) & ~(V - 1));
-}
-
-template <int V, typename T, class Team, class Epi>
-__device__ __forceinline__ void spmv_v(const Team& tm, int rows, const int* rp, const int* ci, const T* val,
-                                       const T* x, Epi& epi)
-{
-    const int r = tm.rank();
-    const int lane = r & (V - 1);
-    const int ng = tm.size() / V;
-    const unsigned mask = group_mask<V>();
-    for (int row = r / V; row < rows; row += ng) {
-        const int s = ro(rp + row), e = ro(rp + row + 1);
+    const int H = 32 / S.V;
+    const int lane = threadIdx.x & 31;
+    const int nw = tm.size() >> 5;
+    const unsigned long long pol = evict_first_policy();
+    for (int s = tm.rank() >> 5; s < S.nslices; s += nw) {
+        const int p0 = ro(S.ptr + s);
+        const int tc = (ro(S.ptr + s + 1) - p0) >> 5;
+        const int* cp = S.col + p0 + lane;
+        const T* vp = S.val + p0 + lane;
         T a0 = 0, a1 = 0;
-        int k = s + lane;
-        for (; k + V < e; k += 2 * V) {
-            const int c0 = ro(ci + k), c1 = ro(ci + k + V);
-            const T v0 = ro(val + k), v1 = ro(val + k + V);
-            a0 += v0 * x[c0];
-            a1 += v1 * x[c1];
+        int t = 0;
+        for (; t + 4 <= tc; t += 4) {
+            const int c0 = ld_stream(cp + 32 * t, pol), c1 = ld_stream(cp + 32 * (t + 1), pol),
+                      c2 = ld_stream(cp + 32 * (t + 2), pol), c3 = ld_stream(cp + 32 * (t + 3), pol);
+            const T v0 = ld_stream(vp + 32 * t, pol), v1 = ld_stream(vp + 32 * (t + 1), pol),
+                    v2 = ld_stream(vp + 32 * (t + 2), pol), v3 = ld_stream(vp + 32 * (t + 3), pol);
+            const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
+            a0 += v0 * x0;
+            a1 += v1 * x1;
+            a0 += v2 * x2;
+            a1 += v3 * x3;
         }
-        if (k < e) a0 += ro(val + k) * x[ro(ci + k)];
+        for (; t < tc; ++t) a0 += ld_stream(vp + 32 * t, pol) * xf(ld_stream(cp + 32 * t, pol));
         T acc = a0 + a1;
-#pragma unroll
-        for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
-        if (lane == 0) epi(row, acc);
+        for (int o = H; o < 32; o <<= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        const int pos = s * H + lane;
+        if (lane < H && pos < S.rows) epi(ro(S.perm + pos), acc);
     }
 }
 
-template <int V, typename T, class Team, class Epi>
-__device__ __forceinline__ void spmv2_v(const Team& tm, int rows, const int* rp, const int* ci, const T* val,
-                                        const T* x1, const T* x2, Epi& epi)
+template <typename T, class Team, class XF1, class XF2, class Epi>
+__device__ __forceinline__ void sell2_v(const Team& tm, const Sell<T>& S, XF1& xf1, XF2& xf2, Epi& epi)
 {
-    const int r = tm.rank();
-    const int lane = r & (V - 1);
-    const int ng = tm.size() / V;
-    const unsigned mask = group_mask<V>();
-    for (int row = r / V; row < rows; row += ng) {
-        const int s = ro(rp + row), e = ro(rp + row + 1);
-        T a1 = 0, a2 = 0;
-        for (int k = s + lane; k < e; k += V) {
-            const int c = ro(ci + k);
-            const T v = ro(val + k);
-            a1 += v * x1[c];
-            a2 += v * x2[c];
+    const int H = 32 / S.V;
+    const int lane = threadIdx.x & 31;
+    const int nw = tm.size() >> 5;
+    const unsigned long long pol = evict_first_policy();
+    for (int s = tm.rank() >> 5; s < S.nslices; s += nw) {
+        const int p0 = ro(S.ptr + s);
+        const int tc = (ro(S.ptr + s + 1) - p0) >> 5;
+        const int* cp = S.col + p0 + lane;
+        const T* vp = S.val + p0 + lane;
+        T a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+        int t = 0;
+        for (; t + 2 <= tc; t += 2) {
+            const int c0 = ld_stream(cp + 32 * t, pol), c1 = ld_stream(cp + 32 * (t + 1), pol);
+            const T v0 = ld_stream(vp + 32 * t, pol), v1 = ld_stream(vp + 32 * (t + 1), pol);
+            a1 += v0 * xf1(c0);
+            a2 += v0 * xf2(c0);
+            b1 += v1 * xf1(c1);
+            b2 += v1 * xf2(c1);
+        }
+        if (t < tc) {
+            const int c0 = ld_stream(cp + 32 * t, pol);
+            const T v0 = ld_stream(vp + 32 * t, pol);
+            a1 += v0 * xf1(c0);
+            a2 += v0 * xf2(c0);
+        }
+        a1 += b1;
+        a2 += b2;
+        for (int o = H; o < 32; o <<= 1) {
+            a1 += __shfl_xor_sync(FULL_MASK, a1, o);
+            a2 += __shfl_xor_sync(FULL_MASK, a2, o);
+        }
+        const int pos = s * H + lane;
+        if (lane < H && pos < S.rows) epi(ro(S.perm + pos), a1, a2);
+    }
+}
+
+// Sparse product with the matrix stream staged through shared memory by TMA
+// bulk copies: each warp owns a contiguous, nnz-balanced run of slices,
+// copies it in chunks of TMA_CH t-steps into a two-stage buffer (one
+// mbarrier per stage) and computes chunk k while chunk k+1 is in flight, so
+// the HBM stream never waits on the gathers.  Waits are bounded: on timeout
+// the abort flag is set, the warp waits (bounded) for its other copy and
+// leaves the product unfinished.
+template <typename T, class Team, class XF, class Epi>
+__device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& xf, Epi& epi)
+{
+    const int H = 32 / S.V;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = tm.rank() >> 5;
+    const int s0 = ro(S.wbnd + gw), s1 = ro(S.wbnd + gw + 1);
+    if (s0 >= s1) return;
+    const int e0 = ro(S.ptr + s0);
+    const int total_t = (ro(S.ptr + s1) - e0) >> 5;
+    constexpr int SB = tma_stage_bytes<T>();
+    unsigned char* wbuf = tm.stage + (size_t)wib * 2 * SB;
+    const unsigned bar0 = smem_addr(&tm.mbar[2 * wib]), bar1 = smem_addr(&tm.mbar[2 * wib + 1]);
+    unsigned ph = tm.ph[wib];
+    const unsigned long long pol = evict_first_policy();
+    const int nch = (total_t + TMA_CH - 1) / TMA_CH;
+    auto issue = [&](int k) {
+        const int t_lo = k * TMA_CH;
+        const int nt = min(TMA_CH, total_t - t_lo);
+        unsigned char* dst = wbuf + (k & 1) * SB;
+        const unsigned bar = (k & 1) ? bar1 : bar0;
+        const unsigned bc = (unsigned)nt * 32u * 4u, bv = (unsigned)nt * 32u * (unsigned)sizeof(T);
+        fence_proxy_async();
+        mbar_expect_tx(bar, bc + bv);
+        tma_load_1d(smem_addr(dst), S.col + e0 + 32 * t_lo, bc, bar, pol);
+        tma_load_1d(smem_addr(dst + TMA_CH * 32 * 4), S.val + e0 + 32 * t_lo, bv, bar, pol);
+    };
+    auto finalize = [&](int sl, T a) {
+        for (int o = H; o < 32; o <<= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
+        const int pos = sl * H + lane;
+        if (lane < H && pos < S.rows) epi(ro(S.perm + pos), a);
+    };
+    if (nch > 0 && lane == 0) issue(0);
+    int cur = s0;
+    int bound = (ro(S.ptr + cur + 1) - e0) >> 5;
+    T acc = 0;
+    for (int k = 0; k < nch; ++k) {
+        const bool more = k + 1 < nch;
+        if (more) {
+            __syncwarp();
+            if (lane == 0) issue(k + 1);
+        }
+        const unsigned bar = (k & 1) ? bar1 : bar0;
+        bool ok = mbar_wait(bar, (ph >> (k & 1)) & 1u, tm.abort_flag);
+        ok = __all_sync(FULL_MASK, ok);
+        ph ^= 1u << (k & 1);
+        if (!ok) {
+            if (more) {
+                const unsigned obar = (k & 1) ? bar0 : bar1;
+                mbar_wait(obar, (ph >> ((k + 1) & 1)) & 1u, nullptr);
+                ph ^= 1u << ((k + 1) & 1);
+            }
+            if (lane == 0) tm.ph[wib] = ph;
+            __syncwarp();
+            return;
+        }
+        const int t_lo = k * TMA_CH;
+        const int nt = min(TMA_CH, total_t - t_lo);
+        const int* sc = (const int*)(wbuf + (k & 1) * SB);
+        const T* sv = (const T*)(wbuf + (k & 1) * SB + TMA_CH * 32 * 4);
+        T prod[TMA_CH];
+#pragma unroll
+        for (int t = 0; t < TMA_CH; ++t) {
+            const int c = t < nt ? sc[t * 32 + lane] : 0;
+            const T v = t < nt ? sv[t * 32 + lane] : T(0);
+            prod[t] = v * xf(c);
         }
 #pragma unroll
-        for (int o = V / 2; o > 0; o >>= 1) {
-            a1 += __shfl_xor_sync(mask, a1, o);
-            a2 += __shfl_xor_sync(mask, a2, o);
+        for (int t = 0; t < TMA_CH; ++t) {
+            if (t < nt) {
+                const int tg = t_lo + t;
+                while (tg == bound) {
+                    finalize(cur, acc);
+                    acc = 0;
+                    ++cur;
+                    bound = (ro(S.ptr + cur + 1) - e0) >> 5;
+                }
+                acc += prod[t];
+            }
         }
-        if (lane == 0) epi(row, a1, a2);
     }
+    while (cur < s1) {
+        finalize(cur, acc);
+        acc = 0;
+        ++cur;
+    }
+    if (lane == 0) tm.ph[wib] = ph;
+    __syncwarp();
+}
+
+template <typename T, class Team, class XF, class Epi>
+__device__ __forceinline__ void spmv_f(const Team& tm, const Sell<T>& S, XF xf, Epi epi)
+{
+    if (S.wbnd != nullptr && tm.stage != nullptr)
+        sell_tma(tm, S, xf, epi);
+    else
+        sell_v(tm, S, xf, epi);
 }
 
 template <typename T, class Team, class Epi>
-__device__ void spmv(const Team& tm, int V, int rows, const int* rp, const int* ci, const T* val, const T* x, Epi epi)
+__device__ __forceinline__ void spmv(const Team& tm, const Sell<T>& S, const T* x, Epi epi)
 {
-    switch (V) {
-        case 1: spmv_v<1>(tm, rows, rp, ci, val, x, epi); break;
-        case 2: spmv_v<2>(tm, rows, rp, ci, val, x, epi); break;
-        case 4: spmv_v<4>(tm, rows, rp, ci, val, x, epi); break;
-        case 8: spmv_v<8>(tm, rows, rp, ci, val, x, epi); break;
-        case 16: spmv_v<16>(tm, rows, rp, ci, val, x, epi); break;
-        default: spmv_v<32>(tm, rows, rp, ci, val, x, epi); break;
-    }
+    auto f = [x](int c) { return x[c]; };
+    spmv_f(tm, S, f, epi);
 }
 
 template <typename T, class Team, class Epi>
-__device__ void spmv2(const Team& tm, int V, int rows, const int* rp, const int* ci, const T* val, const T* x1,
-                      const T* x2, Epi epi)
+__device__ __forceinline__ void spmv2(const Team& tm, const Sell<T>& S, const T* x1, const T* x2, Epi epi)
 {
-    switch (V) {
-        case 1: spmv2_v<1>(tm, rows, rp, ci, val, x1, x2, epi); break;
-        case 2: spmv2_v<2>(tm, rows, rp, ci, val, x1, x2, epi); break;
-        case 4: spmv2_v<4>(tm, rows, rp, ci, val, x1, x2, epi); break;
-        case 8: spmv2_v<8>(tm, rows, rp, ci, val, x1, x2, epi); break;
-        case 16: spmv2_v<16>(tm, rows, rp, ci, val, x1, x2, epi); break;
-        default: spmv2_v<32>(tm, rows, rp, ci, val, x1, x2, epi); break;
-    }
+    auto f1 = [x1](int c) { return x1[c]; };
+    auto f2 = [x2](int c) { return x2[c]; };
+    sell2_v(tm, S, f1, f2, epi);
 }
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
 // ---------------------------------------------------------------------------
 // M^{-1}(a, e) for M = [I A^T; -A I]: x = (I + A^T A)^{-1}(a - A^T e) by CG
@@ -189,21 +322,19 @@ __device__ void spmv2(const Team& tm, int V, int rows, const int* rp, const int*
 // ---------------------------------------------------------------------------
 template <typename T, class Team>
 __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T* a, const T* e, T* x, double rtol,
-                    int cg_max, double& htp)
+                    int cg_max, double& htp, double atol = 0.0)
 {
-    const int n = P.n, m = P.m;
+    const int n = P.n;
     T* tmv = W.tm;
     T* r = W.cr;
-    T* p = W.cp;
     T* q = W.cq;
-    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, x, [&](int i, T s) { tmv[i] = s; });
+    spmv(tm, P.A, x, [&](int i, T s) { tmv[i] = s; });
     tm.sync();
     T acc_b = 0, acc_r = 0;
-    spmv2(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, e, tmv, [&](int j, T s1, T s2) {
+    spmv2(tm, P.AT, e, tmv, [&](int j, T s1, T s2) {
         const T rhs = a[j] - s1;
         const T res = rhs - x[j] - s2;
         r[j] = res;
-        p[j] = res;
         acc_b += rhs * rhs;
         acc_r += res * res;
     });
@@ -211,46 +342,66 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     tm.reduce(red2);
     const double rhs2 = red2[0];
     double rr = red2[1];
-    const double tol = rtol * sqrt(rhs2);
+    const double tol = fmax(rtol * sqrt(rhs2), atol);
     int it = 0;
     if (rhs2 == 0.0) {
         for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
         tm.sync();
     } else if (sqrt(rr) > tol) {
+        // CG with one reduction per iteration: <p,q>, <r,q>, <q,q> are reduced
+        // together, ||r - alpha q||^2 = rr - 2 alpha <r,q> + alpha^2 <q,q> gives
+        // beta, and x, r, p are updated in one pass.  The exact ||r||^2 of the
+        // updated r rides along with the next reduction and replaces the
+        // recurrence value before it is used for alpha.
+        T* p = W.cp;
+        for (int j = tm.rank(); j < n; j += tm.size()) p[j] = r[j];
+        tm.sync();
+        T rr_part = 0;
+        bool have_part = false;
         while (it < cg_max) {
             if (tm.aborted()) break;
-            spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, p, [&](int i, T s) { tmv[i] = s; });
+            spmv(tm, P.A, p, [&](int i, T s) { tmv[i] = s; });
             tm.sync();
-            T pq = 0;
-            spmv(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, tmv, [&](int j, T s) {
+            T pq = 0, rq = 0, qq = 0;
+            spmv(tm, P.AT, tmv, [&](int j, T s) {
                 const T qj = p[j] + s;
                 q[j] = qj;
                 pq += p[j] * qj;
+                rq += r[j] * qj;
+                qq += qj * qj;
             });
-            double red1[1] = {(double)pq};
-            tm.reduce(red1);
-            const double alpha = rr / red1[0];
-            const T ta = (T)alpha;
-            T rn = 0;
-            for (int j = tm.rank(); j < n; j += tm.size()) {
-                x[j] += ta * p[j];
-                const T rj = r[j] - ta * q[j];
-                r[j] = rj;
-                rn += rj * rj;
-            }
-            double red3[1] = {(double)rn};
-            tm.reduce(red3);
+            double red[4] = {(double)pq, (double)rq, (double)qq, (double)rr_part};
+            tm.reduce(red);
+            if (have_part) rr = red[3];
+            const double alpha = rr / red[0];
+            double rr_new = rr - 2.0 * alpha * red[1] + alpha * alpha * red[2];
+            if (rr_new < 0.0) rr_new = 0.0;
             ++it;
-            if (!(sqrt(red3[0]) > tol)) break;
-            const T tb = (T)(red3[0] / rr);
-            rr = red3[0];
-            for (int j = tm.rank(); j < n; j += tm.size()) p[j] = r[j] + tb * p[j];
+            const bool done = !(sqrt(rr_new) > tol) || it >= cg_max;
+            const T ta = (T)alpha;
+            const T tb = (T)(rr_new / rr);
+            rr_part = 0;
+            if (done) {
+                for (int j = tm.rank(); j < n; j += tm.size()) x[j] += ta * p[j];
+            } else {
+                for (int j = tm.rank(); j < n; j += tm.size()) {
+                    const T pj = p[j];
+                    x[j] += ta * pj;
+                    const T rj = r[j] - ta * q[j];
+                    r[j] = rj;
+                    p[j] = rj + tb * pj;
+                    rr_part += rj * rj;
+                }
+            }
+            have_part = true;
+            rr = rr_new;
             tm.sync();
+            if (done) break;
         }
     }
     T hb = 0, hc = 0;
     T* py = W.py;
-    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, x, [&](int i, T s) {
+    spmv(tm, P.A, x, [&](int i, T s) {
         const T yi = e[i] + s;
         py[i] = yi;
         hb += ro(P.b + i) * yi;
@@ -267,13 +418,13 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
 // r and out must not share storage of the bulk part.
 template <typename T, class Team>
 __device__ int linsys(Team& tm, const DevProb<T>& P, const DevWork<T>& W, HV<T> r, HV<T> out, int slot,
-                      double rtol, int cg_max, double hg)
+                      double rtol, int cg_max, double hg, double atol = 0.0)
 {
     const int n = P.n, m = P.m;
     const double rtau = *r.t;
     T* x = W.ws[slot];
     double htp;
-    const int it = minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp);
+    const int it = minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol);
     const double tau = (rtau + htp) / (1.0 + hg);
     const T tt = (T)tau;
     for (int i = tm.rank(); i < n; i += tm.size()) out.v[i] = x[i] - tt * W.g[i];
@@ -652,8 +803,8 @@ __device__ int termination(Team& tm, const DevProb<T>& P, const DevWork<T>& W, d
     const double taub = *W.ub.t;
     T* tmv = W.tm;
     T* tnv = W.tn;
-    spmv(tm, P.vecA, m, P.Ap, P.Ai, P.Ax, chib, [&](int i, T s) { tmv[i] = s; });
-    spmv(tm, P.vecT, n, P.Tp, P.Ti, P.Tx, psib, [&](int j, T s) { tnv[j] = s; });
+    spmv(tm, P.A, chib, [&](int i, T s) { tmv[i] = s; });
+    spmv(tm, P.AT, psib, [&](int j, T s) { tnv[j] = s; });
     tm.sync();
     if (tm.leader()) W.st->mat_passes += 2;
     const bool pos = taub > 0.0;
@@ -1076,10 +1227,16 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
                 need_final_check = false;
                 break;
             }
+            if (S.switch_kkt > 0.0 && fmax(to.pr, fmax(to.dr, to.gap)) <= S.switch_kkt) {
+                status = ST_STALLED;  // hand over to the FP64 phase
+                need_final_check = false;
+                break;
+            }
             if (S.stall_iters > 0) {
-                const double kkt = fmax(to.pr, fmax(to.dr, to.gap));
-                if (kkt < 0.9 * best_kkt) {
-                    best_kkt = kkt;
+                // FP32 phase of SCS_MIXED: stop once ||Ru|| has not dropped 10% below
+                // its best value for stall_iters iterations (the FP32 floor)
+                if (nRu < 0.9 * best_kkt) {
+                    best_kkt = nRu;
                     best_it = nu;
                 } else if (nu - best_it >= S.stall_iters) {
                     status = ST_STALLED;
@@ -1098,7 +1255,8 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             if (tm.leader()) *W.d.t = 0.0;
             tm.sync();
         }
-        cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg);
+        const double atol = S.cg_adapt > 0.0 ? S.cg_adapt * nRu : 0.0;
+        cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg, atol);
         if (nRu <= S.c0 * eta) {
             // K0
             eta = nRu;
@@ -1172,7 +1330,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
                     }
                     tm.reduce(red2);
                     nz2 = red2[0];
-                    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+                    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol);
                     OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
                     project_pass(tm, P, opr, psd);
                     double red3[1] = {(double)opr.acc0};

@@ -63,13 +63,87 @@ struct HostProb {
     std::vector<int> q, s, q_off, s_off;
     double nb = 0, nc = 0;
     int vecA = 32, vecT = 32;
+    struct Sell {
+        int rows = 0, V = 1, nslices = 0;
+        std::vector<int> ptr, col, perm;
+        std::vector<double> val;
+        std::vector<int> wbnd;  // per-warp slice ranges for the TMA-staged product (grid team)
+    } SA, ST;
 };
 
-static int pick_vec(long long nnz, int rows)
+// nnz-balanced contiguous slice ranges for W warps: warp w owns [b[w], b[w+1])
+static void warp_bounds(HostProb::Sell& S, int W)
+{
+    S.wbnd.assign(W + 1, 0);
+    const long long total = S.ptr.back();
+    for (int w = 0; w <= W; ++w) {
+        const long long target = total * w / W;
+        S.wbnd[w] = (int)(std::lower_bound(S.ptr.begin(), S.ptr.end(), target) - S.ptr.begin());
+        if (S.wbnd[w] > S.nslices) S.wbnd[w] = S.nslices;
+    }
+    S.wbnd[W] = S.nslices;
+}
+
+// Sliced ELL (SELL-H-sigma) from CSR: rows sorted by length (descending,
+// stable) inside windows of sigma rows, H = 32 / V rows per slice, slice
+// width = longest row rounded up to a multiple of V; padding has value 0 and
+// repeats the row's last column (or 0 for an empty row).
+static void build_sell(int rows, const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<double>& vx,
+                       int V, HostProb::Sell& S)
+{
+    const int H = 32 / V;
+    const int sigma = 4096;
+    S.rows = rows;
+    S.V = V;
+    S.nslices = (rows + H - 1) / H;
+    std::vector<int> order(rows);
+    std::iota(order.begin(), order.end(), 0);
+    for (int w0 = 0; w0 < rows; w0 += sigma) {
+        const int w1 = std::min(rows, w0 + sigma);
+        std::stable_sort(order.begin() + w0, order.begin() + w1,
+                         [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    }
+    S.perm.assign((size_t)S.nslices * H, -1);
+    for (int i = 0; i < rows; ++i) S.perm[i] = order[i];
+    S.ptr.assign(S.nslices + 1, 0);
+    for (int s = 0; s < S.nslices; ++s) {
+        int w = 0;
+        for (int r = 0; r < H; ++r) {
+            const int pos = s * H + r;
+            if (pos < rows) w = std::max(w, rp[order[pos] + 1] - rp[order[pos]]);
+        }
+        w = (w + V - 1) / V * V;
+        S.ptr[s + 1] = S.ptr[s] + w * H;
+    }
+    const size_t tot = (size_t)S.ptr[S.nslices];
+    S.col.assign(tot, 0);
+    S.val.assign(tot, 0.0);
+    for (int s = 0; s < S.nslices; ++s) {
+        const int w = (S.ptr[s + 1] - S.ptr[s]) / H;
+        for (int r = 0; r < H; ++r) {
+            const int pos = s * H + r;
+            if (pos >= rows) continue;
+            const int row = order[pos];
+            const int b = rp[row], len = rp[row + 1] - b;
+            const int padc = len > 0 ? ci[b + len - 1] : 0;
+            for (int j = 0; j < w; ++j) {
+                const size_t idx = (size_t)S.ptr[s] + (size_t)j * H + r;
+                if (j < len) {
+                    S.col[idx] = ci[b + j];
+                    S.val[idx] = vx[b + j];
+                } else {
+                    S.col[idx] = padc;
+                }
+            }
+        }
+    }
+}
+
+static int pick_lanes(long long nnz, int rows)
 {
     const double avg = rows > 0 ? (double)nnz / rows : 0.0;
     int v = 1;
-    while (v < 32 && v < avg / 2.0) v <<= 1;
+    while (v < 32 && 2.0 * v * 8.0 <= avg) v <<= 1;  // about 8 or more elements per lane
     return v;
 }
 
@@ -153,8 +227,21 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err)
     s = 0;
     for (int j = 0; j < n; ++j) s += H.c[j] * H.c[j];
     H.nc = std::sqrt(s);
-    H.vecA = pick_vec(nnz, m);
-    H.vecT = pick_vec(nnz, n);
+    H.vecA = pick_lanes(nnz, m);
+    H.vecT = pick_lanes(nnz, n);
+    build_sell(m, H.Ap, H.Ai, H.Ax, H.vecA, H.SA);
+    build_sell(n, H.Tp, H.Ti, H.Tx, H.vecT, H.ST);
+    // the CSR copies are only needed to build the sliced layouts
+    std::vector<int>().swap(H.Ap);
+    std::vector<int>().swap(H.Ai);
+    std::vector<int>().swap(H.Tp);
+    std::vector<int>().swap(H.Ti);
+    std::vector<double>().swap(H.Ax);
+    std::vector<double>().swap(H.Tx);
+    if ((long long)H.SA.ptr.back() >= (1ll << 31) || (long long)H.ST.ptr.back() >= (1ll << 31)) {
+        set_err(err, "padded matrix too large");
+        return SCS_EINVAL;
+    }
     return SCS_OK;
 }
 
@@ -197,17 +284,25 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     const long long nnz = H.nnz;
     P.n = n;
     P.m = m;
+    auto lay_sell = [&](const HostProb::Sell& hs, Sell<T>& ds) {
+        ds.rows = hs.rows;
+        ds.V = hs.V;
+        ds.nslices = hs.nslices;
+        if (shared_idx == nullptr) {
+            ds.ptr = A.take<int>(hs.ptr.size());
+            ds.col = A.take<int>(hs.col.size());
+            ds.perm = A.take<int>(hs.perm.size());
+            ds.wbnd = hs.wbnd.empty() ? nullptr : A.take<int>(hs.wbnd.size());
+        }
+        ds.val = A.take<T>(hs.val.size());
+    };
+    lay_sell(H.SA, P.A);
+    lay_sell(H.ST, P.AT);
     if (shared_idx == nullptr) {
-        P.Ap = A.take<int>(m + 1);
-        P.Ai = A.take<int>(nnz);
-        P.Tp = A.take<int>(n + 1);
-        P.Ti = A.take<int>(nnz);
         P.q_off = A.take<int>(H.q_off.size());
         P.s_dim = A.take<int>(H.s.size());
         P.s_off = A.take<int>(H.s_off.size());
     }
-    P.Ax = A.take<T>(nnz);
-    P.Tx = A.take<T>(nnz);
     P.b = A.take<T>(m);
     P.c = A.take<T>(n);
     P.nb = H.nb;
@@ -216,8 +311,6 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     P.l = H.l;
     P.nq = (int)H.q.size();
     P.ns = (int)H.s.size();
-    P.vecA = H.vecA;
-    P.vecT = H.vecT;
     double* taus = A.take<double>(16);
     HV<T>* hvs[] = {&W.u, &W.ut, &W.ub, &W.Ru, &W.d, &W.dt, &W.wb, &W.Rw, &W.zp, &W.xip, &W.zt};
     for (int i = 0; i < 11; ++i) {
@@ -246,7 +339,7 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     W.y_out = A.take<double>(m);
     W.s_out = A.take<double>(m);
     W.u_out = A.take<double>(nm + 1);
-    W.partials = A.take<double>((size_t)2 * KMAX * std::max(max_blocks, 1));
+    W.partials = A.take<double>((size_t)2 * KMAX * std::max(max_blocks, 1) + 2 * KMAX);
     W.bar = A.take<unsigned>(4);
     W.abort_flag = A.take<int>(4);
     W.st = A.take<DevState>(1);
@@ -255,34 +348,35 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
 template <typename T>
 static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t st, char* err)
 {
-    if (idx) {
-        CU(cudaMemcpyAsync((void*)P.Ap, H.Ap.data(), sizeof(int) * H.Ap.size(), cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.Ai, H.Ai.data(), sizeof(int) * H.Ai.size(), cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.Tp, H.Tp.data(), sizeof(int) * H.Tp.size(), cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.Ti, H.Ti.data(), sizeof(int) * H.Ti.size(), cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.q_off, H.q_off.data(), sizeof(int) * H.q_off.size(), cudaMemcpyHostToDevice, st), err);
-        if (!H.s.empty()) {
-            CU(cudaMemcpyAsync((void*)P.s_dim, H.s.data(), sizeof(int) * H.s.size(), cudaMemcpyHostToDevice, st), err);
-            CU(cudaMemcpyAsync((void*)P.s_off, H.s_off.data(), sizeof(int) * H.s_off.size(), cudaMemcpyHostToDevice, st), err);
-        }
-    }
-    if (sizeof(T) == sizeof(double)) {
-        CU(cudaMemcpyAsync((void*)P.Ax, H.Ax.data(), sizeof(double) * H.nnz, cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.Tx, H.Tx.data(), sizeof(double) * H.nnz, cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.b, H.b.data(), sizeof(double) * H.m, cudaMemcpyHostToDevice, st), err);
-        CU(cudaMemcpyAsync((void*)P.c, H.c.data(), sizeof(double) * H.n, cudaMemcpyHostToDevice, st), err);
-    } else {
-        std::vector<float> tmp;
-        auto put = [&](const std::vector<double>& v, const T* dst) -> int {
+    auto put_i = [&](const std::vector<int>& v, const int* dst) -> int {
+        if (!v.empty()) CU(cudaMemcpyAsync((void*)dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st), err);
+        return SCS_OK;
+    };
+    std::vector<T> tmp;
+    auto put_t = [&](const std::vector<double>& v, const T* dst) -> int {
+        if (v.empty()) return SCS_OK;
+        if (sizeof(T) == sizeof(double)) {
+            CU(cudaMemcpyAsync((void*)dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, st), err);
+        } else {
             tmp.resize(v.size());
-            for (size_t i = 0; i < v.size(); ++i) tmp[i] = (float)v[i];
-            CU(cudaMemcpyAsync((void*)dst, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice, st), err);
+            for (size_t i = 0; i < v.size(); ++i) tmp[i] = (T)v[i];
+            CU(cudaMemcpyAsync((void*)dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice, st), err);
             CU(cudaStreamSynchronize(st), err);  // tmp is reused
-            return SCS_OK;
-        };
-        int rc;
-        if ((rc = put(H.Ax, P.Ax)) || (rc = put(H.Tx, P.Tx)) || (rc = put(H.b, P.b)) || (rc = put(H.c, P.c))) return rc;
+        }
+        return SCS_OK;
+    };
+    int rc;
+    if (idx) {
+        if ((rc = put_i(H.SA.ptr, P.A.ptr)) || (rc = put_i(H.SA.col, P.A.col)) || (rc = put_i(H.SA.perm, P.A.perm)) ||
+            (rc = put_i(H.ST.ptr, P.AT.ptr)) || (rc = put_i(H.ST.col, P.AT.col)) || (rc = put_i(H.ST.perm, P.AT.perm)) ||
+            (rc = put_i(H.SA.wbnd, P.A.wbnd)) || (rc = put_i(H.ST.wbnd, P.AT.wbnd)) ||
+            (rc = put_i(H.q_off, P.q_off)) || (rc = put_i(H.s, P.s_dim)) || (rc = put_i(H.s_off, P.s_off)))
+            return rc;
     }
+    if ((rc = put_t(H.SA.val, P.A.val)) || (rc = put_t(H.ST.val, P.AT.val)) || (rc = put_t(H.b, P.b)) ||
+        (rc = put_t(H.c, P.c)))
+        return rc;
+    CU(cudaStreamSynchronize(st), err);
     return SCS_OK;
 }
 
@@ -307,6 +401,8 @@ static DevSettings dev_settings(const scs_settings* S)
     D.time_limit_ns = S->time_limit_s > 0 ? S->time_limit_s * 1e9 : 0.0;
     D.stall_iters = 0;
     D.use_warm = 0;
+    D.switch_kkt = 0.0;
+    D.cg_adapt = S->cg_adapt;
     return D;
 }
 
@@ -319,9 +415,11 @@ struct DevInfo {
 };
 
 template <typename T>
-static size_t dyn_smem(const HostProb& H)
+static size_t dyn_smem(const HostProb& H, int threads, bool tma)
 {
-    return H.s.empty() ? 0 : psd_smem_bytes<T>();
+    const size_t psd = H.s.empty() ? 0 : psd_smem_bytes<T>();
+    const size_t stage = tma ? (size_t)(threads / 32) * 2 * tma_stage_bytes<T>() : 0;
+    return std::max(psd, stage);
 }
 
 template <typename T>
@@ -405,6 +503,8 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->mixed_cg_rtol = 1e-6;
     o->mixed_stall = 50;
     o->mixed_max_iters = 10000;
+    o->mixed_switch = 0.0;
+    o->cg_adapt = 0.0;
     return SCS_OK;
 }
 
@@ -456,10 +556,11 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     if (team == SCS_TEAM_AUTO) team = (work_size < 150000 || !coop) ? SCS_TEAM_BLOCK : SCS_TEAM_GRID;
     if (team == SCS_TEAM_GRID && !coop) { set_err(w->err, "device lacks cooperative launch"); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
     w->D.team = team;
-    w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? 512 : 256);
+    w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? 1024 : 256);
     w->has32 = settings->precision == SCS_MIXED;
-    w->D.dyn64 = dyn_smem<double>(H);
-    w->D.dyn32 = w->has32 ? dyn_smem<float>(H) : 0;
+    const bool tma = team == SCS_TEAM_GRID;
+    w->D.dyn64 = dyn_smem<double>(H, w->D.threads, tma);
+    w->D.dyn32 = w->has32 ? dyn_smem<float>(H, w->D.threads, tma) : 0;
     int rc2 = config_kernels<double>(w->D.dyn64, w->err);
     if (!rc2 && w->has32) rc2 = config_kernels<float>(w->D.dyn32, w->err);
     if (rc2) { memcpy(g_err, w->err, 512); delete w; return rc2; }
@@ -473,6 +574,8 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
         }
         if (nb < 1) { set_err(w->err, "solver kernel cannot be resident with %d threads", w->D.threads); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
         w->D.grid = w->D.sms * std::min(nb, 4);
+        warp_bounds(w->H.SA, w->D.grid * (w->D.threads / 32));
+        warp_bounds(w->H.ST, w->D.grid * (w->D.threads / 32));
     } else {
         w->D.grid = 1;
     }
@@ -494,10 +597,14 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     lay_out<double>(A, H, mem, w->D.grid, w->P64, w->W64, nullptr);
     if (w->has32) {
         lay_out<float>(A, H, mem, w->D.grid, w->P32, w->W32, (const int*)1);
-        w->P32.Ap = w->P64.Ap;
-        w->P32.Ai = w->P64.Ai;
-        w->P32.Tp = w->P64.Tp;
-        w->P32.Ti = w->P64.Ti;
+        w->P32.A.ptr = w->P64.A.ptr;
+        w->P32.A.col = w->P64.A.col;
+        w->P32.A.perm = w->P64.A.perm;
+        w->P32.AT.ptr = w->P64.AT.ptr;
+        w->P32.AT.col = w->P64.AT.col;
+        w->P32.AT.perm = w->P64.AT.perm;
+        w->P32.A.wbnd = w->P64.A.wbnd;
+        w->P32.AT.wbnd = w->P64.AT.wbnd;
         w->P32.q_off = w->P64.q_off;
         w->P32.s_dim = w->P64.s_dim;
         w->P32.s_off = w->P64.s_off;
@@ -584,6 +691,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         DevSettings S32 = S;
         S32.cg_rtol = w->S.mixed_cg_rtol > 0 ? w->S.mixed_cg_rtol : 1e-6;
         S32.stall_iters = w->S.mixed_stall;
+        S32.switch_kkt = w->S.mixed_switch;
         S32.max_iters = w->S.mixed_max_iters > 0 ? std::min(w->S.mixed_max_iters, w->S.max_iters) : w->S.max_iters;
         if (S.use_warm) CU(cudaMemcpyAsync(w->W32.warm, w->W64.warm, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
         Args<float> a32 = make_args(w->P32, w->W32, S32, MODE_SOLVE);
@@ -837,7 +945,9 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
             lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1);
             DevProb<float>& p = b->a32[qi].P;
             const DevProb<double>& q = b->a64[qi].P;
-            p.Ap = q.Ap; p.Ai = q.Ai; p.Tp = q.Tp; p.Ti = q.Ti; p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
+            p.A.ptr = q.A.ptr; p.A.col = q.A.col; p.A.perm = q.A.perm;
+            p.AT.ptr = q.AT.ptr; p.AT.col = q.AT.col; p.AT.perm = q.AT.perm;
+            p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
         }
     }
     b->d64 = A.take<Args<double>>(B);
@@ -888,6 +998,7 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
         DevSettings S32 = S;
         S32.cg_rtol = b->S.mixed_cg_rtol > 0 ? b->S.mixed_cg_rtol : 1e-6;
         S32.stall_iters = b->S.mixed_stall;
+        S32.switch_kkt = b->S.mixed_switch;
         S32.max_iters = b->S.mixed_max_iters > 0 ? std::min(b->S.mixed_max_iters, b->S.max_iters) : b->S.max_iters;
         if ((rc = batch_launch<float>(b, MODE_SOLVE, S32, b->d32, b->a32, b->dyn32))) return rc;
         for (int qi = 0; qi < b->B; ++qi) {

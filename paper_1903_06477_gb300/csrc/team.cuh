@@ -35,6 +35,10 @@ __device__ __forceinline__ void block_partial(double (&v)[K], double* red)
 
 struct BlockTeam {
     double* red;
+    unsigned char* stage;      // TMA staging (unused by this team: null)
+    unsigned long long* mbar;  // per-warp mbarriers
+    unsigned* ph;              // per-warp mbarrier phase bits
+    int* abort_flag;
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }
     __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
@@ -60,6 +64,9 @@ struct BlockTeam {
 
 struct GridTeam {
     double* red;          // shared memory
+    unsigned char* stage;      // dynamic shared memory: per-warp TMA staging (null when off)
+    unsigned long long* mbar;  // shared: 2 mbarriers per warp
+    unsigned* ph;              // shared: phase bits per warp
     double* partials;     // global, [2][KMAX][gridDim.x]
     unsigned* bar;        // global, [0] arrival count, [1] generation
     int* abort_flag;      // global
@@ -104,26 +111,70 @@ struct GridTeam {
         __syncthreads();
     }
 
+    // Team-wide sum of K values.  Every block writes its partial, then arrives
+    // at the grid barrier; the last block to arrive sums the partials in
+    // block order, publishes the K results and only then releases the
+    // barrier, so every block reads the same K numbers (deterministic).
     template <int K>
     __device__ void reduce(double (&v)[K])
     {
+        __shared__ int s_last;
         block_partial<K>(v, red);
         const int nw = blockDim.x >> 5;
         const int B = gridDim.x;
         double* P = partials + (size_t)parity * KMAX * B;
+        double* R = partials + (size_t)2 * KMAX * B + (size_t)parity * KMAX;
         if (threadIdx.x < K) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
             P[(size_t)threadIdx.x * B + blockIdx.x] = s;
         }
-        sync();
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int k = wid; k < K; k += nw) {
-            double s = 0.0;
-            for (int j = lane; j < B; j += 32) s += P[(size_t)k * B + j];
-            s = warp_sum(s);
-            if (lane == 0) red[MAX_WARPS * KMAX + k] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int last = 0;
+            volatile unsigned* vgen = bar + 1;
+            if (*(volatile int*)abort_flag == 0) {
+                const unsigned gen = *vgen;
+                __threadfence();
+                const unsigned prev = atomicAdd(bar, 1u);
+                if (prev == gridDim.x - 1) {
+                    __threadfence();
+                    last = 1;
+                } else {
+                    const unsigned long long t0 = gtimer();
+                    unsigned ns = 16;
+                    while (*vgen == gen) {
+                        if (*(volatile int*)abort_flag != 0) break;
+                        if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
+                            atomicExch(abort_flag, 1);
+                            break;
+                        }
+                        __nanosleep(ns);
+                        if (ns < 64) ns <<= 1;
+                    }
+                    __threadfence();
+                }
+            }
+            s_last = last;
         }
+        __syncthreads();
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (s_last) {
+            for (int k = wid; k < K; k += nw) {
+                double s = 0.0;
+                for (int j = lane; j < B; j += 32) s += __ldcg(P + (size_t)k * B + j);
+                s = warp_sum(s);
+                if (lane == 0) R[k] = s;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            }
+        }
+        if (threadIdx.x < K) red[MAX_WARPS * KMAX + threadIdx.x] = __ldcg(R + threadIdx.x);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = red[MAX_WARPS * KMAX + k];
