@@ -107,6 +107,7 @@ typedef struct {
     double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
+    int32_t spmv_path;      /* 0 or 1: direct streaming loads; 2: TMA-staged stream (grid team only) */
 } scs_settings;
 
 typedef struct {
@@ -164,6 +165,14 @@ int scs_linsys(scs_work *work, const double *r, double *out, int32_t slot);
 int scs_project_cone(scs_work *work, const double *v, double *out);
 /* Tu = u + Pi_C(2u~ - u) - u~ and Ru = u - Tu (Sec. 4.1-4.2); either may be NULL. */
 int scs_apply_T(scs_work *work, const double *u, double *Tu, double *Ru);
+
+/* Device-side timing (globaltimer between team barriers, inside one launch)
+ * of the solver's building blocks on this problem, for roofline measurement:
+ * ns[0] one product with A, ns[1] one with A^T, ns[2] one team barrier,
+ * ns[3] one team reduction, ns[4] one CG iteration; each averaged over reps.
+ * precision SCS_FP64 times the FP64 data; SCS_MIXED the FP32 copy (only on
+ * works set up with SCS_MIXED).  Overwrites the work's scratch vectors. */
+int scs_profile(scs_work *work, int32_t precision, int32_t reps, double *ns);
 
 /* Frees everything owned by work; NULL-safe. */
 void scs_finish(scs_work *work);

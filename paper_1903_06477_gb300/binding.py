@@ -42,7 +42,7 @@ class Settings(C.Structure):
         ("precision", C.c_int32), ("warm", C.c_int32), ("warm_u", C.c_void_p), ("verbose", C.c_int32),
         ("aa_reg", C.c_double), ("team", C.c_int32), ("threads", C.c_int32),
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
-        ("mixed_switch", C.c_double), ("cg_adapt", C.c_double),
+        ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
     ]
 
 
@@ -79,6 +79,7 @@ _SIGS = [
     ("scs_linsys", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("scs_finish", None, [C.c_void_p]),
     ("scs_last_error", C.c_char_p, [C.c_void_p]),
     ("scs_batch_setup", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,
@@ -225,6 +226,12 @@ class Work:
         out = np.empty(self.N)
         _check(lib().scs_project_cone(self.h, _ptr(v), _ptr(out)), self.h)
         return out
+
+    def profile(self, precision=FP64, reps=20):
+        """ns per A pass, A^T pass, barrier, reduction, CG iteration (device timer)."""
+        ns = np.zeros(5)
+        _check(lib().scs_profile(self.h, precision, reps, _ptr(ns)), self.h)
+        return dict(zip(("A", "AT", "barrier", "reduce", "cg_iter"), ns.tolist()))
 
     def apply_T(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)

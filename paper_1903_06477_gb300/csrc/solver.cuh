@@ -19,7 +19,7 @@ constexpr int MAXMEM = 64;   // direction memory cap (RB)
 constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared memory)
 constexpr int PSD_MAX = 64;  // largest PSD order
 
-enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4 };
+enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5 };
 enum { ST_SOLVED = 1, ST_INFEASIBLE = -1, ST_UNBOUNDED = -2, ST_MAX_ITERS = -3, ST_TIME_LIMIT = -4,
        ST_NUMERICAL = -5, ST_STALLED = -6 };
 
@@ -113,6 +113,9 @@ struct Args {
     int slot;
 };
 
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
 // ---------------------------------------------------------------------------
 // sparse products on the sliced-ELL layout: warps of the team take slices in
 // turn; xf(c) supplies the gathered vector entry, epi(row, sum) consumes the
@@ -138,10 +141,10 @@ __device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf,
             const T v0 = ld_stream(vp + 32 * t, pol), v1 = ld_stream(vp + 32 * (t + 1), pol),
                     v2 = ld_stream(vp + 32 * (t + 2), pol), v3 = ld_stream(vp + 32 * (t + 3), pol);
             const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
-            a0 += v0 * x0;
-            a1 += v1 * x1;
-            a0 += v2 * x2;
-            a1 += v3 * x3;
+            a0 = fmaT(v0, x0, a0);
+            a1 = fmaT(v1, x1, a1);
+            a0 = fmaT(v2, x2, a0);
+            a1 = fmaT(v3, x3, a1);
         }
         for (; t < tc; ++t) a0 += ld_stream(vp + 32 * t, pol) * xf(ld_stream(cp + 32 * t, pol));
         T acc = a0 + a1;
@@ -257,13 +260,15 @@ __device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& x
         const int nt = min(TMA_CH, total_t - t_lo);
         const int* sc = (const int*)(wbuf + (k & 1) * SB);
         const T* sv = (const T*)(wbuf + (k & 1) * SB + TMA_CH * 32 * 4);
-        T prod[TMA_CH];
+        int cs[TMA_CH];
+        T vs[TMA_CH], xs[TMA_CH];
 #pragma unroll
         for (int t = 0; t < TMA_CH; ++t) {
-            const int c = t < nt ? sc[t * 32 + lane] : 0;
-            const T v = t < nt ? sv[t * 32 + lane] : T(0);
-            prod[t] = v * xf(c);
+            cs[t] = t < nt ? sc[t * 32 + lane] : 0;
+            vs[t] = t < nt ? sv[t * 32 + lane] : T(0);
         }
+#pragma unroll
+        for (int t = 0; t < TMA_CH; ++t) xs[t] = xf(cs[t]);
 #pragma unroll
         for (int t = 0; t < TMA_CH; ++t) {
             if (t < nt) {
@@ -274,7 +279,7 @@ __device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& x
                     ++cur;
                     bound = (ro(S.ptr + cur + 1) - e0) >> 5;
                 }
-                acc += prod[t];
+                acc = fmaT(vs[t], xs[t], acc);
             }
         }
     }
@@ -310,9 +315,6 @@ __device__ __forceinline__ void spmv2(const Team& tm, const Sell<T>& S, const T*
     auto f2 = [x2](int c) { return x2[c]; };
     sell2_v(tm, S, f1, f2, epi);
 }
-
-__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
 // ---------------------------------------------------------------------------
 // M^{-1}(a, e) for M = [I A^T; -A I]: x = (I + A^T A)^{-1}(a - A^T e) by CG
@@ -1404,6 +1406,70 @@ __device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, 
     }
     if (a.mode == MODE_SOLVE) {
         superscs(tm, P, W, a.S, G, sm_rhs, sm_L, sm_t, psd);
+        return;
+    }
+    if (a.mode == MODE_PROFILE) {
+        // device-side timing of the solver's building blocks on this problem:
+        // io_out[0..4] = ns per A pass, A^T pass, grid barrier, 1-value
+        // reduction, and one CG iteration (A pass, barrier, A^T pass with
+        // three dots, reduction, update pass, barrier)
+        const int reps = a.slot > 0 ? a.slot : 10;
+        T* xv = W.cp;
+        T* yv = W.tm;
+        T* zv = W.tn;
+        for (int j = tm.rank(); j < n; j += tm.size()) {
+            xv[j] = T(1) / T(1 + (j % 7));
+            W.cr[j] = xv[j];
+        }
+        tm.sync();
+        double t[6];
+        t[0] = (double)gtimer();
+        for (int r = 0; r < reps; ++r) {
+            spmv(tm, P.A, xv, [&](int i, T s) { yv[i] = s; });
+            tm.sync();
+        }
+        t[1] = (double)gtimer();
+        for (int r = 0; r < reps; ++r) {
+            spmv(tm, P.AT, yv, [&](int j, T s) { zv[j] = s; });
+            tm.sync();
+        }
+        t[2] = (double)gtimer();
+        for (int r = 0; r < reps; ++r) tm.sync();
+        t[3] = (double)gtimer();
+        for (int r = 0; r < reps; ++r) {
+            double v1[1] = {1.0};
+            tm.reduce(v1);
+        }
+        t[4] = (double)gtimer();
+        T* q = W.cq;
+        T* rr = W.cr;
+        for (int r = 0; r < reps; ++r) {
+            spmv(tm, P.A, xv, [&](int i, T s) { yv[i] = s; });
+            tm.sync();
+            T pq = 0, rq = 0, qq = 0;
+            spmv(tm, P.AT, yv, [&](int j, T s) {
+                const T qj = xv[j] + s;
+                q[j] = qj;
+                pq += xv[j] * qj;
+                rq += rr[j] * qj;
+                qq += qj * qj;
+            });
+            double red[4] = {(double)pq, (double)rq, (double)qq, 0.0};
+            tm.reduce(red);
+            const T ta = (T)(1e-30 * red[0]);
+            for (int j = tm.rank(); j < n; j += tm.size()) {
+                const T pj = xv[j];
+                W.ws[1][j] += ta * pj;
+                const T rj = rr[j] - ta * q[j];
+                rr[j] = rj;
+                xv[j] = rj + ta * pj;
+            }
+            tm.sync();
+        }
+        t[5] = (double)gtimer();
+        if (tm.leader())
+            for (int k = 0; k < 5; ++k) W.io_out[k] = (t[k + 1] - t[k]) / reps;
+        tm.sync();
         return;
     }
     // single operators: io_in (FP64, N) -> u (T), results to io_out / io_out2

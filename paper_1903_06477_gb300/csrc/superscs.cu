@@ -505,6 +505,7 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->mixed_max_iters = 10000;
     o->mixed_switch = 0.0;
     o->cg_adapt = 0.0;
+    o->spmv_path = 0;
     return SCS_OK;
 }
 
@@ -558,7 +559,9 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     w->D.team = team;
     w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? 1024 : 256);
     w->has32 = settings->precision == SCS_MIXED;
-    const bool tma = team == SCS_TEAM_GRID;
+    // the TMA-staged stream only on request: on the gather-bound products it
+    // measured no faster than direct streaming loads
+    const bool tma = team == SCS_TEAM_GRID && settings->spmv_path == 2;
     w->D.dyn64 = dyn_smem<double>(H, w->D.threads, tma);
     w->D.dyn32 = w->has32 ? dyn_smem<float>(H, w->D.threads, tma) : 0;
     int rc2 = config_kernels<double>(w->D.dyn64, w->err);
@@ -574,8 +577,10 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
         }
         if (nb < 1) { set_err(w->err, "solver kernel cannot be resident with %d threads", w->D.threads); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
         w->D.grid = w->D.sms * std::min(nb, 4);
-        warp_bounds(w->H.SA, w->D.grid * (w->D.threads / 32));
-        warp_bounds(w->H.ST, w->D.grid * (w->D.threads / 32));
+        if (tma) {
+            warp_bounds(w->H.SA, w->D.grid * (w->D.threads / 32));
+            warp_bounds(w->H.ST, w->D.grid * (w->D.threads / 32));
+        }
     } else {
         w->D.grid = 1;
     }
@@ -807,6 +812,25 @@ static int single_op(scs_work* w, int mode, int slot, const double* in, double* 
     if (rc) return rc;
     if (out) CU(cudaMemcpyAsync(out, w->W64.io_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     if (out2) CU(cudaMemcpyAsync(out2, w->W64.io_out2, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_profile(scs_work* w, int32_t precision, int32_t reps, double* ns)
+{
+    if (!w || !ns || reps < 1) { set_err(w ? w->err : g_err, "bad arguments"); return SCS_EINVAL; }
+    DevSettings S = dev_settings(&w->S);
+    int rc;
+    if (precision == SCS_MIXED) {
+        if (!w->has32) { set_err(w->err, "work was not set up with SCS_MIXED"); return SCS_EINVAL; }
+        Args<float> a = make_args(w->P32, w->W32, S, MODE_PROFILE, reps);
+        if ((rc = launch<float>(w->D.team, w->D.threads, w->D.grid, w->D.dyn32, a, w->dargs32, w->queue, w->stream, w->err))) return rc;
+        CU(cudaMemcpyAsync(ns, w->W32.io_out, 5 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
+    } else {
+        Args<double> a = make_args(w->P64, w->W64, S, MODE_PROFILE, reps);
+        if ((rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
+        CU(cudaMemcpyAsync(ns, w->W64.io_out, 5 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
+    }
     CU(cudaStreamSynchronize(w->stream), w->err);
     return SCS_OK;
 }

@@ -158,13 +158,19 @@ struct GridTeam {
             s_last = last;
         }
         __syncthreads();
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (s_last) {
-            for (int k = wid; k < K; k += nw) {
+            // all threads of the last block: thread j loads block j's K partials
+            double pv[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) pv[k] = 0.0;
+            for (int j = threadIdx.x; j < B; j += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < K; ++k) pv[k] += __ldcg(P + (size_t)k * B + j);
+            block_partial<K>(pv, red);
+            if (threadIdx.x < K) {
                 double s = 0.0;
-                for (int j = lane; j < B; j += 32) s += __ldcg(P + (size_t)k * B + j);
-                s = warp_sum(s);
-                if (lane == 0) R[k] = s;
+                for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
+                R[threadIdx.x] = s;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
