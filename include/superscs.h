@@ -157,6 +157,14 @@ int scs_update_bc(scs_work *work, const double *b, const double *c);
  * and checkpoint/resume (any u0 converges, Sec. 4.5). */
 int scs_get_u(scs_work *work, double *u);
 
+/* Relative primal residual, dual residual and duality gap of Sec. 4.3 for a
+ * caller's candidate (x, y, s) on the work's data:
+ *   out[0] = ||A x + s - b|| / (1 + ||b||),  out[1] = ||A^T y + c|| / (1 + ||c||),
+ *   out[2] = |<c,x> + <b,y>| / (1 + |<c,x>| + |<b,y>|).
+ * x (n), y (m), s (m) and out (3) may be host or device pointers.  Cone
+ * membership of s and y is not checked.  Synchronises the work's stream. */
+int scs_residuals(scs_work *work, const double *x, const double *y, const double *s, double *out);
+
 /* --- single operators of Eq. (drs), for checking one step at a time ------ */
 /* out = (I+Q)^{-1} r on N-vectors (Sec. 4.1, linear-system step of Eq. drs).
  * Uses and updates the work's CG warm start of slot 0 (u~) or 1 (d~). */

@@ -80,6 +80,7 @@ _SIGS = [
     ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    ("scs_residuals", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_finish", None, [C.c_void_p]),
     ("scs_last_error", C.c_char_p, [C.c_void_p]),
     ("scs_batch_setup", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,
@@ -226,6 +227,14 @@ class Work:
         out = np.empty(self.N)
         _check(lib().scs_project_cone(self.h, _ptr(v), _ptr(out)), self.h)
         return out
+
+    def residuals(self, x, y, s, out=None):
+        """(pr, dr, gap) of Sec. 4.3 for a candidate; arrays host or CUDA."""
+        conv = lambda a: a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=np.float64)
+        x, y, s = conv(x), conv(y), conv(s)
+        o = np.empty(3) if out is None else out
+        _check(lib().scs_residuals(self.h, _ptr(x), _ptr(y), _ptr(s), _ptr(o)), self.h)
+        return o
 
     def profile(self, precision=FP64, reps=20):
         """ns per A pass, A^T pass, barrier, reduction, CG iteration (device timer)."""

@@ -19,7 +19,8 @@ constexpr int MAXMEM = 64;   // direction memory cap (RB)
 constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared memory)
 constexpr int PSD_MAX = 64;  // largest PSD order
 
-enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5 };
+enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5,
+            MODE_RESID = 6 };
 enum { ST_SOLVED = 1, ST_INFEASIBLE = -1, ST_UNBOUNDED = -2, ST_MAX_ITERS = -3, ST_TIME_LIMIT = -4,
        ST_NUMERICAL = -5, ST_STALLED = -6 };
 
@@ -1406,6 +1407,42 @@ __device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, 
     }
     if (a.mode == MODE_SOLVE) {
         superscs(tm, P, W, a.S, G, sm_rhs, sm_L, sm_t, psd);
+        return;
+    }
+    if (a.mode == MODE_RESID) {
+        // Sec. 4.3 residuals of a caller's candidate: x = io_in[0,n), y = io_in[n,n+m),
+        // s = io_out2[0,m); io_out[0..2] = pr, dr, gap (FP64 data only)
+        if constexpr (sizeof(T) == sizeof(double)) {
+            const T* xv = W.io_in;
+            const T* yv = W.io_in + n;
+            const T* sv = W.io_out2;
+            T* tmv = W.tm;
+            T* tnv = W.tn;
+            spmv(tm, P.A, xv, [&](int i, T v) { tmv[i] = v; });
+            spmv(tm, P.AT, yv, [&](int j, T v) { tnv[j] = v; });
+            tm.sync();
+            double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            for (int i = tm.rank(); i < m; i += tm.size()) {
+                const double bi = ro(P.b + i);
+                const double e = tmv[i] + sv[i] - bi;
+                a0 += e * e;
+                a3 += bi * yv[i];
+            }
+            for (int j = tm.rank(); j < n; j += tm.size()) {
+                const double cj = ro(P.c + j);
+                const double g = tnv[j] + cj;
+                a1 += g * g;
+                a2 += cj * xv[j];
+            }
+            double red[4] = {a0, a1, a2, a3};
+            tm.reduce(red);
+            if (tm.leader()) {
+                W.io_out[0] = sqrt(red[0]) / (1.0 + P.nb);
+                W.io_out[1] = sqrt(red[1]) / (1.0 + P.nc);
+                W.io_out[2] = fabs(red[2] + red[3]) / (1.0 + fabs(red[2]) + fabs(red[3]));
+            }
+            tm.sync();
+        }
         return;
     }
     if (a.mode == MODE_PROFILE) {

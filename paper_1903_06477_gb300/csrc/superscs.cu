@@ -835,6 +835,22 @@ extern "C" int scs_profile(scs_work* w, int32_t precision, int32_t reps, double*
     return SCS_OK;
 }
 
+extern "C" int scs_residuals(scs_work* w, const double* x, const double* y, const double* s, double* out)
+{
+    if (!w || !x || !y || !s || !out) { set_err(w ? w->err : g_err, "NULL argument"); return SCS_EINVAL; }
+    const int n = w->H.n, m = w->H.m;
+    CU(cudaMemcpyAsync(w->W64.io_in, x, sizeof(double) * n, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaMemcpyAsync(w->W64.io_in + n, y, sizeof(double) * m, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaMemcpyAsync(w->W64.io_out2, s, sizeof(double) * m, cudaMemcpyDefault, w->stream), w->err);
+    DevSettings S = dev_settings(&w->S);
+    Args<double> a = make_args(w->P64, w->W64, S, MODE_RESID);
+    int rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, w->W64.io_out, 3 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
 extern "C" int scs_linsys(scs_work* w, const double* r, double* out, int32_t slot)
 {
     return single_op(w, MODE_LINSYS, slot ? 1 : 0, r, out, nullptr);

@@ -224,3 +224,17 @@ def test_repeat_solves_are_deterministic():
     b = work.solve()
     np.testing.assert_array_equal(a[0], b[0])
     assert a[3]["iters"] == b[3]["iters"]
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_residuals_entry_matches_numpy(team):
+    """scs_residuals evaluates Sec. 4.3's pr, dr, gap for any candidate."""
+    prob = PROBS["planted_mixed_cones"]
+    work = B.Work(prob, team=team, eps=1e-6, max_iters=20000)
+    x, y, s, info = work.solve()
+    out = work.residuals(x, y, s)
+    ref = _kkt(prob, x, y, s)
+    np.testing.assert_allclose(out, ref, rtol=1e-9, atol=1e-15)
+    rng = np.random.default_rng(4)
+    xr, yr, sr = rng.standard_normal(work.n), rng.standard_normal(work.m), rng.standard_normal(work.m)
+    np.testing.assert_allclose(work.residuals(xr, yr, sr), _kkt(prob, xr, yr, sr), rtol=1e-12)
