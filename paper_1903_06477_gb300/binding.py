@@ -81,6 +81,7 @@ _SIGS = [
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("scs_residuals", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_residuals_noalloc", C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 10),
     ("scs_finish", None, [C.c_void_p]),
     ("scs_last_error", C.c_char_p, [C.c_void_p]),
     ("scs_batch_setup", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,

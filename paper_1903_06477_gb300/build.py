@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsuperscs.so")
-UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_block_f64.cu", "kernels_block_f32.cu", "superscs.cu"]
+UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_block_f64.cu", "kernels_block_f32.cu", "superscs.cu",
+         "residuals_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177"]

@@ -42,6 +42,10 @@ static void set_err(char* dst, const char* fmt, ...)
     if (dst != g_err) memcpy(g_err, dst, 512);
 }
 
+namespace sscs {
+void record_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace sscs
+
 #define CU(call, errbuf)                                                                                    \
     do {                                                                                                    \
         cudaError_t e_ = (call);                                                                            \
