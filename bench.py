@@ -129,6 +129,11 @@ def build_workload(name, rank):
         kw = dict(direction=1, mem=10, c0=0.1, eps=1e-5, max_iters=20000, cg_rtol=1e-10)
         cfg = {"workload": "LASSO 60x120 epigraph (m=302, n=241), RB mem 10, eps 1e-5", "n": 241, "m": 302,
                "nnz": int(prob["A"].nnz)}
+    elif name == "c3":
+        prob = W.c3_planted_sdp(seed=0)
+        kw = dict(direction=0, mem=10, eps=1e-4, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-4)
+        cfg = {"workload": "planted SDP: 512 PSD blocks 64x64 + 50000 orthant rows, n=20000, nnz=1e6, AA mem 10, "
+                           "eps 1e-4", "n": prob["A"].shape[1], "m": prob["A"].shape[0], "nnz": int(prob["A"].nnz)}
     else:
         raise SystemExit(f"unknown workload {name}")
     return prob, kw, cfg
@@ -198,6 +203,56 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The batched workload: 4096 independent portfolio SOCPs (k ~ U{20..400})
+    in one persistent launch per precision phase; step = one batch solve."""
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    from paper_1903_06477_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    probs = W.c4_portfolios(4096)
+    kw = dict(direction=0, mem=10, eps=1e-5, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5)
+    prec = B.MIXED if args.precision == "mixed" else B.FP64
+    t0 = time.perf_counter()
+    batch = B.Batch(probs, precision=prec, **kw)
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        batch.solve()
+    times, infos = [], None
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, _, infos = batch.solve()
+            times.append(time.perf_counter() - t0)
+    ksum = infos[0]["kernel_s"][0] + infos[0]["kernel_s"][1]
+    solved = sum(1 for i in infos if i["status"] == B.SOLVED)
+    # looped plain FP64 single solves on a sample, for comparison
+    samp = probs[:: len(probs) // 32][:32]
+    t0 = time.perf_counter()
+    for p in samp:
+        w = B.Work(p, precision=B.FP64, **kw)
+        w.solve()
+        w.close()
+    loop_s = (time.perf_counter() - t0) / len(samp)
+    line = {
+        "metric": METRIC, "value": len(probs) / float(np.mean(times)), "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == B.MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "4096 portfolio SOCPs, k ~ U{20..400}, rank k/10, eps 1e-5, AA mem 10",
+                   "precision": args.precision, "instances": len(probs),
+                   "nnz_total": int(sum(p["A"].nnz for p in probs))},
+        "solved": solved, "threads_per_block": infos[0]["threads_per_block"], "setup_s": setup_s,
+        "kernel_s_per_step": ksum, "looped_fp64_single_solves_per_s": 1.0 / loop_s,
+        "speedup_vs_looped_fp64": (len(probs) / float(np.mean(times))) * loop_s,
+        "median_iters": float(np.median([i["iters"] for i in infos])),
+        "gpu_launches": args.steps * (4 if prec == B.MIXED else 2), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +271,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_batch(args)
 
     import torch
     from paper_1903_06477_gb300 import binding as B
@@ -318,7 +375,7 @@ def main():
                "d2h_bytes_per_step": int(d2h), "includes": "scs_setup (validation, A^T build, H2D, g solve) + "
                                                             "scs_solve + D2H, host buffers"}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("c2"):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
         val, det = oracle_baseline(prob, kw, W.c2_planted(seed=0, scale=0.02))
         cpu = {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "FP64 oracle, 1 thread: setup + 1 outer iteration on the full instance, scaled by the "

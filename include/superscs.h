@@ -125,6 +125,9 @@ typedef struct {
                             (CUDA events on the work's stream) */
     int64_t mat_passes[2]; /* passes over A or A^T (one SpMV each) in the FP64 [0] / FP32 [1] phase */
     int64_t cg_iters_fp32; /* CG iterations of the FP32 phase */
+    double psd_resid_fp32; /* largest FP64-evaluated ||X V - V L||_F / ||X||_F of the FP32 PSD
+                              eigensolves (SCS_MIXED with PSD cones) */
+    int32_t threads_per_block; /* launch shape used (batches: chosen by the autotuner unless set) */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
@@ -215,13 +218,18 @@ void scs_finish(scs_work *work);
 const char *scs_last_error(const scs_work *work);
 
 /* --- batched solves ------------------------------------------------------ */
-/* B independent instances of any sizes, solved by one persistent launch in
- * which each thread block takes instances from a queue, largest first.
- * The settings apply to every instance (team is ignored: one block each). */
+/* B independent instances of any sizes, solved by one persistent launch (per
+ * precision phase) in which each thread block takes instances from a queue,
+ * largest first.  The settings apply to every instance (team is ignored: one
+ * block each).  With settings->threads = 0 and B >= 64 the setup times the
+ * first solve phase on a sample of instances for 128, 256 and 512 threads per
+ * block and keeps the fastest. */
 int scs_batch_setup(int32_t B, const scs_data *const *data, const scs_cone *const *cones,
                     const scs_settings *settings, void *cuda_stream, scs_batch **out);
-/* x[i], y[i], s[i] (any may be NULL, as may the arrays) receive instance i's
- * result as in scs_solve; infos may be NULL or hold B entries. */
+/* x[i], y[i], s[i] (host pointers; any may be NULL, as may the arrays)
+ * receive instance i's result as in scs_solve; infos may be NULL or hold B
+ * entries.  Results are gathered on the device and copied back in one
+ * transfer. */
 int scs_batch_solve(scs_batch *batch, double *const *x, double *const *y, double *const *s,
                     scs_info *infos);
 void scs_batch_finish(scs_batch *batch);

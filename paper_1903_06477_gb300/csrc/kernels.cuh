@@ -33,11 +33,11 @@ __global__ void __launch_bounds__(1024) k_grid(const __grid_constant__ Args<T> a
     }
     __syncthreads();
     GridTeam tm{sf.red, tma ? dyn : nullptr, sf.mbar, sf.ph, a.W.partials, a.W.bar, a.W.abort_flag, 0};
-    run_mode<T>(tm, a, sf.G, sf.rhs, sf.L, sf.t, dyn);
+    run_mode<T>(tm, a.P, a.W, a.S, a.mode, a.slot, sf.G, sf.rhs, sf.L, sf.t, dyn);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int* queue)
+__global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int* queue, DevSettings S, int mode)
 {
     __shared__ SmemFixed sf;
     __shared__ int sidx;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int
         const int i = sidx;
         __syncthreads();
         if (i >= B) break;
-        run_mode<T>(tm, insts[i], sf.G, sf.rhs, sf.L, sf.t, dyn);
+        run_mode<T>(tm, insts[i].P, insts[i].W, S, mode, insts[i].slot, sf.G, sf.rhs, sf.L, sf.t, dyn);
         __syncthreads();
     }
 }
@@ -67,9 +67,10 @@ const void* kgrid_ptr() { return (const void*)k_grid<T>; }
 template <typename T>
 const void* kblock_ptr() { return (const void*)k_block<T>; }
 template <typename T>
-cudaError_t launch_block(int grid, int threads, size_t dyn, cudaStream_t st, const Args<T>* insts, int B, int* queue)
+cudaError_t launch_block(int grid, int threads, size_t dyn, cudaStream_t st, const Args<T>* insts, int B, int* queue,
+                         const DevSettings& S, int mode)
 {
-    k_block<T><<<grid, threads, dyn, st>>>(insts, B, queue);
+    k_block<T><<<grid, threads, dyn, st>>>(insts, B, queue, S, mode);
     return cudaGetLastError();
 }
 

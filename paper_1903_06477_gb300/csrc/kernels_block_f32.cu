@@ -3,5 +3,6 @@
 
 namespace sscs {
 template const void* kblock_ptr<float>();
-template cudaError_t launch_block<float>(int, int, size_t, cudaStream_t, const Args<float>*, int, int*);
+template cudaError_t launch_block<float>(int, int, size_t, cudaStream_t, const Args<float>*, int, int*,
+                                         const DevSettings&, int);
 }  // namespace sscs

@@ -40,6 +40,7 @@ struct DevSettings {
     int use_warm;
     double switch_kkt;     // > 0: stop (hand over) once max(pr,dr,gap) <= switch_kkt
     double cg_adapt;       // > 0: CG inside the loop also stops at ||res|| <= cg_adapt ||Ru||
+    int keep_ws;           // 1: keep the CG warm starts found in ws (handed over by the FP32 phase)
 };
 
 struct DevState {
@@ -48,6 +49,7 @@ struct DevState {
     double pr, dr, gap, ic, uc, pobj, dobj, nRu, hg;
     int setup_cg, pad;
     long long mat_passes;  // SpMV passes over A or A^T
+    double psd_resid;      // largest ||X V - V L||_F / ||X||_F of the FP32 eigensolves, in FP64
 };
 
 // Sliced ELL with row sorting (SELL-H-sigma) and V lanes per row, H = 32 / V
@@ -548,12 +550,14 @@ struct PsdSmem {
     T* sn;
     T* lam;
     double* red;
+    double* X0;  // FP32 eigensolves only: the input matrix in FP64 for the residual recheck
 };
 
 template <typename T>
 __host__ __device__ constexpr size_t psd_smem_bytes()
 {
-    return sizeof(T) * (2 * PSD_MAX * PSD_MAX + 3 * PSD_MAX) + sizeof(int) * PSD_MAX + 64 * sizeof(double);
+    return sizeof(T) * (2 * PSD_MAX * PSD_MAX + 3 * PSD_MAX) + sizeof(int) * PSD_MAX + 64 * sizeof(double) +
+           (sizeof(T) == 4 ? sizeof(double) * PSD_MAX * PSD_MAX : 0);
 }
 
 template <typename T>
@@ -568,11 +572,13 @@ __device__ PsdSmem<T> psd_smem(unsigned char* base)
     s.red = (double*)(s.lam + 2 * PSD_MAX);
     s.pp = (int*)(s.red + 32);
     s.qq = s.pp + PSD_MAX / 2;
+    s.X0 = sizeof(T) == 4 ? (double*)(s.qq + PSD_MAX / 2) : nullptr;
     return s;
 }
 
 template <typename T, class Team, class Op>
-__device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned char* psd_base)
+__device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned char* psd_base,
+                             double* psd_resid = nullptr)
 {
     const int n = P.n;
     const int lin = n + P.f + P.l;
@@ -641,10 +647,28 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                     val = (ii == jj) ? v : (T)((double)v * isq2);
                 }
                 sm.X[idx] = val;
+                if constexpr (sizeof(T) == 4) sm.X0[idx] = (double)val;
             }
             __syncthreads();
             const double tol2 = sizeof(T) == 8 ? 1e-26 : 1e-11;
             jacobi_block<T>(sm.X, sm.V, dp, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2, sizeof(T) == 8 ? 20 : 15);
+            if constexpr (sizeof(T) == 4) {
+                // FP64 recheck of the FP32 eigenpairs: ||X V - V diag(l)||_F / ||X||_F
+                double r2 = 0.0, x2 = 0.0;
+                for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
+                    const int i = idx / dp, k = idx % dp;
+                    double acc = -(double)sm.V[i * dp + k] * (double)sm.X[k * dp + k];
+                    for (int j = 0; j < dp; ++j) acc += sm.X0[i * dp + j] * (double)sm.V[j * dp + k];
+                    r2 += acc * acc;
+                    x2 += sm.X0[idx] * sm.X0[idx];
+                }
+                r2 = block_sum(r2, sm.red);
+                x2 = block_sum(x2, sm.red);
+                if (threadIdx.x == 0 && x2 > 0.0 && psd_resid) {
+                    const double rel = sqrt(r2 / x2);
+                    atomicMax((unsigned long long*)psd_resid, (unsigned long long)__double_as_longlong(rel));
+                }
+            }
             for (int i = threadIdx.x; i < dp; i += blockDim.x) {
                 const T l = sm.X[i * dp + i];
                 sm.lam[i] = l > T(0) ? l : T(0);
@@ -1185,6 +1209,16 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
     long long cg_total = 0;
     int k0 = 0, k1 = 0, k2 = 0, bt = 0;
     const double deadline = S.time_limit_ns > 0.0 ? (double)gtimer() + S.time_limit_ns : 0.0;
+    // CG warm starts from zero unless the previous phase handed them over
+    if (!S.keep_ws)
+        for (int i = tm.rank(); i < n; i += tm.size()) {
+            W.ws[0][i] = T(0);
+            W.ws[1][i] = T(0);
+        }
+    if (tm.leader()) {
+        W.st->mat_passes = 0;
+        W.st->psd_resid = 0.0;
+    }
     // u0
     for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = S.use_warm ? (T)W.warm[i] : T(0);
     if (tm.leader()) *W.u.t = S.use_warm ? W.warm[nm] : 1.0;
@@ -1193,7 +1227,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
     double nRu;
     {
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd);
+        project_pass(tm, P, op, psd, &W.st->psd_resid);
         double red[1] = {(double)op.acc0};
         tm.reduce(red);
         nRu = sqrt(red[0]);
@@ -1264,7 +1298,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             // K0
             eta = nRu;
             OpK0<T> op{W.u, W.ut, W.ub, W.Ru, W.d, W.dt, W.zp, W.xip, T(0), T(0)};
-            project_pass(tm, P, op, psd);
+            project_pass(tm, P, op, psd, &W.st->psd_resid);
             double red[2] = {(double)op.acc0, (double)op.acc1};
             tm.reduce(red);
             nRu = sqrt(red[0]);
@@ -1275,7 +1309,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             for (int ls = 0; ls <= S.ls_max; ++ls) {
                 if (ls == S.ls_max) alpha = 0.0;
                 OpTrial<T> op{W.u, W.ut, W.d, W.dt, W.wb, W.Rw, alpha, T(0), T(0)};
-                project_pass(tm, P, op, psd);
+                project_pass(tm, P, op, psd, &W.st->psd_resid);
                 double red[2] = {(double)op.acc0, (double)op.acc1};
                 tm.reduce(red);
                 const double nRw = sqrt(red[0]);
@@ -1335,7 +1369,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
                     nz2 = red2[0];
                     cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol);
                     OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
-                    project_pass(tm, P, opr, psd);
+                    project_pass(tm, P, opr, psd, &W.st->psd_resid);
                     double red3[1] = {(double)opr.acc0};
                     tm.reduce(red3);
                     nRu = sqrt(red3[0]);
@@ -1382,17 +1416,15 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
 // one entry for every mode
 // ---------------------------------------------------------------------------
 template <typename T, class Team>
-__device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, double* sm_L, double* sm_t,
-                         unsigned char* psd)
+__device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, int mode, int slot,
+                         double* G, double* sm_rhs, double* sm_L, double* sm_t, unsigned char* psd)
 {
-    const DevProb<T>& P = a.P;
-    const DevWork<T>& W = a.W;
     const int n = P.n, m = P.m, nm = n + m;
-    if (a.mode == MODE_SETUP) {
+    if (mode == MODE_SETUP) {
         // g = M^{-1}(c, b) from a zero start; ws[0] is zero on entry and left zero
         T* x = W.ws[0];
         double htp;
-        const int it = minv(tm, P, W, P.c, P.b, x, a.S.cg_rtol, a.S.cg_max, htp);
+        const int it = minv(tm, P, W, P.c, P.b, x, S.cg_rtol, S.cg_max, htp);
         for (int i = tm.rank(); i < n; i += tm.size()) {
             W.g[i] = x[i];
             x[i] = T(0);
@@ -1405,11 +1437,11 @@ __device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, 
         tm.sync();
         return;
     }
-    if (a.mode == MODE_SOLVE) {
-        superscs(tm, P, W, a.S, G, sm_rhs, sm_L, sm_t, psd);
+    if (mode == MODE_SOLVE) {
+        superscs(tm, P, W, S, G, sm_rhs, sm_L, sm_t, psd);
         return;
     }
-    if (a.mode == MODE_RESID) {
+    if (mode == MODE_RESID) {
         // Sec. 4.3 residuals of a caller's candidate: x = io_in[0,n), y = io_in[n,n+m),
         // s = io_out2[0,m); io_out[0..2] = pr, dr, gap (FP64 data only)
         if constexpr (sizeof(T) == sizeof(double)) {
@@ -1445,12 +1477,12 @@ __device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, 
         }
         return;
     }
-    if (a.mode == MODE_PROFILE) {
+    if (mode == MODE_PROFILE) {
         // device-side timing of the solver's building blocks on this problem:
         // io_out[0..4] = ns per A pass, A^T pass, grid barrier, 1-value
         // reduction, and one CG iteration (A pass, barrier, A^T pass with
         // three dots, reduction, update pass, barrier)
-        const int reps = a.slot > 0 ? a.slot : 10;
+        const int reps = slot > 0 ? slot : 10;
         T* xv = W.cp;
         T* yv = W.tm;
         T* zv = W.tn;
@@ -1513,20 +1545,20 @@ __device__ void run_mode(Team& tm, const Args<T>& a, double* G, double* sm_rhs, 
     for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = (T)W.io_in[i];
     if (tm.leader()) *W.u.t = W.io_in[nm];
     tm.sync();
-    if (a.mode == MODE_LINSYS) {
-        linsys(tm, P, W, W.u, W.ut, a.slot, a.S.cg_rtol, a.S.cg_max, W.st->hg);
+    if (mode == MODE_LINSYS) {
+        linsys(tm, P, W, W.u, W.ut, slot, S.cg_rtol, S.cg_max, W.st->hg);
         for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ut.v[i];
         if (tm.leader()) W.io_out[nm] = *W.ut.t;
-    } else if (a.mode == MODE_PROJECT) {
+    } else if (mode == MODE_PROJECT) {
         OpProject<T> op{W.u.v, W.u.t, W.ub.v, W.ub.t};
-        project_pass(tm, P, op, psd);
+        project_pass(tm, P, op, psd, &W.st->psd_resid);
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ub.v[i];
         if (tm.leader()) W.io_out[nm] = *W.ub.t;
-    } else if (a.mode == MODE_APPLY_T) {
-        linsys(tm, P, W, W.u, W.ut, 0, a.S.cg_rtol, a.S.cg_max, W.st->hg);
+    } else if (mode == MODE_APPLY_T) {
+        linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, W.st->hg);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd);
+        project_pass(tm, P, op, psd, &W.st->psd_resid);
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) {
             W.io_out[i] = (double)W.u.v[i] - (double)W.Ru.v[i];

@@ -282,7 +282,8 @@ struct Arena {
 // layout of one instance's data and work in precision T; base == nullptr only measures
 template <typename T>
 static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevProb<T>& P, DevWork<T>& W,
-                    const int* shared_idx /* Ap,Ai,Tp,Ti,q_off,s_dim,s_off from another precision or null */)
+                    const int* shared_idx /* index arrays shared with another precision or null */,
+                    DevState* st_ext = nullptr)
 {
     const int n = H.n, m = H.m, nm = n + m;
     const long long nnz = H.nnz;
@@ -346,7 +347,7 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     W.partials = A.take<double>((size_t)2 * KMAX * std::max(max_blocks, 1) + 2 * KMAX);
     W.bar = A.take<unsigned>(4);
     W.abort_flag = A.take<int>(4);
-    W.st = A.take<DevState>(1);
+    W.st = st_ext ? st_ext : A.take<DevState>(1);
 }
 
 template <typename T>
@@ -407,6 +408,7 @@ static DevSettings dev_settings(const scs_settings* S)
     D.use_warm = 0;
     D.switch_kkt = 0.0;
     D.cg_adapt = S->cg_adapt;
+    D.keep_ws = 0;
     return D;
 }
 
@@ -448,7 +450,7 @@ static int launch(int team, int threads, int grid, size_t dyn, const Args<T>& a,
     } else {
         CU(cudaMemcpyAsync(dev_args, &a, sizeof(Args<T>), cudaMemcpyHostToDevice, st), err);
         CU(cudaMemsetAsync(queue, 0, sizeof(int), st), err);
-        CU(launch_block<T>(1, threads, dyn, st, dev_args, 1, queue), err);
+        CU(launch_block<T>(1, threads, dyn, st, dev_args, 1, queue, a.S, a.mode), err);
     }
     return SCS_OK;
 }
@@ -671,15 +673,6 @@ static void fill_info(scs_info* info, const DevState& s)
     info->dobj = s.dobj;
 }
 
-template <typename T>
-static int reset_solve_state(scs_work* w, const DevWork<T>& W, const HostProb& H)
-{
-    CU(cudaMemsetAsync(W.ws[0], 0, sizeof(T) * H.n, w->stream), w->err);
-    CU(cudaMemsetAsync(W.ws[1], 0, sizeof(T) * H.n, w->stream), w->err);
-    CU(cudaMemsetAsync(&W.st->mat_passes, 0, sizeof(long long), w->stream), w->err);
-    return SCS_OK;
-}
-
 extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info* info)
 {
     if (!w) { set_err(g_err, "work is NULL"); return SCS_EINVAL; }
@@ -693,10 +686,8 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         CU(cudaMemcpyAsync(w->W64.warm, w->S.warm_u, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
         S.use_warm = 1;
     }
-    if ((rc = reset_solve_state<double>(w, w->W64, H))) return rc;
     DevState st32{};
     if (w->has32) {
-        if ((rc = reset_solve_state<float>(w, w->W32, H))) return rc;
         DevSettings S32 = S;
         S32.cg_rtol = w->S.mixed_cg_rtol > 0 ? w->S.mixed_cg_rtol : 1e-6;
         S32.stall_iters = w->S.mixed_stall;
@@ -713,6 +704,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
             CU(launch_f2d(w->W32.ws[k], w->W64.ws[k], H.n, w->stream), w->err);
         }
         S.use_warm = 1;
+        S.keep_ws = 1;
         CU(cudaMemcpyAsync(&st32, w->W32.st, sizeof(DevState), cudaMemcpyDeviceToHost, w->stream), w->err);
     }
     Args<double> a = make_args(w->P64, w->W64, S, MODE_SOLVE);
@@ -744,6 +736,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         info->setup_s = w->setup_s;
         info->solve_s = now_s() - t0;
         info->device_error = abort_flag | abort32;
+        info->threads_per_block = w->D.threads;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w->ev[0], w->ev[1]) == cudaSuccess) info->kernel_s[0] = ms * 1e-3;
         info->mat_passes[0] = st.mat_passes;
@@ -751,6 +744,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
             if (cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]) == cudaSuccess) info->kernel_s[1] = ms * 1e-3;
             info->mat_passes[1] = st32.mat_passes;
             info->cg_iters_fp32 = st32.cg_iters;
+            info->psd_resid_fp32 = st32.psd_resid;
         }
     }
     if (abort_flag || abort32) { set_err(w->err, "device barrier timed out"); return SCS_ETIMEOUT; }
@@ -869,7 +863,10 @@ extern "C" int scs_apply_T(scs_work* w, const double* u, double* Tu, double* Ru)
 }
 
 // ---------------------------------------------------------------------------
-// batches: one arena, one descriptor per instance, persistent CTAs
+// batches: one arena, one descriptor per instance (uploaded once), persistent
+// CTAs taking instances from a queue; states and outputs are gathered into
+// contiguous buffers so a batch solve needs a fixed number of launches and
+// copies whatever B is.
 // ---------------------------------------------------------------------------
 struct scs_batch {
     int B = 0;
@@ -878,38 +875,79 @@ struct scs_batch {
     scs_settings S;
     cudaStream_t stream = nullptr;
     char* arena = nullptr;
-    int threads = 256, grid = 1;
+    int threads = 256, grid = 1, sms = 1;
+    bool autotuned = false;
     bool has32 = false;
     size_t dyn64 = 0, dyn32 = 0;
     std::vector<Args<double>> a64;
     std::vector<Args<float>> a32;
     Args<double>* d64 = nullptr;
     Args<float>* d32 = nullptr;
+    DevState* st64 = nullptr;  // B contiguous states (queue order)
+    DevState* st32 = nullptr;
+    long long* off = nullptr;  // packed output offsets (queue order)
+    double* packed = nullptr;  // n + 2m doubles per instance
+    std::vector<long long> hoff;
+    long long packed_len = 0;
+    double* hpacked = nullptr;  // pinned host staging
+    DevState* hst = nullptr;    // pinned host staging (2B states)
     int* queue = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     char err[512];
     double setup_s = 0;
+    double tune_ms[3] = {0, 0, 0};
 };
 
-static int pick_threads(const std::vector<HostProb>& H)
+static int occupancy_grid(const void* fn, int threads, size_t dyn, int sms, int B)
 {
-    long long tot = 0;
-    for (const auto& h : H) tot += h.n + h.m;
-    const double avg = H.empty() ? 0 : (double)tot / H.size();
-    return avg < 600 ? 128 : (avg < 3000 ? 256 : 512);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, dyn);
+    return std::max(1, std::min(B, sms * std::max(nb, 1)));
 }
 
 template <typename T>
-static int batch_launch(scs_batch* b, int mode, const DevSettings& S, Args<T>* dargs, std::vector<Args<T>>& host_args,
-                        size_t dyn)
+static DevSettings batch_settings(const scs_batch* b, bool first_phase_of_mixed)
 {
-    for (auto& a : host_args) {
-        a.S = S;
-        a.mode = mode;
+    DevSettings S = dev_settings(&b->S);
+    if (first_phase_of_mixed) {
+        S.cg_rtol = b->S.mixed_cg_rtol > 0 ? b->S.mixed_cg_rtol : 1e-6;
+        S.stall_iters = b->S.mixed_stall;
+        S.switch_kkt = b->S.mixed_switch;
+        S.max_iters = b->S.mixed_max_iters > 0 ? std::min(b->S.mixed_max_iters, b->S.max_iters) : b->S.max_iters;
     }
-    CU(cudaMemcpyAsync(dargs, host_args.data(), sizeof(Args<T>) * host_args.size(), cudaMemcpyHostToDevice, b->stream), b->err);
-    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
-    CU(launch_block<T>(b->grid, b->threads, dyn, b->stream, dargs, b->B, b->queue), b->err);
-    CU(cudaStreamSynchronize(b->stream), b->err);  // host_args may change before the next launch
+    return S;
+}
+
+// Autotuner: time the first solve phase on an evenly spaced sample of the
+// (size-sorted) instances for 128, 256 and 512 threads per CTA and keep the
+// fastest; the sample's results are discarded (the real solve overwrites them).
+template <typename T>
+static int autotune(scs_batch* b, const std::vector<Args<T>>& host_args, size_t dyn, const DevSettings& S,
+                    Args<T>* scratch_args)
+{
+    const int nsamp = std::min(b->B, 2 * b->sms);
+    std::vector<Args<T>> samp(nsamp);
+    for (int i = 0; i < nsamp; ++i) samp[i] = host_args[(size_t)i * b->B / nsamp];
+    CU(cudaMemcpyAsync(scratch_args, samp.data(), sizeof(Args<T>) * nsamp, cudaMemcpyHostToDevice, b->stream), b->err);
+    const int cand[3] = {128, 256, 512};
+    float best = 1e30f;
+    for (int c = 0; c < 3; ++c) {
+        const int grid = occupancy_grid(sizeof(T) == 8 ? kblock_ptr<double>() : kblock_ptr<float>(), cand[c], dyn,
+                                        b->sms, nsamp);
+        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+        CU(cudaEventRecord(b->ev[0], b->stream), b->err);
+        CU(launch_block<T>(grid, cand[c], dyn, b->stream, scratch_args, nsamp, b->queue, S, MODE_SOLVE), b->err);
+        CU(cudaEventRecord(b->ev[1], b->stream), b->err);
+        CU(cudaEventSynchronize(b->ev[1]), b->err);
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]), b->err);
+        b->tune_ms[c] = ms;
+        if (ms < best) {
+            best = ms;
+            b->threads = cand[c];
+        }
+    }
+    b->autotuned = true;
     return SCS_OK;
 }
 
@@ -954,24 +992,59 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
         delete b;
         return rc;
     }
-    b->threads = settings->threads ? settings->threads : pick_threads(b->H);
-    int dev = 0, sms = 0, nb = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kblock_ptr<double>(), b->threads, b->dyn64);
-    b->grid = std::max(1, std::min(B, sms * std::max(nb, 1)));
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     const int mem = std::max(settings->mem, 1);
+    b->hoff.resize(B + 1, 0);
+    for (int qi = 0; qi < B; ++qi) {
+        const HostProb& h = b->H[b->order[qi]];
+        b->hoff[qi + 1] = b->hoff[qi] + h.n + 2LL * h.m;
+    }
+    b->packed_len = b->hoff[B];
     Arena A;
     b->a64.resize(B);
     if (b->has32) b->a32.resize(B);
-    for (int qi = 0; qi < B; ++qi) {
-        const HostProb& h = b->H[b->order[qi]];
-        lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr);
-        if (b->has32) lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1);
-    }
-    A.take<Args<double>>(B);
-    A.take<Args<float>>(B);
-    A.take<int>(4);
+    auto lay_all = [&](bool real) {
+        DevState* st64 = A.take<DevState>(B);
+        DevState* st32 = A.take<DevState>(B);
+        for (int qi = 0; qi < B; ++qi) {
+            const HostProb& h = b->H[b->order[qi]];
+            lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
+            b->a64[qi].slot = 0;
+            if (b->has32) {
+                lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
+                b->a32[qi].slot = 0;
+                if (real) {
+                    DevProb<float>& p = b->a32[qi].P;
+                    const DevProb<double>& q = b->a64[qi].P;
+                    p.A.ptr = q.A.ptr; p.A.col = q.A.col; p.A.perm = q.A.perm; p.A.wbnd = q.A.wbnd;
+                    p.AT.ptr = q.AT.ptr; p.AT.col = q.AT.col; p.AT.perm = q.AT.perm; p.AT.wbnd = q.AT.wbnd;
+                    p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
+                }
+            }
+        }
+        if (real) {
+            b->st64 = st64;
+            b->st32 = st32;
+        }
+        Args<double>* d64 = A.take<Args<double>>(B);
+        Args<float>* d32 = A.take<Args<float>>(B);
+        Args<double>* t64 = A.take<Args<double>>(2 * b->sms);
+        Args<float>* t32 = A.take<Args<float>>(2 * b->sms);
+        long long* off = A.take<long long>(B + 1);
+        double* packed = A.take<double>(b->packed_len);
+        int* queue = A.take<int>(4);
+        if (real) {
+            b->d64 = d64;
+            b->d32 = d32;
+            b->off = off;
+            b->packed = packed;
+            b->queue = queue;
+        }
+        return std::make_pair(t64, t32);
+    };
+    lay_all(false);
     const size_t bytes = A.off + 1024;
     if (cudaMalloc((void**)&b->arena, bytes) != cudaSuccess) {
         set_err(b->err, "cudaMalloc(%zu) failed", bytes);
@@ -980,36 +1053,52 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
         return SCS_ENOMEM;
     }
     auto fail = [&](int r) { memcpy(g_err, b->err, 512); scs_batch_finish(b); return r; };
+    if (cudaMallocHost((void**)&b->hpacked, sizeof(double) * std::max<long long>(b->packed_len, 1)) != cudaSuccess ||
+        cudaMallocHost((void**)&b->hst, sizeof(DevState) * 2 * B) != cudaSuccess) {
+        set_err(b->err, "cudaMallocHost failed");
+        return fail(SCS_ENOMEM);
+    }
+    for (auto& e : b->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { set_err(b->err, "cudaEventCreate failed"); return fail(SCS_ECUDA); }
     A.off = 0;
     A.base = b->arena;
-    for (int qi = 0; qi < B; ++qi) {
-        const HostProb& h = b->H[b->order[qi]];
-        lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr);
-        if (b->has32) {
-            lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1);
-            DevProb<float>& p = b->a32[qi].P;
-            const DevProb<double>& q = b->a64[qi].P;
-            p.A.ptr = q.A.ptr; p.A.col = q.A.col; p.A.perm = q.A.perm;
-            p.AT.ptr = q.AT.ptr; p.AT.col = q.AT.col; p.AT.perm = q.AT.perm;
-            p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
-        }
-    }
-    b->d64 = A.take<Args<double>>(B);
-    b->d32 = A.take<Args<float>>(B);
-    b->queue = A.take<int>(4);
+    auto tune_args = lay_all(true);
     if (cudaMemsetAsync(b->arena, 0, bytes, b->stream) != cudaSuccess) { set_err(b->err, "memset failed"); return fail(SCS_ECUDA); }
     for (int qi = 0; qi < B; ++qi) {
         const HostProb& h = b->H[b->order[qi]];
         if ((rc = upload<double>(h, b->a64[qi].P, true, b->stream, b->err))) return fail(rc);
         if (b->has32 && (rc = upload<float>(h, b->a32[qi].P, false, b->stream, b->err))) return fail(rc);
     }
+    if (cudaMemcpyAsync(b->off, b->hoff.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d64, b->a64.data(), sizeof(Args<double>) * B, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        (b->has32 && cudaMemcpyAsync(b->d32, b->a32.data(), sizeof(Args<float>) * B, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)) {
+        set_err(b->err, "descriptor upload failed");
+        return fail(SCS_ECUDA);
+    }
     DevSettings S = dev_settings(settings);
     S.cg_max = std::max(10 * settings->cg_max, 10000);
     DevSettings S64 = S, S32 = S;
     S64.cg_rtol = std::min(settings->cg_rtol, 1e-12);
     S32.cg_rtol = std::min(settings->cg_rtol, 1e-7);
-    if ((rc = batch_launch<double>(b, MODE_SETUP, S64, b->d64, b->a64, b->dyn64))) return fail(rc);
-    if (b->has32 && (rc = batch_launch<float>(b, MODE_SETUP, S32, b->d32, b->a32, b->dyn32))) return fail(rc);
+    // setup (g = M^{-1}(c, b)) with a provisional shape
+    b->threads = settings->threads ? settings->threads : 256;
+    b->grid = occupancy_grid(kblock_ptr<double>(), b->threads, b->dyn64, b->sms, B);
+    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+    CU(launch_block<double>(b->grid, b->threads, b->dyn64, b->stream, b->d64, B, b->queue, S64, MODE_SETUP), b->err);
+    if (b->has32) {
+        const int g32 = occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B);
+        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+        CU(launch_block<float>(g32, b->threads, b->dyn32, b->stream, b->d32, B, b->queue, S32, MODE_SETUP), b->err);
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        set_err(b->err, "batch setup kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SCS_ECUDA);
+    }
+    if (!settings->threads && B >= 64) {
+        if (b->has32) rc = autotune<float>(b, b->a32, b->dyn32, batch_settings<float>(b, true), tune_args.second);
+        else rc = autotune<double>(b, b->a64, b->dyn64, batch_settings<double>(b, false), tune_args.first);
+        if (rc) return fail(rc);
+    }
     b->setup_s = now_s() - t0;
     *out = b;
     return SCS_OK;
@@ -1018,6 +1107,10 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
 extern "C" void scs_batch_finish(scs_batch* b)
 {
     if (!b) return;
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->hpacked) cudaFreeHost(b->hpacked);
+    if (b->hst) cudaFreeHost(b->hst);
     if (b->arena) cudaFree(b->arena);
     delete b;
 }
@@ -1026,64 +1119,69 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
 {
     if (!b) { set_err(g_err, "batch is NULL"); return SCS_EINVAL; }
     const double t0 = now_s();
-    int rc;
-    for (int qi = 0; qi < b->B; ++qi) {
-        const HostProb& h = b->H[b->order[qi]];
-        CU(cudaMemsetAsync(b->a64[qi].W.ws[0], 0, sizeof(double) * h.n, b->stream), b->err);
-        CU(cudaMemsetAsync(b->a64[qi].W.ws[1], 0, sizeof(double) * h.n, b->stream), b->err);
-        if (b->has32) {
-            CU(cudaMemsetAsync(b->a32[qi].W.ws[0], 0, sizeof(float) * h.n, b->stream), b->err);
-            CU(cudaMemsetAsync(b->a32[qi].W.ws[1], 0, sizeof(float) * h.n, b->stream), b->err);
-        }
-    }
-    DevSettings S = dev_settings(&b->S);
-    std::vector<DevState> st32(b->B);
+    const int B = b->B;
+    float ms32 = 0.f, ms64 = 0.f;
     if (b->has32) {
-        DevSettings S32 = S;
-        S32.cg_rtol = b->S.mixed_cg_rtol > 0 ? b->S.mixed_cg_rtol : 1e-6;
-        S32.stall_iters = b->S.mixed_stall;
-        S32.switch_kkt = b->S.mixed_switch;
-        S32.max_iters = b->S.mixed_max_iters > 0 ? std::min(b->S.mixed_max_iters, b->S.max_iters) : b->S.max_iters;
-        if ((rc = batch_launch<float>(b, MODE_SOLVE, S32, b->d32, b->a32, b->dyn32))) return rc;
-        for (int qi = 0; qi < b->B; ++qi) {
-            const HostProb& h = b->H[b->order[qi]];
-            const int N = h.n + h.m + 1;
-            CU(cudaMemcpyAsync(b->a64[qi].W.warm, b->a32[qi].W.u_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, b->stream), b->err);
-            for (int k = 0; k < 2; ++k)
-                CU(launch_f2d(b->a32[qi].W.ws[k], b->a64[qi].W.ws[k], h.n, b->stream), b->err);
-            CU(cudaMemcpyAsync(&st32[qi], b->a32[qi].W.st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), b->err);
-        }
-        S.use_warm = 1;
+        const DevSettings S32 = batch_settings<float>(b, true);
+        const int g32 = occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B);
+        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+        CU(cudaEventRecord(b->ev[2], b->stream), b->err);
+        CU(launch_block<float>(g32, b->threads, b->dyn32, b->stream, b->d32, B, b->queue, S32, MODE_SOLVE), b->err);
+        CU(cudaEventRecord(b->ev[3], b->stream), b->err);
+        CU(launch_batch_handoff(b->d32, b->d64, B, b->stream), b->err);
     }
-    if ((rc = batch_launch<double>(b, MODE_SOLVE, S, b->d64, b->a64, b->dyn64))) return rc;
-    std::vector<DevState> st(b->B);
-    for (int qi = 0; qi < b->B; ++qi) {
+    DevSettings S = batch_settings<double>(b, false);
+    if (b->has32) {
+        S.use_warm = 1;
+        S.keep_ws = 1;
+    }
+    const int g64 = occupancy_grid(kblock_ptr<double>(), b->threads, b->dyn64, b->sms, B);
+    b->grid = g64;
+    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+    CU(cudaEventRecord(b->ev[0], b->stream), b->err);
+    CU(launch_block<double>(g64, b->threads, b->dyn64, b->stream, b->d64, B, b->queue, S, MODE_SOLVE), b->err);
+    CU(cudaEventRecord(b->ev[1], b->stream), b->err);
+    CU(launch_batch_pack(b->d64, B, b->off, b->packed, b->stream), b->err);
+    CU(cudaMemcpyAsync(b->hpacked, b->packed, sizeof(double) * b->packed_len, cudaMemcpyDeviceToHost, b->stream), b->err);
+    CU(cudaMemcpyAsync(b->hst, b->st64, sizeof(DevState) * B, cudaMemcpyDeviceToHost, b->stream), b->err);
+    if (b->has32) CU(cudaMemcpyAsync(b->hst + B, b->st32, sizeof(DevState) * B, cudaMemcpyDeviceToHost, b->stream), b->err);
+    CU(cudaStreamSynchronize(b->stream), b->err);
+    cudaEventElapsedTime(&ms64, b->ev[0], b->ev[1]);
+    if (b->has32) cudaEventElapsedTime(&ms32, b->ev[2], b->ev[3]);
+    for (int qi = 0; qi < B; ++qi) {
         const int i = b->order[qi];
         const HostProb& h = b->H[i];
-        CU(cudaMemcpyAsync(&st[qi], b->a64[qi].W.st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream), b->err);
-        if (x && x[i]) CU(cudaMemcpyAsync(x[i], b->a64[qi].W.x_out, sizeof(double) * h.n, cudaMemcpyDefault, b->stream), b->err);
-        if (y && y[i]) CU(cudaMemcpyAsync(y[i], b->a64[qi].W.y_out, sizeof(double) * h.m, cudaMemcpyDefault, b->stream), b->err);
-        if (s && s[i]) CU(cudaMemcpyAsync(s[i], b->a64[qi].W.s_out, sizeof(double) * h.m, cudaMemcpyDefault, b->stream), b->err);
+        const double* src = b->hpacked + b->hoff[qi];
+        if (x && x[i]) memcpy(x[i], src, sizeof(double) * h.n);
+        if (y && y[i]) memcpy(y[i], src + h.n, sizeof(double) * h.m);
+        if (s && s[i]) memcpy(s[i], src + h.n + h.m, sizeof(double) * h.m);
     }
-    CU(cudaStreamSynchronize(b->stream), b->err);
     const double el = now_s() - t0;
     if (infos) {
-        for (int qi = 0; qi < b->B; ++qi) {
+        for (int qi = 0; qi < B; ++qi) {
             const int i = b->order[qi];
             scs_info* info = &infos[i];
             memset(info, 0, sizeof(*info));
-            fill_info(info, st[qi]);
+            fill_info(info, b->hst[qi]);
+            info->mat_passes[0] = b->hst[qi].mat_passes;
+            info->kernel_s[0] = ms64 * 1e-3;
             if (b->has32) {
-                info->iters += st32[qi].iters;
-                info->iters_fp32 = st32[qi].iters;
-                info->k0 += st32[qi].k0;
-                info->k1 += st32[qi].k1;
-                info->k2 += st32[qi].k2;
-                info->backtracks += st32[qi].backtracks;
-                info->cg_iters += st32[qi].cg_iters;
+                const DevState& t = b->hst[B + qi];
+                info->iters += t.iters;
+                info->iters_fp32 = t.iters;
+                info->k0 += t.k0;
+                info->k1 += t.k1;
+                info->k2 += t.k2;
+                info->backtracks += t.backtracks;
+                info->cg_iters += t.cg_iters;
+                info->cg_iters_fp32 = t.cg_iters;
+                info->mat_passes[1] = t.mat_passes;
+                info->psd_resid_fp32 = t.psd_resid;
+                info->kernel_s[1] = ms32 * 1e-3;
             }
             info->setup_s = b->setup_s;
             info->solve_s = el;
+            info->threads_per_block = b->threads;
         }
     }
     return SCS_OK;

@@ -209,24 +209,25 @@ def portfolio(seed=0, k=None, gamma=1.0):
     Dg = rng.uniform(0.01, 0.1, k)
     mu = rng.normal(0.05, 0.02, k)
     n = k + 1
-    rows, cols, vals = [], [], []
-    # zero cone: 1^T w = 1
-    rows += [0] * k; cols += list(range(k)); vals += [1.0] * k
-    # orthant: s = w
-    rows += list(range(1, k + 1)); cols += list(range(k)); vals += [-1.0] * k
-    o = k + 1
-    # SOC (F^T w, D^{1/2} w, t)
-    for j in range(r):
-        rows += [o + j] * k; cols += list(range(k)); vals += list(-F[:, j])
-    o += r
-    rows += list(range(o, o + k)); cols += list(range(k)); vals += list(-np.sqrt(Dg))
-    o += k
-    rows += [o]; cols += [k]; vals += [-1.0]
-    m = o + 1
+    w = np.arange(k)
+    rows = np.concatenate([np.zeros(k, np.int64),              # zero cone: 1^T w = 1
+                           1 + w,                               # orthant: s = w
+                           (k + 1) + np.repeat(np.arange(r), k),  # SOC: F^T w
+                           (k + 1 + r) + w,                     # SOC: D^{1/2} w
+                           [2 * k + r + 1]])                    # SOC: t (last)
+    cols = np.concatenate([w, w, np.tile(w, r), w, [k]])
+    vals = np.concatenate([np.ones(k), -np.ones(k), -F.T.ravel(), -np.sqrt(Dg), [-1.0]])
+    m = 2 * k + r + 2
     A = _csr(rows, cols, vals, m, n)
-    b = np.zeros(m); b[0] = 1.0
+    b = np.zeros(m)
+    b[0] = 1.0
     c = np.concatenate([-mu, [gamma]])
     return dict(A=A, b=b, c=c, f=1, l=k, q=[r + k + 1], s=[], meta=dict(k=k, r=r))
+
+
+def c4_portfolios(count=4096, seed0=1000):
+    """The batched family: independent portfolio SOCPs with k ~ U{20..400}."""
+    return [portfolio(seed=seed0 + i) for i in range(count)]
 
 
 def infeasible(seed=0, n=200, l=200, soc=(10,) * 4, nnz=None):

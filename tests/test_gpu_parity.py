@@ -238,3 +238,47 @@ def test_residuals_entry_matches_numpy(team):
     rng = np.random.default_rng(4)
     xr, yr, sr = rng.standard_normal(work.n), rng.standard_normal(work.m), rng.standard_normal(work.m)
     np.testing.assert_allclose(work.residuals(xr, yr, sr), _kkt(prob, xr, yr, sr), rtol=1e-12)
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_psd_projection_large_blocks(team):
+    """PSD blocks up to the largest supported order (64), odd orders padded."""
+    prob = W.planted(seed=41, n=40, l=10, psd=[64, 33, 17, 2], nnz=2000)
+    work = B.Work(prob, team=team)
+    orc = O.Oracle(prob)
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        v = rng.standard_normal(work.N) * 2
+        np.testing.assert_allclose(work.project_cone(v), orc.proj_C(v), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+def test_planted_sdp_small(precision):
+    prob = W.planted(seed=42, n=300, l=200, psd=[16] * 6 + [9, 33], nnz=6000)
+    eps = 1e-5
+    work = B.Work(prob, precision=precision, eps=eps, max_iters=20000, cg_adapt=1e-2)
+    x, y, s, info = work.solve()
+    assert info["status"] == B.SOLVED, info
+    pr, dr, gap = _kkt(prob, x, y, s)
+    assert max(pr, dr, gap) <= eps * 1.01
+    check_in_cone(prob, s, dual=False, tol=1e-6)
+    check_in_cone(prob, y, dual=True, tol=1e-6)
+    pstar = prob["c"] @ prob["xstar"]
+    assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+    if precision == B.MIXED:
+        assert 0 < info["psd_resid_fp32"] < 1e-4  # FP64 recheck of the FP32 eigensolves
+
+
+def test_batch_autotuned_mixed():
+    probs = [W.portfolio(seed=500 + i, k=int(k)) for i, k in enumerate(np.linspace(20, 160, 96))]
+    eps = 1e-5
+    batch = B.Batch(probs, precision=B.MIXED, eps=eps, max_iters=20000, cg_adapt=1e-2)
+    xs, ys, ss, infos = batch.solve()
+    assert infos[0]["threads_per_block"] in (128, 256, 512)
+    for p, x, y, s, info in zip(probs, xs, ys, ss, infos):
+        assert info["status"] == B.SOLVED, info
+        assert max(_kkt(p, x, y, s)) <= eps * 1.01
+    # a second solve of the same batch gives the same answers
+    xs2, _, _, infos2 = batch.solve()
+    for a, b2 in zip(xs, xs2):
+        np.testing.assert_array_equal(a, b2)
