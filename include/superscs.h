@@ -108,6 +108,8 @@ typedef struct {
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
     int32_t spmv_path;      /* 0 or 1: direct streaming loads; 2: TMA-staged stream (grid team only) */
+    int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
+                               after this many iterations is abandoned for the cold start */
 } scs_settings;
 
 typedef struct {
@@ -128,6 +130,7 @@ typedef struct {
     double psd_resid_fp32; /* largest FP64-evaluated ||X V - V L||_F / ||X||_F of the FP32 PSD
                               eigensolves (SCS_MIXED with PSD cones) */
     int32_t threads_per_block; /* launch shape used (batches: chosen by the autotuner unless set) */
+    int32_t warm_fallback_taken; /* 1 if the warm start was abandoned for the cold start */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
@@ -233,6 +236,17 @@ int scs_batch_setup(int32_t B, const scs_data *const *data, const scs_cone *cons
 int scs_batch_solve(scs_batch *batch, double *const *x, double *const *y, double *const *s,
                     scs_info *infos);
 void scs_batch_finish(scs_batch *batch);
+/* A batch of B instances sharing the matrix A and cones of *data (its b and
+ * c are ignored) with instance i's b[i] (m) and c[i] (n): the matrix is
+ * prepared and stored once; everything else is as scs_batch_setup.  For
+ * parametric families such as the LASSO family of a fixed design matrix. */
+int scs_batch_setup_shared(int32_t B, const scs_data *data, const scs_cone *cone, const double *const *b,
+                           const double *const *c, const scs_settings *settings, void *cuda_stream,
+                           scs_batch **out);
+/* Warm starts for the next solves of the batch: u[i] (N_i values, host or
+ * device) is instance i's u0; u = NULL returns to cold starts.  Combined
+ * with settings->warm_fallback. */
+int scs_batch_set_warm(scs_batch *batch, const double *const *u);
 /* One-shot: setup, solve, finish. */
 int scs_solve_batch(int32_t B, const scs_data *const *data, const scs_cone *const *cones,
                     const scs_settings *settings, void *cuda_stream, double *const *x,

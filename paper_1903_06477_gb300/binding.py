@@ -43,6 +43,7 @@ class Settings(C.Structure):
         ("aa_reg", C.c_double), ("team", C.c_int32), ("threads", C.c_int32),
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
+        ("warm_fallback", C.c_int32),
     ]
 
 
@@ -54,7 +55,7 @@ class Info(C.Structure):
         ("pobj", C.c_double), ("dobj", C.c_double), ("setup_s", C.c_double), ("solve_s", C.c_double),
         ("err_vs_fp64", C.c_double), ("iters_fp32", C.c_int32), ("device_error", C.c_int32),
         ("kernel_s", C.c_double * 2), ("mat_passes", C.c_int64 * 2), ("cg_iters_fp32", C.c_int64),
-        ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32),
+        ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32), ("warm_fallback_taken", C.c_int32),
     ]
 
     def as_dict(self):
@@ -70,7 +71,7 @@ class SCSError(RuntimeError):
 
 _lib = None
 
-# (name, restype, argtypes) of every exported entry point of include/superscs.h
+# (name, restype, argtypes) of every exported entry point of include/superscs.h and superscs_mlp.h
 _SIGS = [
     ("scs_default_settings", C.c_int, [C.POINTER(Settings)]),
     ("scs_setup", C.c_int, [C.POINTER(Data), C.POINTER(Cone), C.POINTER(Settings), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -89,8 +90,23 @@ _SIGS = [
                                   C.POINTER(C.c_void_p)]),
     ("scs_batch_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     ("scs_batch_finish", None, [C.c_void_p]),
+    ("scs_batch_setup_shared", C.c_int, [C.c_int32, C.POINTER(Data), C.POINTER(Cone), C.c_void_p, C.c_void_p,
+                                         C.POINTER(Settings), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("scs_batch_set_warm", C.c_int, [C.c_void_p, C.c_void_p]),
     ("scs_solve_batch", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Settings), C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+    ("scs_mlp_create", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    ("scs_mlp_fit_normalization", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    ("scs_mlp_train_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                     C.POINTER(C.c_float)]),
+    ("scs_mlp_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("scs_mlp_gradients", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                    C.POINTER(C.c_float)]),
+    ("scs_mlp_num_params", C.c_int64, [C.c_void_p]),
+    ("scs_mlp_get_params", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("scs_mlp_set_params", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("scs_mlp_destroy", None, [C.c_void_p]),
 ]
 
 
@@ -252,19 +268,42 @@ class Work:
 
 
 class Batch:
-    """B independent problems solved by one persistent launch."""
+    """B independent problems solved by one persistent launch.  With
+    ``shared=(prob0, bs, cs)`` the instances share prob0's A and cones and
+    differ in b = bs[i], c = cs[i] (scs_batch_setup_shared)."""
 
-    def __init__(self, probs, settings: Settings | None = None, stream=None, **kw):
+    def __init__(self, probs=None, settings: Settings | None = None, stream=None, shared=None, **kw):
         L = lib()
-        self.keeps = [_Keep(p) for p in probs]
-        self.B = len(probs)
         self.settings = settings if settings is not None else default_settings(**kw)
-        self._dp = (C.POINTER(Data) * self.B)(*[C.pointer(k.data) for k in self.keeps])
-        self._cp = (C.POINTER(Cone) * self.B)(*[C.pointer(k.cone) for k in self.keeps])
         h = C.c_void_p()
         st = C.c_void_p(stream) if isinstance(stream, int) else (C.c_void_p(stream.cuda_stream) if stream is not None else None)
-        _check(L.scs_batch_setup(self.B, self._dp, self._cp, C.byref(self.settings), st, C.byref(h)))
+        if shared is not None:
+            prob0, bs, cs = shared
+            k0 = _Keep(prob0)
+            self.B = len(bs)
+            self._bs = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+            self._cs = [np.ascontiguousarray(c, dtype=np.float64) for c in cs]
+            self.keeps = [k0] * self.B
+            bp = (C.c_void_p * self.B)(*[b.ctypes.data for b in self._bs])
+            cp = (C.c_void_p * self.B)(*[c.ctypes.data for c in self._cs])
+            _check(L.scs_batch_setup_shared(self.B, C.byref(k0.data), C.byref(k0.cone), bp, cp,
+                                            C.byref(self.settings), st, C.byref(h)))
+        else:
+            self.keeps = [_Keep(p) for p in probs]
+            self.B = len(probs)
+            self._dp = (C.POINTER(Data) * self.B)(*[C.pointer(k.data) for k in self.keeps])
+            self._cp = (C.POINTER(Cone) * self.B)(*[C.pointer(k.cone) for k in self.keeps])
+            _check(L.scs_batch_setup(self.B, self._dp, self._cp, C.byref(self.settings), st, C.byref(h)))
         self.h = h
+
+    def set_warm(self, us):
+        """us: list of N-vectors (numpy or CUDA tensors) or None for cold starts."""
+        if us is None:
+            _check(lib().scs_batch_set_warm(self.h, None))
+            return
+        self._warm = [u if hasattr(u, "data_ptr") else np.ascontiguousarray(u, dtype=np.float64) for u in us]
+        arr = (C.c_void_p * self.B)(*[_ptr(u).value for u in self._warm])
+        _check(lib().scs_batch_set_warm(self.h, arr))
 
     def solve(self):
         xs = [np.empty(k.n) for k in self.keeps]
@@ -278,6 +317,59 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().scs_batch_finish(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned warm-start network (include/superscs_mlp.h).  Batches are
+    CUDA torch tensors (float32, row-major)."""
+
+    def __init__(self, d_in, d_hidden, d_out, max_batch, seed=0, stream=None):
+        h = C.c_void_p()
+        st = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(lib().scs_mlp_create(d_in, d_hidden, d_out, max_batch, seed, st, C.byref(h)))
+        self.h = h
+        self.dims = (d_in, d_hidden, d_out)
+
+    @property
+    def num_params(self):
+        return lib().scs_mlp_num_params(self.h)
+
+    def fit_normalization(self, X, Y):
+        _check(lib().scs_mlp_fit_normalization(self.h, _ptr(X), _ptr(Y), X.shape[0]))
+
+    def train_step(self, X, Y, lr):
+        loss = C.c_float()
+        _check(lib().scs_mlp_train_step(self.h, _ptr(X), _ptr(Y), X.shape[0], lr, C.byref(loss)))
+        return loss.value
+
+    def forward(self, X, out):
+        _check(lib().scs_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(out)))
+        return out
+
+    def gradients(self, X, Y, grad_out=None):
+        loss = C.c_float()
+        _check(lib().scs_mlp_gradients(self.h, _ptr(X), _ptr(Y), X.shape[0], _ptr(grad_out), C.byref(loss)))
+        return loss.value
+
+    def get_params(self):
+        p = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().scs_mlp_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().scs_mlp_set_params(self.h, _ptr(p)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().scs_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

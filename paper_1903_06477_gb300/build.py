@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsuperscs.so")
 UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_block_f64.cu", "kernels_block_f32.cu", "superscs.cu",
-         "residuals_static.cu"]
+         "residuals_static.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177"]
@@ -31,7 +31,7 @@ def _nvcc():
 
 def _sources():
     return (glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-            + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "superscs.h")])
+            + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def up_to_date() -> bool:

@@ -1,0 +1,631 @@
+// mlp.cu -- the learned warm start: a 3-layer MLP trained and evaluated
+// entirely by the kernels in this file (see include/superscs_mlp.h).
+//
+// GEMMs use the BF16 tensor-core MMA (m16n8k16, FP32 accumulation) on
+// 128x128x32 block tiles staged through shared memory by cp.async; every
+// product is written as C = A B^T with both operands K-contiguous, so the
+// backward pass works on transposed copies made by a tiled transpose kernel.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/superscs.h"
+#include "../../include/superscs_mlp.h"
+
+namespace sscs {
+void record_error(const char* msg);
+}
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int BM = 128, BN = 128, BK = 32, NTH = 256, SROW = BK + 8;  // 80-byte smem rows: ldmatrix conflict-free
+
+struct Epi {
+    const float* bias;  // per column, or null
+    const bf16* mask;   // relu' mask (value > 0 keeps), row-major with ldm, or null
+    int ldm;
+    int relu;
+    float* C32;         // FP32 output or null
+    int ldc;
+    bf16* C16;          // BF16 output or null
+    int ldc16;
+};
+
+__device__ __forceinline__ unsigned sa(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+// 16-byte async copy with zero fill of the bytes past src_bytes
+__device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(sa(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C[M x N] = A[M x K] * B[N x K]^T.  lda, ldb multiples of 8, A and B 16-byte
+// aligned; tails in M, N and K are zero-filled on load and masked on store.
+__global__ void __launch_bounds__(NTH) gemm_nt(int M, int N, int K, const bf16* __restrict__ A, int lda,
+                                               const bf16* __restrict__ Bm, int ldb, Epi e)
+{
+    __shared__ __align__(16) bf16 As[2][BM][SROW];
+    __shared__ __align__(16) bf16 Bs[2][BN][SROW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, 64 x 32 each
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    auto load = [&](int st, int k0) {
+        for (int c = tid; c < BM * (BK / 8); c += NTH) {
+            const int r = c >> 2, kc = (c & 3) * 8;
+            const int gk = k0 + kc;
+            int gm = m0 + r;
+            int bytes = (gm < M && gk < K) ? min(16, (K - gk) * 2) : 0;
+            const bf16* src = bytes ? A + (size_t)gm * lda + gk : A;
+            cp16(&As[st][r][kc], src, bytes);
+            const int gn = n0 + r;
+            bytes = (gn < N && gk < K) ? min(16, (K - gk) * 2) : 0;
+            src = bytes ? Bm + (size_t)gn * ldb + gk : Bm;
+            cp16(&Bs[st][r][kc], src, bytes);
+        }
+    };
+
+    const int KT = (K + BK - 1) / BK;
+    load(0, 0);
+    cp_commit();
+    for (int kt = 0; kt < KT; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < KT) {
+            load(st ^ 1, (kt + 1) * BK);
+            cp_commit();
+            cp_wait1();
+        } else {
+            cp_wait0();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned af[4][4];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                const int row = wm * 64 + mi * 16 + (lane & 15);
+                const int col = kk + (lane >> 4) * 8;
+                ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3], &As[st][row][col]);
+            }
+            unsigned bfr[4][2];
+#pragma unroll
+            for (int nj = 0; nj < 4; nj += 2) {
+                const int row = wn * 32 + nj * 8 + (lane & 7) + (lane >> 4) * 8;
+                const int col = kk + ((lane >> 3) & 1) * 8;
+                ldsm_x4(bfr[nj][0], bfr[nj][1], bfr[nj + 1][0], bfr[nj + 1][1], &Bs[st][row][col]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm * 64 + mi * 16 + g + h * 8;
+                if (m >= M) continue;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int n = n0 + wn * 32 + ni * 8 + 2 * t + q;
+                    if (n >= N) continue;
+                    float v = acc[mi][ni][h * 2 + q];
+                    if (e.bias) v += e.bias[n];
+                    if (e.mask && !((float)e.mask[(size_t)m * e.ldm + n] > 0.f)) v = 0.f;
+                    if (e.relu) v = fmaxf(v, 0.f);
+                    if (e.C32) e.C32[(size_t)m * e.ldc + n] = v;
+                    if (e.C16) e.C16[(size_t)m * e.ldc16 + n] = __float2bfloat16(v);
+                }
+            }
+}
+
+// out (C x R, ld_out) = in (R x C, ld_in)^T, BF16, 32 x 32 tiles
+__global__ void transpose_bf16(const bf16* in, int R, int C, int ld_in, bf16* out, int ld_out)
+{
+    __shared__ bf16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[i][threadIdx.x] = in[(size_t)r * ld_in + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * ld_out + r] = tile[threadIdx.x][i];
+    }
+}
+
+// Xn (bf16, ld) = (X - mean) / std, X row-major B x d
+__global__ void normalize_to_bf16(const float* X, int B, int d, const float* mean, const float* istd, bf16* out, int ld)
+{
+    const long long total = (long long)B * d;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / d), c = (int)(i % d);
+        out[(size_t)r * ld + c] = __float2bfloat16((X[i] - mean[c]) * istd[c]);
+    }
+}
+
+// loss partials and dy = (y - (t - mean)/std) / (B d): dy32 (B x d), dy16 (ld16)
+__global__ void loss_grad(const float* y, const float* tgt, int B, int d, const float* mean, const float* istd,
+                          float* dy32, bf16* dy16, int ld16, double* part)
+{
+    const long long total = (long long)B * d;
+    const float scale = 1.0f / (float)total;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / d), c = (int)(i % d);
+        const float diff = y[i] - (tgt[i] - mean[c]) * istd[c];
+        acc += (double)diff * diff;
+        const float g = diff * scale;
+        dy32[i] = g;
+        dy16[(size_t)r * ld16 + c] = __float2bfloat16(g);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void sum_partials(const double* part, int nb, double scale, double* out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t * scale;
+    }
+}
+
+// db[c] = sum_r D[r][c]
+__global__ void col_sums(const float* D, int B, int d, float* db)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d; c += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int r = 0; r < B; ++r) s += D[(size_t)r * d + c];
+        db[c] = s;
+    }
+}
+
+// Adam on all parameters; refreshes the BF16 copies of the weight matrices
+struct Seg {
+    long long off, len;
+    bf16* w16;  // BF16 copy or null for biases
+    int cols;   // row length of the matrix
+    int ld16;   // leading dimension of the BF16 copy
+};
+struct Segs {
+    Seg s[6];
+};
+__global__ void adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1c, float b2c, Segs segs)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / b1c) / (sqrtf(vi / b2c) + 1e-8f);
+        p[i] = pi;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (segs.s[k].w16 && i >= segs.s[k].off && i < segs.s[k].off + segs.s[k].len) {
+                const long long j = i - segs.s[k].off;
+                segs.s[k].w16[(j / segs.s[k].cols) * segs.s[k].ld16 + j % segs.s[k].cols] = __float2bfloat16(pi);
+            }
+    }
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+// uniform(-a, a) from a counter-based hash of (seed, index); zero outside [off, off+len) of weights
+__global__ void init_uniform(float* p, long long off, long long len, float a, unsigned long long seed)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long h = mix64(seed ^ mix64((unsigned long long)(off + i)));
+        const double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+        p[off + i] = (float)((2.0 * u - 1.0) * a);
+    }
+}
+
+// out (rows x cols, ld) = in (rows x cols, packed)
+__global__ void f32_to_bf16_2d(const float* in, long long rows, int cols, bf16* out, int ld)
+{
+    const long long n = rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[(i / cols) * ld + i % cols] = __float2bfloat16(in[i]);
+}
+
+// Y = y * std + mean (output units)
+__global__ void denormalize(const float* y, int B, int d, const float* mean, const float* stdv, float* Y)
+{
+    const long long total = (long long)B * d;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % d);
+        Y[i] = y[i] * stdv[c] + mean[c];
+    }
+}
+
+// per-column mean and inverse std (two passes in FP64), std < 1e-6 -> 1
+__global__ void col_stats(const float* X, long long rows, int d, float* mean, float* stdv, float* istd)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d; c += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (long long r = 0; r < rows; ++r) s += X[(size_t)r * d + c];
+        const double mu = s / (double)rows;
+        double q = 0.0;
+        for (long long r = 0; r < rows; ++r) {
+            const double e = X[(size_t)r * d + c] - mu;
+            q += e * e;
+        }
+        double sd = sqrt(q / (double)rows);
+        if (!(sd >= 1e-6)) sd = 1.0;
+        mean[c] = (float)mu;
+        stdv[c] = (float)sd;
+        istd[c] = (float)(1.0 / sd);
+    }
+}
+
+__global__ void fill_f32(float* p, long long n, float v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+int pad8(int x) { return (x + 7) & ~7; }
+int grid1d(long long n, int th = 256) { return (int)std::max<long long>(1, std::min<long long>((n + th - 1) / th, 8192)); }
+
+}  // namespace
+
+struct scs_mlp {
+    int din, dh, dout, maxB;
+    int ldin, ldout;  // padded leading dimensions (multiples of 8)
+    cudaStream_t st;
+    long long np;
+    long long oW1, ob1, oW2, ob2, oW3, ob3;
+    float *p, *g, *m, *v;                // parameters, gradients, Adam moments
+    bf16 *W1, *W2, *W3, *W2t, *W3t;      // BF16 copies (W2t: h x h, W3t: h x ldout)
+    float *in_mean, *in_std, *in_istd, *out_mean, *out_std, *out_istd;
+    bf16 *Xn, *Xnt, *h1, *h1t, *h2, *h2t, *dy16, *dyt, *dh2_16, *dh2t, *dh1_16, *dh1t;
+    float *y, *dy32, *dh2_32, *dh1_32;
+    double *part, *loss;
+    int step;
+    char* arena;
+};
+
+static int mlp_err(const char* what, cudaError_t e)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    sscs::record_error(buf);
+    return SCS_ECUDA;
+}
+#define MCU(x)                                          \
+    do {                                                \
+        cudaError_t e_ = (x);                           \
+        if (e_ != cudaSuccess) return mlp_err(#x, e_); \
+    } while (0)
+
+static int gemm(scs_mlp* n, int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const Epi& e)
+{
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_nt<<<grid, NTH, 0, n->st>>>(M, N, K, A, lda, B, ldb, e);
+    return cudaGetLastError() == cudaSuccess ? SCS_OK : mlp_err("gemm_nt launch", cudaGetLastError());
+}
+static void transpose(scs_mlp* n, const bf16* in, int R, int C, int ld_in, bf16* out, int ld_out)
+{
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    transpose_bf16<<<grid, block, 0, n->st>>>(in, R, C, ld_in, out, ld_out);
+}
+static Epi epi(const float* bias, const bf16* mask, int ldm, int relu, float* C32, int ldc, bf16* C16, int ldc16)
+{
+    Epi e;
+    e.bias = bias;
+    e.mask = mask;
+    e.ldm = ldm;
+    e.relu = relu;
+    e.C32 = C32;
+    e.ldc = ldc;
+    e.C16 = C16;
+    e.ldc16 = ldc16;
+    return e;
+}
+
+extern "C" int scs_mlp_create(int32_t din, int32_t dh, int32_t dout, int32_t maxB, uint64_t seed, void* stream,
+                              scs_mlp** out)
+{
+    if (!out || din <= 0 || dh <= 0 || dout <= 0 || maxB <= 0 || dh % 8 != 0) {
+        sscs::record_error("scs_mlp_create: bad sizes (all positive, d_hidden a multiple of 8)");
+        return SCS_EINVAL;
+    }
+    *out = nullptr;
+    scs_mlp* n = new (std::nothrow) scs_mlp();
+    if (!n) return SCS_ENOMEM;
+    memset(n, 0, sizeof(*n));
+    n->din = din;
+    n->dh = dh;
+    n->dout = dout;
+    n->maxB = maxB;
+    n->ldin = pad8(din);
+    n->ldout = pad8(dout);
+    n->st = (cudaStream_t)stream;
+    const int Bp = pad8(maxB);
+    n->oW1 = 0;
+    n->ob1 = n->oW1 + (long long)dh * din;
+    n->oW2 = n->ob1 + dh;
+    n->ob2 = n->oW2 + (long long)dh * dh;
+    n->oW3 = n->ob2 + dh;
+    n->ob3 = n->oW3 + (long long)dout * dh;
+    n->np = n->ob3 + dout;
+    // one arena
+    size_t off = 0;
+    std::vector<std::pair<void**, size_t>> plan;
+    auto take = [&](void** ptr, size_t bytes) { plan.push_back({ptr, bytes}); };
+    take((void**)&n->p, sizeof(float) * n->np);
+    take((void**)&n->g, sizeof(float) * n->np);
+    take((void**)&n->m, sizeof(float) * n->np);
+    take((void**)&n->v, sizeof(float) * n->np);
+    take((void**)&n->W1, sizeof(bf16) * (size_t)dh * n->ldin);
+    take((void**)&n->W2, sizeof(bf16) * (size_t)dh * dh);
+    take((void**)&n->W3, sizeof(bf16) * (size_t)dout * dh);
+    take((void**)&n->W2t, sizeof(bf16) * (size_t)dh * dh);
+    take((void**)&n->W3t, sizeof(bf16) * (size_t)dh * n->ldout);
+    take((void**)&n->in_mean, sizeof(float) * din);
+    take((void**)&n->in_std, sizeof(float) * din);
+    take((void**)&n->in_istd, sizeof(float) * din);
+    take((void**)&n->out_mean, sizeof(float) * dout);
+    take((void**)&n->out_std, sizeof(float) * dout);
+    take((void**)&n->out_istd, sizeof(float) * dout);
+    take((void**)&n->Xn, sizeof(bf16) * (size_t)maxB * n->ldin);
+    take((void**)&n->Xnt, sizeof(bf16) * (size_t)din * Bp);
+    take((void**)&n->h1, sizeof(bf16) * (size_t)maxB * dh);
+    take((void**)&n->h1t, sizeof(bf16) * (size_t)dh * Bp);
+    take((void**)&n->h2, sizeof(bf16) * (size_t)maxB * dh);
+    take((void**)&n->h2t, sizeof(bf16) * (size_t)dh * Bp);
+    take((void**)&n->dy16, sizeof(bf16) * (size_t)maxB * n->ldout);
+    take((void**)&n->dyt, sizeof(bf16) * (size_t)dout * Bp);
+    take((void**)&n->dh2_16, sizeof(bf16) * (size_t)maxB * dh);
+    take((void**)&n->dh2t, sizeof(bf16) * (size_t)dh * Bp);
+    take((void**)&n->dh1_16, sizeof(bf16) * (size_t)maxB * dh);
+    take((void**)&n->dh1t, sizeof(bf16) * (size_t)dh * Bp);
+    take((void**)&n->y, sizeof(float) * (size_t)maxB * dout);
+    take((void**)&n->dy32, sizeof(float) * (size_t)maxB * dout);
+    take((void**)&n->dh2_32, sizeof(float) * (size_t)maxB * dh);
+    take((void**)&n->dh1_32, sizeof(float) * (size_t)maxB * dh);
+    take((void**)&n->part, sizeof(double) * 8192);
+    take((void**)&n->loss, sizeof(double) * 2);
+    for (auto& pl : plan) off += (pl.second + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc((void**)&n->arena, off);
+    if (e != cudaSuccess) {
+        delete n;
+        return mlp_err("cudaMalloc", e);
+    }
+    size_t o = 0;
+    for (auto& pl : plan) {
+        *pl.first = n->arena + o;
+        o += (pl.second + 255) & ~size_t(255);
+    }
+    auto fail = [&](int rc) { scs_mlp_destroy(n); return rc; };
+    if (cudaMemsetAsync(n->arena, 0, off, n->st) != cudaSuccess) return fail(mlp_err("memset", cudaGetLastError()));
+    init_uniform<<<grid1d((long long)dh * din), 256, 0, n->st>>>(n->p, n->oW1, (long long)dh * din, 1.f / sqrtf((float)din), seed);
+    init_uniform<<<grid1d((long long)dh * dh), 256, 0, n->st>>>(n->p, n->oW2, (long long)dh * dh, 1.f / sqrtf((float)dh), seed);
+    init_uniform<<<grid1d((long long)dout * dh), 256, 0, n->st>>>(n->p, n->oW3, (long long)dout * dh, 1.f / sqrtf((float)dh), seed);
+    fill_f32<<<grid1d(din), 256, 0, n->st>>>(n->in_std, din, 1.f);
+    fill_f32<<<grid1d(din), 256, 0, n->st>>>(n->in_istd, din, 1.f);
+    fill_f32<<<grid1d(dout), 256, 0, n->st>>>(n->out_std, dout, 1.f);
+    fill_f32<<<grid1d(dout), 256, 0, n->st>>>(n->out_istd, dout, 1.f);
+    int rc = scs_mlp_set_params(n, nullptr);
+    if (rc) return fail(rc);
+    *out = n;
+    return SCS_OK;
+}
+
+// refresh the BF16 copies (and transposes) from the FP32 parameters
+static int refresh_bf16(scs_mlp* n)
+{
+    f32_to_bf16_2d<<<grid1d((long long)n->dh * n->din), 256, 0, n->st>>>(n->p + n->oW1, n->dh, n->din, n->W1, n->ldin);
+    f32_to_bf16_2d<<<grid1d((long long)n->dh * n->dh), 256, 0, n->st>>>(n->p + n->oW2, n->dh, n->dh, n->W2, n->dh);
+    f32_to_bf16_2d<<<grid1d((long long)n->dout * n->dh), 256, 0, n->st>>>(n->p + n->oW3, n->dout, n->dh, n->W3, n->dh);
+    transpose(n, n->W2, n->dh, n->dh, n->dh, n->W2t, n->dh);
+    transpose(n, n->W3, n->dout, n->dh, n->dh, n->W3t, n->ldout);
+    MCU(cudaGetLastError());
+    return SCS_OK;
+}
+
+extern "C" int64_t scs_mlp_num_params(const scs_mlp* n) { return n ? n->np : 0; }
+
+extern "C" int scs_mlp_get_params(scs_mlp* n, float* params)
+{
+    if (!n || !params) return SCS_EINVAL;
+    MCU(cudaMemcpyAsync(params, n->p, sizeof(float) * n->np, cudaMemcpyDefault, n->st));
+    MCU(cudaStreamSynchronize(n->st));
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_set_params(scs_mlp* n, const float* params)
+{
+    if (!n) return SCS_EINVAL;
+    if (params) MCU(cudaMemcpyAsync(n->p, params, sizeof(float) * n->np, cudaMemcpyDefault, n->st));
+    int rc = refresh_bf16(n);
+    if (rc) return rc;
+    MCU(cudaStreamSynchronize(n->st));
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_fit_normalization(scs_mlp* n, const float* X, const float* Y, int64_t rows)
+{
+    if (!n || !X || !Y || rows <= 0) return SCS_EINVAL;
+    col_stats<<<grid1d(n->din, 128), 128, 0, n->st>>>(X, rows, n->din, n->in_mean, n->in_std, n->in_istd);
+    col_stats<<<grid1d(n->dout, 128), 128, 0, n->st>>>(Y, rows, n->dout, n->out_mean, n->out_std, n->out_istd);
+    MCU(cudaGetLastError());
+    MCU(cudaStreamSynchronize(n->st));
+    return SCS_OK;
+}
+
+static int forward(scs_mlp* n, const float* X, int B)
+{
+    int rc;
+    normalize_to_bf16<<<grid1d((long long)B * n->din), 256, 0, n->st>>>(X, B, n->din, n->in_mean, n->in_istd, n->Xn, n->ldin);
+    if ((rc = gemm(n, B, n->dh, n->din, n->Xn, n->ldin, n->W1, n->ldin,
+                   epi(n->p + n->ob1, nullptr, 0, 1, nullptr, 0, n->h1, n->dh))))
+        return rc;
+    if ((rc = gemm(n, B, n->dh, n->dh, n->h1, n->dh, n->W2, n->dh,
+                   epi(n->p + n->ob2, nullptr, 0, 1, nullptr, 0, n->h2, n->dh))))
+        return rc;
+    if ((rc = gemm(n, B, n->dout, n->dh, n->h2, n->dh, n->W3, n->dh,
+                   epi(n->p + n->ob3, nullptr, 0, 0, n->y, n->dout, nullptr, 0))))
+        return rc;
+    return SCS_OK;
+}
+
+// loss and gradients into n->g; returns loss in *loss_host
+static int backward(scs_mlp* n, const float* Y, int B, float* loss_host)
+{
+    const int Bp = pad8(B);
+    const int nb = grid1d((long long)B * n->dout);
+    int rc;
+    loss_grad<<<nb, 256, 0, n->st>>>(n->y, Y, B, n->dout, n->out_mean, n->out_istd, n->dy32, n->dy16, n->ldout, n->part);
+    sum_partials<<<1, 256, 0, n->st>>>(n->part, nb, 0.5 / ((double)B * n->dout), n->loss);
+    transpose(n, n->dy16, B, n->dout, n->ldout, n->dyt, Bp);
+    transpose(n, n->h2, B, n->dh, n->dh, n->h2t, Bp);
+    transpose(n, n->h1, B, n->dh, n->dh, n->h1t, Bp);
+    transpose(n, n->Xn, B, n->din, n->ldin, n->Xnt, Bp);
+    // layer 3: gW3 = dy^T h2, gb3 = colsum(dy), dh2 = (dy W3) * [h2 > 0]
+    if ((rc = gemm(n, n->dout, n->dh, B, n->dyt, Bp, n->h2t, Bp, epi(nullptr, nullptr, 0, 0, n->g + n->oW3, n->dh, nullptr, 0))))
+        return rc;
+    col_sums<<<grid1d(n->dout), 256, 0, n->st>>>(n->dy32, B, n->dout, n->g + n->ob3);
+    if ((rc = gemm(n, B, n->dh, n->dout, n->dy16, n->ldout, n->W3t, n->ldout,
+                   epi(nullptr, n->h2, n->dh, 0, n->dh2_32, n->dh, n->dh2_16, n->dh))))
+        return rc;
+    // layer 2
+    transpose(n, n->dh2_16, B, n->dh, n->dh, n->dh2t, Bp);
+    if ((rc = gemm(n, n->dh, n->dh, B, n->dh2t, Bp, n->h1t, Bp, epi(nullptr, nullptr, 0, 0, n->g + n->oW2, n->dh, nullptr, 0))))
+        return rc;
+    col_sums<<<grid1d(n->dh), 256, 0, n->st>>>(n->dh2_32, B, n->dh, n->g + n->ob2);
+    if ((rc = gemm(n, B, n->dh, n->dh, n->dh2_16, n->dh, n->W2t, n->dh,
+                   epi(nullptr, n->h1, n->dh, 0, n->dh1_32, n->dh, n->dh1_16, n->dh))))
+        return rc;
+    // layer 1
+    transpose(n, n->dh1_16, B, n->dh, n->dh, n->dh1t, Bp);
+    if ((rc = gemm(n, n->dh, n->din, B, n->dh1t, Bp, n->Xnt, Bp, epi(nullptr, nullptr, 0, 0, n->g + n->oW1, n->din, nullptr, 0))))
+        return rc;
+    col_sums<<<grid1d(n->dh), 256, 0, n->st>>>(n->dh1_32, B, n->dh, n->g + n->ob1);
+    MCU(cudaGetLastError());
+    if (loss_host) {
+        double l = 0.0;
+        MCU(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->st));
+        MCU(cudaStreamSynchronize(n->st));
+        *loss_host = (float)l;
+    }
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_forward(scs_mlp* n, const float* X, int32_t B, float* Y)
+{
+    if (!n || !X || !Y || B <= 0 || B > n->maxB) {
+        sscs::record_error("scs_mlp_forward: bad arguments");
+        return SCS_EINVAL;
+    }
+    int rc = forward(n, X, B);
+    if (rc) return rc;
+    denormalize<<<grid1d((long long)B * n->dout), 256, 0, n->st>>>(n->y, B, n->dout, n->out_mean, n->out_std, Y);
+    MCU(cudaGetLastError());
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_gradients(scs_mlp* n, const float* X, const float* Y, int32_t B, float* grad, float* loss)
+{
+    if (!n || !X || !Y || B <= 0 || B > n->maxB) {
+        sscs::record_error("scs_mlp_gradients: bad arguments");
+        return SCS_EINVAL;
+    }
+    int rc = forward(n, X, B);
+    if (!rc) rc = backward(n, Y, B, loss);
+    if (rc) return rc;
+    if (grad) MCU(cudaMemcpyAsync(grad, n->g, sizeof(float) * n->np, cudaMemcpyDefault, n->st));
+    MCU(cudaStreamSynchronize(n->st));
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_train_step(scs_mlp* n, const float* X, const float* Y, int32_t B, float lr, float* loss)
+{
+    if (!n || !X || !Y || B <= 0 || B > n->maxB) {
+        sscs::record_error("scs_mlp_train_step: bad arguments");
+        return SCS_EINVAL;
+    }
+    int rc = forward(n, X, B);
+    if (!rc) rc = backward(n, Y, B, loss);
+    if (rc) return rc;
+    n->step++;
+    const float b1c = 1.f - powf(0.9f, (float)n->step), b2c = 1.f - powf(0.999f, (float)n->step);
+    Segs segs;
+    segs.s[0] = {n->oW1, (long long)n->dh * n->din, n->W1, n->din, n->ldin};
+    segs.s[1] = {n->ob1, n->dh, nullptr, 1, 1};
+    segs.s[2] = {n->oW2, (long long)n->dh * n->dh, n->W2, n->dh, n->dh};
+    segs.s[3] = {n->ob2, n->dh, nullptr, 1, 1};
+    segs.s[4] = {n->oW3, (long long)n->dout * n->dh, n->W3, n->dh, n->dh};
+    segs.s[5] = {n->ob3, n->dout, nullptr, 1, 1};
+    adam<<<grid1d(n->np), 256, 0, n->st>>>(n->p, n->g, n->m, n->v, n->np, lr, b1c, b2c, segs);
+    transpose(n, n->W2, n->dh, n->dh, n->dh, n->W2t, n->dh);
+    transpose(n, n->W3, n->dout, n->dh, n->dh, n->W3t, n->ldout);
+    MCU(cudaGetLastError());
+    return SCS_OK;
+}
+
+extern "C" void scs_mlp_destroy(scs_mlp* n)
+{
+    if (!n) return;
+    if (n->arena) cudaFree(n->arena);
+    delete n;
+}

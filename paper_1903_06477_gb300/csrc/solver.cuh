@@ -41,6 +41,8 @@ struct DevSettings {
     double switch_kkt;     // > 0: stop (hand over) once max(pr,dr,gap) <= switch_kkt
     double cg_adapt;       // > 0: CG inside the loop also stops at ||res|| <= cg_adapt ||Ru||
     int keep_ws;           // 1: keep the CG warm starts found in ws (handed over by the FP32 phase)
+    int warm_fallback;     // > 0 with a warm start: restart cold if ||Ru|| is not below the cold
+                           // start's ||Ru0|| after this many iterations
 };
 
 struct DevState {
@@ -50,6 +52,8 @@ struct DevState {
     int setup_cg, pad;
     long long mat_passes;  // SpMV passes over A or A^T
     double psd_resid;      // largest ||X V - V L||_F / ||X||_F of the FP32 eigensolves, in FP64
+    int fallback;          // 1 if the warm start was abandoned for the cold start
+    int pad2;
 };
 
 // Sliced ELL with row sorting (SELL-H-sigma) and V lanes per row, H = 32 / V
@@ -1200,13 +1204,16 @@ __device__ void write_outputs(Team& tm, const DevProb<T>& P, const DevWork<T>& W
 // K1; secant pair z = w - u, xi = Rw - Ru of the last evaluated w; after K2
 // the new u~ is solved from the new u; termination before the direction.
 // ---------------------------------------------------------------------------
+// Returns 1 (and writes no result) when a warm start is abandoned for the
+// cold start; the caller then runs it again cold with the counts carried over.
 template <typename T, class Team>
-__device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, double* G,
-                         double* sm_rhs, double* sm_L, double* sm_t, unsigned char* psd)
+__device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, double* G,
+                        double* sm_rhs, double* sm_L, double* sm_t, unsigned char* psd, bool use_warm,
+                        int iter_base, long long cg_base, int& iters_out, long long& cg_out)
 {
     const int n = P.n, m = P.m, nm = n + m;
     const double hg = W.st->hg;
-    long long cg_total = 0;
+    long long cg_total = cg_base;
     int k0 = 0, k1 = 0, k2 = 0, bt = 0;
     const double deadline = S.time_limit_ns > 0.0 ? (double)gtimer() + S.time_limit_ns : 0.0;
     // CG warm starts from zero unless the previous phase handed them over
@@ -1215,13 +1222,28 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             W.ws[0][i] = T(0);
             W.ws[1][i] = T(0);
         }
-    if (tm.leader()) {
+    if (tm.leader() && iter_base == 0) {
         W.st->mat_passes = 0;
         W.st->psd_resid = 0.0;
+        W.st->fallback = 0;
+    }
+    // residual of the cold start, the yardstick of the warm-start fallback
+    double nRu_cold = INFINITY;
+    const bool watch = use_warm && S.warm_fallback > 0;
+    if (watch) {
+        for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = T(0);
+        if (tm.leader()) *W.u.t = 1.0;
+        tm.sync();
+        cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+        OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
+        project_pass(tm, P, op, psd, &W.st->psd_resid);
+        double red[1] = {(double)op.acc0};
+        tm.reduce(red);
+        nRu_cold = sqrt(red[0]);
     }
     // u0
-    for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = S.use_warm ? (T)W.warm[i] : T(0);
-    if (tm.leader()) *W.u.t = S.use_warm ? W.warm[nm] : 1.0;
+    for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = use_warm ? (T)W.warm[i] : T(0);
+    if (tm.leader()) *W.u.t = use_warm ? W.warm[nm] : 1.0;
     tm.sync();
     cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
     double nRu;
@@ -1246,9 +1268,19 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
     const int check_every = S.check_every > 0 ? S.check_every : 1;
     bool need_final_check = true;
     int nu;
-    for (nu = 0; nu < S.max_iters; ++nu) {
+    for (nu = 0; nu < S.max_iters - iter_base; ++nu) {
         if (tm.aborted()) break;
+        if (watch && nu == S.warm_fallback && !(nRu < nRu_cold)) {
+            iters_out = iter_base + nu;
+            cg_out = cg_total;
+            return 1;
+        }
         if (!isfinite(nRu)) {
+            if (watch) {
+                iters_out = iter_base + nu;
+                cg_out = cg_total;
+                return 1;
+            }
             status = ST_NUMERICAL;
             break;
         }
@@ -1387,10 +1419,12 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
         if (st != 0 && status != ST_NUMERICAL) status = st;
     }
     write_outputs(tm, P, W, status, to);
+    iters_out = iter_base + nu;
+    cg_out = cg_total;
     if (tm.leader()) {
         DevState* st = W.st;
         st->status = status;
-        st->iters = nu;
+        st->iters = iter_base + nu;
         st->k0 = k0;
         st->k1 = k1;
         st->k2 = k2;
@@ -1410,6 +1444,7 @@ __device__ void superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             st->dobj = NAN;
         }
     }
+    return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1438,7 +1473,13 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
         return;
     }
     if (mode == MODE_SOLVE) {
-        superscs(tm, P, W, S, G, sm_rhs, sm_L, sm_t, psd);
+        int its = 0;
+        long long cgs = 0;
+        if (superscs(tm, P, W, S, G, sm_rhs, sm_L, sm_t, psd, S.use_warm != 0, 0, 0, its, cgs)) {
+            // the warm start did not beat the cold start's residual: restart cold
+            superscs(tm, P, W, S, G, sm_rhs, sm_L, sm_t, psd, false, its, cgs, its, cgs);
+            if (tm.leader()) W.st->fallback = 1;
+        }
         return;
     }
     if (mode == MODE_RESID) {

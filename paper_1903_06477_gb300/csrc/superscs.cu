@@ -351,7 +351,7 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
 }
 
 template <typename T>
-static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t st, char* err)
+static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t st, char* err, bool matrix = true)
 {
     auto put_i = [&](const std::vector<int>& v, const int* dst) -> int {
         if (!v.empty()) CU(cudaMemcpyAsync((void*)dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st), err);
@@ -371,6 +371,11 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         return SCS_OK;
     };
     int rc;
+    if (!matrix) {
+        if ((rc = put_t(H.b, P.b)) || (rc = put_t(H.c, P.c))) return rc;
+        CU(cudaStreamSynchronize(st), err);
+        return SCS_OK;
+    }
     if (idx) {
         if ((rc = put_i(H.SA.ptr, P.A.ptr)) || (rc = put_i(H.SA.col, P.A.col)) || (rc = put_i(H.SA.perm, P.A.perm)) ||
             (rc = put_i(H.ST.ptr, P.AT.ptr)) || (rc = put_i(H.ST.col, P.AT.col)) || (rc = put_i(H.ST.perm, P.AT.perm)) ||
@@ -409,6 +414,7 @@ static DevSettings dev_settings(const scs_settings* S)
     D.switch_kkt = 0.0;
     D.cg_adapt = S->cg_adapt;
     D.keep_ws = 0;
+    D.warm_fallback = S->warm_fallback;
     return D;
 }
 
@@ -512,6 +518,7 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->mixed_switch = 0.0;
     o->cg_adapt = 0.0;
     o->spmv_path = 0;
+    o->warm_fallback = 0;
     return SCS_OK;
 }
 
@@ -657,6 +664,7 @@ extern "C" const char* scs_last_error(const scs_work* w) { return w ? w->err : g
 
 static void fill_info(scs_info* info, const DevState& s)
 {
+    info->warm_fallback_taken = s.fallback;
     info->status = s.status;
     info->iters = s.iters;
     info->k0 = s.k0;
@@ -705,6 +713,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         }
         S.use_warm = 1;
         S.keep_ws = 1;
+        S.warm_fallback = 0;
         CU(cudaMemcpyAsync(&st32, w->W32.st, sizeof(DevState), cudaMemcpyDeviceToHost, w->stream), w->err);
     }
     Args<double> a = make_args(w->P64, w->W64, S, MODE_SOLVE);
@@ -725,6 +734,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         memset(info, 0, sizeof(*info));
         fill_info(info, st);
         if (w->has32) {
+            info->warm_fallback_taken |= st32.fallback;
             info->iters += st32.iters;
             info->iters_fp32 = st32.iters;
             info->k0 += st32.k0;
@@ -878,6 +888,8 @@ struct scs_batch {
     int threads = 256, grid = 1, sms = 1;
     bool autotuned = false;
     bool has32 = false;
+    bool shared = false;  // all instances share instance 0's matrix arrays
+    bool use_warm = false;
     size_t dyn64 = 0, dyn32 = 0;
     std::vector<Args<double>> a64;
     std::vector<Args<float>> a32;
@@ -951,6 +963,8 @@ static int autotune(scs_batch* b, const std::vector<Args<T>>& host_args, size_t 
     return SCS_OK;
 }
 
+static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_batch** out, double t0);
+
 extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs_cone* const* cones,
                                const scs_settings* settings, void* cuda_stream, scs_batch** out)
 {
@@ -977,6 +991,14 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
             return rc;
         }
     }
+    return batch_finish_setup(b, settings, out, t0);
+}
+
+// common part of the batch setups once every b->H[i] is prepared
+static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_batch** out, double t0)
+{
+    const int B = b->B;
+    int rc = 0;
     b->order.resize(B);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
@@ -1012,6 +1034,13 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
             const HostProb& h = b->H[b->order[qi]];
             lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
             b->a64[qi].slot = 0;
+            if (real && b->shared && qi > 0) {
+                b->a64[qi].P.A = b->a64[0].P.A;
+                b->a64[qi].P.AT = b->a64[0].P.AT;
+                b->a64[qi].P.q_off = b->a64[0].P.q_off;
+                b->a64[qi].P.s_dim = b->a64[0].P.s_dim;
+                b->a64[qi].P.s_off = b->a64[0].P.s_off;
+            }
             if (b->has32) {
                 lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
                 b->a32[qi].slot = 0;
@@ -1021,6 +1050,10 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
                     p.A.ptr = q.A.ptr; p.A.col = q.A.col; p.A.perm = q.A.perm; p.A.wbnd = q.A.wbnd;
                     p.AT.ptr = q.AT.ptr; p.AT.col = q.AT.col; p.AT.perm = q.AT.perm; p.AT.wbnd = q.AT.wbnd;
                     p.q_off = q.q_off; p.s_dim = q.s_dim; p.s_off = q.s_off;
+                    if (b->shared && qi > 0) {
+                        p.A.val = b->a32[0].P.A.val;
+                        p.AT.val = b->a32[0].P.AT.val;
+                    }
                 }
             }
         }
@@ -1066,8 +1099,9 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
     if (cudaMemsetAsync(b->arena, 0, bytes, b->stream) != cudaSuccess) { set_err(b->err, "memset failed"); return fail(SCS_ECUDA); }
     for (int qi = 0; qi < B; ++qi) {
         const HostProb& h = b->H[b->order[qi]];
-        if ((rc = upload<double>(h, b->a64[qi].P, true, b->stream, b->err))) return fail(rc);
-        if (b->has32 && (rc = upload<float>(h, b->a32[qi].P, false, b->stream, b->err))) return fail(rc);
+        const bool mat = !b->shared || qi == 0;
+        if ((rc = upload<double>(h, b->a64[qi].P, true, b->stream, b->err, mat))) return fail(rc);
+        if (b->has32 && (rc = upload<float>(h, b->a32[qi].P, false, b->stream, b->err, mat))) return fail(rc);
     }
     if (cudaMemcpyAsync(b->off, b->hoff.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->d64, b->a64.data(), sizeof(Args<double>) * B, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
@@ -1104,6 +1138,63 @@ extern "C" int scs_batch_setup(int32_t B, const scs_data* const* data, const scs
     return SCS_OK;
 }
 
+extern "C" int scs_batch_setup_shared(int32_t B, const scs_data* data, const scs_cone* cone, const double* const* bv,
+                                      const double* const* cv, const scs_settings* settings, void* cuda_stream,
+                                      scs_batch** out)
+{
+    if (!out) { set_err(g_err, "out must not be NULL"); return SCS_EINVAL; }
+    *out = nullptr;
+    if (B <= 0 || !data || !cone || !bv || !cv) { set_err(g_err, "bad batch arguments"); return SCS_EINVAL; }
+    const double t0 = now_s();
+    scs_batch* b = new (std::nothrow) scs_batch();
+    if (!b) return SCS_ENOMEM;
+    b->err[0] = 0;
+    int rc = check_settings(settings, b->err);
+    if (rc) { memcpy(g_err, b->err, 512); delete b; return rc; }
+    b->B = B;
+    b->S = *settings;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->shared = true;
+    b->H.resize(B);
+    if ((rc = prepare(data, cone, b->H[0], b->err))) { memcpy(g_err, b->err, 512); delete b; return rc; }
+    for (int i = 0; i < B; ++i) {
+        HostProb& h = b->H[i];
+        if (i > 0) {  // light copy: sizes and cones; the matrix stays with instance 0
+            const HostProb& h0 = b->H[0];
+            h.n = h0.n; h.m = h0.m; h.nnz = h0.nnz; h.f = h0.f; h.l = h0.l;
+            h.q = h0.q; h.s = h0.s; h.q_off = h0.q_off; h.s_off = h0.s_off; h.vecA = h0.vecA; h.vecT = h0.vecT;
+            h.SA.rows = h0.SA.rows; h.SA.V = h0.SA.V; h.SA.nslices = h0.SA.nslices;
+            h.ST.rows = h0.ST.rows; h.ST.V = h0.ST.V; h.ST.nslices = h0.ST.nslices;
+        }
+        if (!bv[i] || !cv[i]) { set_err(b->err, "instance %d: NULL b or c", i); memcpy(g_err, b->err, 512); delete b; return SCS_EINVAL; }
+        h.b.assign(bv[i], bv[i] + h.m);
+        h.c.assign(cv[i], cv[i] + h.n);
+        double sb = 0, sc = 0;
+        for (double v : h.b) { if (!std::isfinite(v)) { set_err(b->err, "instance %d: non-finite b", i); memcpy(g_err, b->err, 512); delete b; return SCS_EINVAL; } sb += v * v; }
+        for (double v : h.c) { if (!std::isfinite(v)) { set_err(b->err, "instance %d: non-finite c", i); memcpy(g_err, b->err, 512); delete b; return SCS_EINVAL; } sc += v * v; }
+        h.nb = std::sqrt(sb);
+        h.nc = std::sqrt(sc);
+    }
+    return batch_finish_setup(b, settings, out, t0);
+}
+
+extern "C" int scs_batch_set_warm(scs_batch* b, const double* const* u)
+{
+    if (!b) { set_err(g_err, "batch is NULL"); return SCS_EINVAL; }
+    if (!u) { b->use_warm = false; return SCS_OK; }
+    for (int qi = 0; qi < b->B; ++qi) {
+        const int i = b->order[qi];
+        const HostProb& h = b->H[i];
+        const size_t N = (size_t)h.n + h.m + 1;
+        if (!u[i]) { set_err(b->err, "instance %d: NULL warm start", i); return SCS_EINVAL; }
+        CU(cudaMemcpyAsync(b->a64[qi].W.warm, u[i], sizeof(double) * N, cudaMemcpyDefault, b->stream), b->err);
+        if (b->has32) CU(cudaMemcpyAsync(b->a32[qi].W.warm, u[i], sizeof(double) * N, cudaMemcpyDefault, b->stream), b->err);
+    }
+    CU(cudaStreamSynchronize(b->stream), b->err);
+    b->use_warm = true;
+    return SCS_OK;
+}
+
 extern "C" void scs_batch_finish(scs_batch* b)
 {
     if (!b) return;
@@ -1122,7 +1213,8 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
     const int B = b->B;
     float ms32 = 0.f, ms64 = 0.f;
     if (b->has32) {
-        const DevSettings S32 = batch_settings<float>(b, true);
+        DevSettings S32 = batch_settings<float>(b, true);
+        S32.use_warm = b->use_warm ? 1 : 0;
         const int g32 = occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B);
         CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
         CU(cudaEventRecord(b->ev[2], b->stream), b->err);
@@ -1134,6 +1226,9 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
     if (b->has32) {
         S.use_warm = 1;
         S.keep_ws = 1;
+        S.warm_fallback = 0;
+    } else {
+        S.use_warm = b->use_warm ? 1 : 0;
     }
     const int g64 = occupancy_grid(kblock_ptr<double>(), b->threads, b->dyn64, b->sms, B);
     b->grid = g64;
@@ -1167,6 +1262,7 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
             info->kernel_s[0] = ms64 * 1e-3;
             if (b->has32) {
                 const DevState& t = b->hst[B + qi];
+                info->warm_fallback_taken |= t.fallback;
                 info->iters += t.iters;
                 info->iters_fp32 = t.iters;
                 info->k0 += t.k0;

@@ -288,3 +288,13 @@ def lasso_family_rhs(F, seed, frac_nz=0.05, noise=0.01):
     idx = rng.choice(nvar, size=k, replace=False)
     x[idx] = rng.standard_normal(k)
     return F @ x + noise * rng.standard_normal(F.shape[0])
+
+
+def lasso_family_bc(F, g, mu_frac=0.1):
+    """b and c of the epigraph LASSO cone program (same layout as lasso())
+    for the design F and parameter g; mu = mu_frac ||F^T g||_inf."""
+    p, nvar = F.shape
+    mu = mu_frac * np.max(np.abs(F.T @ g))
+    b = np.concatenate([np.zeros(2 * nvar), -math.sqrt(2.0) * np.asarray(g, np.float64), [-1.0, 1.0]])
+    c = np.concatenate([np.zeros(nvar), mu * np.ones(nvar), [1.0]])
+    return b, c

@@ -21,8 +21,8 @@ def test_library_exports_every_declared_symbol():
     if not os.path.exists(binding.LIB_PATH):
         pytest.skip("libsuperscs.so not built (run __graft_entry__.build())")
     L = ctypes.CDLL(binding.LIB_PATH)
-    names = _declared("superscs.h")
-    assert len(names) >= 14
+    names = sorted(set(_declared("superscs.h")) | set(_declared("superscs_mlp.h")))
+    assert len(names) >= 24
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
     # the binding wraps every declared entry point
