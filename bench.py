@@ -253,6 +253,107 @@ def run_batch(args):
     return 0
 
 
+def run_c5(args):
+    """Learned warm start on the parametric LASSO family (F 2000 x 5000 at 1%,
+    g = F x + 0.01 N(0,1), x 5% sparse): solutions of the family generated by
+    the batched solver (shared A), the MLP 2000 -> 1024 -> 1024 -> 22004
+    trained by the library's kernels, then batches of 256 held-out instances
+    solved cold and warm (network output as u0, cold-start fallback)."""
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    from paper_1903_06477_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    F = W.lasso_family_matrix(seed=0)
+    eps = 1e-5
+    kw = dict(precision=B.MIXED, eps=eps, max_iters=20000, cg_adapt=1e-2, mixed_switch=1e-5)
+    prob0 = W.lasso(F=F, g=W.lasso_family_rhs(F, seed=1))
+
+    def batch_of(gs):
+        bcs = [W.lasso_family_bc(F, g) for g in gs]
+        return B.Batch(shared=(prob0, [b for b, _ in bcs], [c for _, c in bcs]), **kw)
+
+    # training solutions
+    t0 = time.perf_counter()
+    G, U, gen_iters = [], [], []
+    chunk = min(args.c5_train, 2048)
+    for c0 in range(0, args.c5_train, chunk):
+        gs = [W.lasso_family_rhs(F, seed=100_000 + i) for i in range(c0, min(args.c5_train, c0 + chunk))]
+        bt = batch_of(gs)
+        xs, ys, ss, infos = bt.solve()
+        bt.close()
+        for g, x, y, s_, inf in zip(gs, xs, ys, ss, infos):
+            if inf["status"] == B.SOLVED:
+                G.append(g.astype(np.float32))
+                U.append(np.concatenate([x, y + s_, [1.0]]).astype(np.float32))
+                gen_iters.append(inf["iters"])
+    gen_s = time.perf_counter() - t0
+    Xd = torch.as_tensor(np.stack(G), device="cuda")
+    Ud = torch.as_tensor(np.stack(U), device="cuda")
+    del G, U
+    net = B.MLP(Xd.shape[1], 1024, Ud.shape[1], max_batch=256, seed=11)
+    net.fit_normalization(Xd, Ud)
+    t0 = time.perf_counter()
+    lr, losses = 1e-3, []
+    nb = Xd.shape[0] // 256
+    for ep in range(args.c5_epochs):
+        perm = torch.randperm(Xd.shape[0], device="cuda")
+        el = 0.0
+        for i in range(nb):
+            idx = perm[i * 256:(i + 1) * 256]
+            el += net.train_step(Xd[idx].contiguous(), Ud[idx].contiguous(), lr)
+        losses.append(el / max(nb, 1))
+        lr *= 0.93
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # held-out batches of 256: cold vs warm
+    gte = [W.lasso_family_rhs(F, seed=900_000 + j) for j in range(256)]
+    Xt = torch.as_tensor(np.stack(gte).astype(np.float32), device="cuda")
+    Yt = torch.empty(256, Ud.shape[1], device="cuda")
+    cold_b = batch_of(gte)
+    warm_b = batch_of(gte)
+    for _ in range(max(1, args.warmup)):
+        cold_b.solve()
+    cold_t, warm_t, inf_t = [], [], []
+    cold_i = warm_i = None
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, _, cold_i = cold_b.solve()
+            cold_t.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            net.forward(Xt, Yt)
+            Yd = Yt.double()
+            Yd[:, -1] = 1.0
+            warm_b.set_warm([Yd[j] for j in range(256)])
+            torch.cuda.synchronize()
+            inf_t.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            _, _, _, warm_i = warm_b.solve()
+            warm_t.append(time.perf_counter() - t0)
+    tc, tw, ti = float(np.mean(cold_t)), float(np.mean(warm_t)), float(np.mean(inf_t))
+    line = {
+        "metric": METRIC, "value": 256.0 / (tw + ti), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (tw + ti) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 solve, bf16 MLP", "data": "synthetic",
+        "config": {"workload": "parametric LASSO F 2000x5000 1% (n=10001, m=12002), batches of 256 held-out "
+                               "instances, MLP 2000-1024-1024-22004", "train_instances": int(Xd.shape[0]),
+                   "epochs": args.c5_epochs, "eps": eps},
+        "cold_solves_per_s": 256.0 / tc, "warm_solves_per_s_incl_inference": 256.0 / (tw + ti),
+        "speedup_warm_vs_cold": tc / (tw + ti),
+        "median_iters_cold": float(np.median([i["iters"] for i in cold_i])),
+        "median_iters_warm": float(np.median([i["iters"] for i in warm_i])),
+        "fallbacks": int(sum(i["warm_fallback_taken"] for i in warm_i)),
+        "solved_cold": int(sum(i["status"] == B.SOLVED for i in cold_i)),
+        "solved_warm": int(sum(i["status"] == B.SOLVED for i in warm_i)),
+        "inference_ms": ti * 1e3, "gen_s": gen_s, "gen_solves_per_s": args.c5_train / gen_s,
+        "gen_median_iters": float(np.median(gen_iters)), "train_s": train_s, "loss_first": losses[0],
+        "loss_last": losses[-1], "gpu_launches": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,11 +369,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
     ap.add_argument("--cg-adapt", type=float, default=None)
     ap.add_argument("--mixed-switch", type=float, default=None)
+    ap.add_argument("--c5-train", type=int, default=4096, help="training instances of the learned warm start")
+    ap.add_argument("--c5-epochs", type=int, default=40)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_c5(args)
 
     import torch
     from paper_1903_06477_gb300 import binding as B

@@ -163,6 +163,10 @@ int scs_update_bc(scs_work *work, const double *b, const double *c);
  * and checkpoint/resume (any u0 converges, Sec. 4.5). */
 int scs_get_u(scs_work *work, double *u);
 
+/* u0 of the next solves: u (N values, host or device) is copied now; NULL
+ * returns to the cold start (0, 0, 1).  Combined with settings->warm_fallback. */
+int scs_set_warm(scs_work *work, const double *u);
+
 /* Relative primal residual, dual residual and duality gap of Sec. 4.3 for a
  * caller's candidate (x, y, s) on the work's data:
  *   out[0] = ||A x + s - b|| / (1 + ||b||),  out[1] = ||A^T y + c|| / (1 + ||c||),

@@ -78,6 +78,7 @@ _SIGS = [
     ("scs_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     ("scs_update_bc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_get_u", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("scs_set_warm", C.c_int, [C.c_void_p, C.c_void_p]),
     ("scs_linsys", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -205,15 +206,12 @@ class Work:
             pass
 
     def set_warm(self, u):
-        """Warm start from an HSDE iterate u (N values); None for a cold start."""
+        """Warm start from an HSDE iterate u (N values, numpy or CUDA); None for a cold start."""
         if u is None:
-            self.settings.warm = 0
-            self.settings.warm_u = None
-            self._warm = None
-        else:
-            self._warm = u if hasattr(u, "data_ptr") else np.ascontiguousarray(u, dtype=np.float64)
-            self.settings.warm = 1
-            self.settings.warm_u = _ptr(self._warm).value
+            _check(lib().scs_set_warm(self.h, None), self.h)
+            return
+        u = u if hasattr(u, "data_ptr") else np.ascontiguousarray(u, dtype=np.float64)
+        _check(lib().scs_set_warm(self.h, _ptr(u)), self.h)
 
     def solve(self, x=None, y=None, s=None):
         """Returns (x, y, s, info dict); outputs may be preallocated host or device buffers."""

@@ -693,6 +693,8 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         if (!w->S.warm_u) { set_err(w->err, "warm = 1 needs warm_u"); return SCS_EINVAL; }
         CU(cudaMemcpyAsync(w->W64.warm, w->S.warm_u, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
         S.use_warm = 1;
+    } else if (w->S.warm == 2) {
+        S.use_warm = 1;  // set by scs_set_warm
     }
     DevState st32{};
     if (w->has32) {
@@ -767,6 +769,22 @@ extern "C" int scs_get_u(scs_work* w, double* u)
     const int N = w->H.n + w->H.m + 1;
     CU(cudaMemcpyAsync(u, w->W64.u_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_set_warm(scs_work* w, const double* u)
+{
+    if (!w) { set_err(g_err, "work is NULL"); return SCS_EINVAL; }
+    if (!u) {
+        w->S.warm = 0;
+        w->S.warm_u = nullptr;
+        return SCS_OK;
+    }
+    const int N = w->H.n + w->H.m + 1;
+    CU(cudaMemcpyAsync(w->W64.warm, u, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    w->S.warm = 2;  // already on the device
+    w->S.warm_u = nullptr;
     return SCS_OK;
 }
 
