@@ -925,7 +925,7 @@ struct scs_batch {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     char err[512];
     double setup_s = 0;
-    double tune_ms[3] = {0, 0, 0};
+    double tune_ms[4] = {0, 0, 0, 0};
 };
 
 static int occupancy_grid(const void* fn, int threads, size_t dyn, int sms, int B)
@@ -959,9 +959,9 @@ static int autotune(scs_batch* b, const std::vector<Args<T>>& host_args, size_t 
     std::vector<Args<T>> samp(nsamp);
     for (int i = 0; i < nsamp; ++i) samp[i] = host_args[(size_t)i * b->B / nsamp];
     CU(cudaMemcpyAsync(scratch_args, samp.data(), sizeof(Args<T>) * nsamp, cudaMemcpyHostToDevice, b->stream), b->err);
-    const int cand[3] = {128, 256, 512};
+    const int cand[4] = {128, 256, 512, 1024};
     float best = 1e30f;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
         const int grid = occupancy_grid(sizeof(T) == 8 ? kblock_ptr<double>() : kblock_ptr<float>(), cand[c], dyn,
                                         b->sms, nsamp);
         CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);

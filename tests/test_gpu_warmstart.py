@@ -62,7 +62,8 @@ def test_learned_warm_start_gains_iterations():
     torch = pytest.importorskip("torch")
     F = W.lasso_family_matrix(seed=4, p=64, nvar=160, density=0.1)
     eps = 1e-5
-    kw = dict(precision=B.FP64, eps=eps, max_iters=20000, cg_adapt=1e-2, warm_fallback=50)
+    kw = dict(direction=B.DIR_RB, mem=10, c0=0.1, precision=B.FP64, eps=eps, max_iters=20000, cg_adapt=1e-2,
+              warm_fallback=50)
 
     def solve(gs, warm=None):
         bcs = [W.lasso_family_bc(F, g) for g in gs]
