@@ -275,12 +275,14 @@ def run_c5(args):
         bcs = [W.lasso_family_bc(F, g) for g in gs]
         return B.Batch(shared=(prob0, [b for b, _ in bcs], [c for _, c in bcs]), **kw)
 
+    rhs = (W.lasso_family_rhs if args.c5_family == "random"
+           else (lambda F_, seed: W.lasso_family_rhs_smooth(F_, seed=seed, base_seed=0)))
     # training solutions
     t0 = time.perf_counter()
     G, U, gen_iters = [], [], []
     chunk = min(args.c5_train, 2048)
     for c0 in range(0, args.c5_train, chunk):
-        gs = [W.lasso_family_rhs(F, seed=100_000 + i) for i in range(c0, min(args.c5_train, c0 + chunk))]
+        gs = [rhs(F, 100_000 + i) for i in range(c0, min(args.c5_train, c0 + chunk))]
         bt = batch_of(gs)
         xs, ys, ss, infos = bt.solve()
         bt.close()
@@ -310,7 +312,7 @@ def run_c5(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # held-out batches of 256: cold vs warm
-    gte = [W.lasso_family_rhs(F, seed=900_000 + j) for j in range(256)]
+    gte = [rhs(F, 900_000 + j) for j in range(256)]
     Xt = torch.as_tensor(np.stack(gte).astype(np.float32), device="cuda")
     Yt = torch.empty(256, Ud.shape[1], device="cuda")
     cold_b = batch_of(gte)
@@ -344,7 +346,7 @@ def run_c5(args):
         "config": {"workload": "parametric LASSO F 2000x5000 1% (n=10001, m=12002), batches of 256 held-out "
                                "instances, MLP 2000-1024-1024-22004", "train_instances": int(Xd.shape[0]),
                    "epochs": args.c5_epochs, "eps": eps, "direction": "RB mem 10, c0 0.1", "precision": "fp64",
-                   "warm_fallback": 50},
+                   "warm_fallback": 50, "family": args.c5_family},
         "cold_solves_per_s": 256.0 / tc, "warm_solves_per_s_incl_inference": 256.0 / (tw + ti),
         "speedup_warm_vs_cold": tc / (tw + ti),
         "median_iters_cold": float(np.median([i["iters"] for i in cold_i])),
@@ -377,6 +379,9 @@ def main():
     ap.add_argument("--mixed-switch", type=float, default=None)
     ap.add_argument("--c5-train", type=int, default=16384, help="training instances of the learned warm start")
     ap.add_argument("--c5-epochs", type=int, default=60)
+    ap.add_argument("--c5-family", default="random", choices=["random", "smooth"],
+                    help="random: a new 5%% support per instance (the specified family); smooth: fixed support, "
+                         "+-10%% amplitudes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -448,6 +448,12 @@ template <typename T>
 static int launch(int team, int threads, int grid, size_t dyn, const Args<T>& a, Args<T>* dev_args, int* queue,
                   cudaStream_t st, char* err)
 {
+    // The sparse products are bound by their random gathers: when the kernel
+    // needs little shared memory, give the rest of the SM's 256 KB to L1 so the
+    // gathered vector stays on chip.  (A per-kernel attribute of this process.)
+    const void* fn = team == SCS_TEAM_GRID ? kgrid_ptr<T>() : kblock_ptr<T>();
+    CU(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            dyn == 0 ? (int)cudaSharedmemCarveoutMaxL1 : (int)cudaSharedmemCarveoutDefault), err);
     if (team == SCS_TEAM_GRID) {
         CU(cudaMemsetAsync(a.W.bar, 0, 4 * sizeof(unsigned), st), err);
         CU(cudaMemsetAsync(a.W.abort_flag, 0, 4 * sizeof(int), st), err);

@@ -298,3 +298,18 @@ def lasso_family_bc(F, g, mu_frac=0.1):
     b = np.concatenate([np.zeros(2 * nvar), -math.sqrt(2.0) * np.asarray(g, np.float64), [-1.0, 1.0]])
     c = np.concatenate([np.zeros(nvar), mu * np.ones(nvar), [1.0]])
     return b, c
+
+
+def lasso_family_rhs_smooth(F, seed, base_seed=0, frac_nz=0.05, rel=0.1, noise=0.01):
+    """A smoothly varying member of the LASSO family: a fixed sparse x_base
+    (frac_nz of the entries N(0,1), from base_seed) scaled entrywise by
+    (1 + rel N(0,1)) per instance, g = F x + noise N(0,1)."""
+    nvar = F.shape[1]
+    rb = np.random.default_rng(base_seed)
+    xb = np.zeros(nvar)
+    k = max(1, int(round(frac_nz * nvar)))
+    idx = rb.choice(nvar, size=k, replace=False)
+    xb[idx] = rb.standard_normal(k)
+    rng = np.random.default_rng(seed)
+    x = xb * (1.0 + rel * rng.standard_normal(nvar))
+    return F @ x + noise * rng.standard_normal(F.shape[0])
