@@ -99,7 +99,8 @@ typedef struct {
     int32_t verbose;
     double aa_reg;       /* Tikhonov factor of the AA normal equations */
     int32_t team;        /* SCS_TEAM_* */
-    int32_t threads;     /* threads per block, 0 = automatic */
+    int32_t threads;     /* threads per block, 0 = automatic (grid team: 512, its maximum;
+                            block team: 256, or the batch autotuner's choice) */
     double mixed_cg_rtol;   /* CG tolerance of the FP32 phase (SCS_MIXED) */
     int32_t mixed_stall;    /* FP32 phase ends after this many iterations without a
                                10% drop of max(pr,dr,gap) (SCS_MIXED) */
@@ -107,7 +108,12 @@ typedef struct {
     double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
-    int32_t spmv_path;      /* 0 or 1: direct streaming loads; 2: TMA-staged stream (grid team only) */
+    int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- the column-blocked
+                               layout (vector slices staged in shared memory, one CTA per SM) where
+                               each CTA gets at least 2048 entries per column block, else sliced
+                               ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL, TMA-staged
+                               stream; 3: column-blocked wherever the layout fits shared memory.
+                               The block team always uses sliced ELL. */
     int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
                                after this many iterations is abandoned for the cold start */
 } scs_settings;
@@ -209,6 +215,16 @@ int scs_linsys(scs_work *work, const double *r, double *out, int32_t slot);
 int scs_project_cone(scs_work *work, const double *v, double *out);
 /* Tu = u + Pi_C(2u~ - u) - u~ and Ru = u - Tu (Sec. 4.1-4.2); either may be NULL. */
 int scs_apply_T(scs_work *work, const double *u, double *Tu, double *Ru);
+
+/* Sparse products of the solver's own matrix copies, in the bulk precision
+ * SCS_FP64 or (works set up with SCS_MIXED) the FP32 copy, for checking the
+ * products on their own -- every CG iteration of Sec. 4.1 is one A and one
+ * A^T product.  op 0: out (m) = A in (n); op 1: out (n) = A^T in (m); op 2:
+ * out = A^T in and out2 = A^T in2 (in, in2 of m entries) in one fused pass.
+ * Results are widened to FP64; pointers host or device.  Overwrites the
+ * work's scratch vectors; SCS_EINVAL on bad arguments. */
+int scs_spmv(scs_work *work, int32_t precision, int32_t op, const double *in, const double *in2, double *out,
+             double *out2);
 
 /* Device-side timing (globaltimer between team barriers, inside one launch)
  * of the solver's building blocks on this problem, for roofline measurement:

@@ -83,6 +83,7 @@ _SIGS = [
     ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    ("scs_spmv", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_residuals", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_residuals_noalloc", C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 10),
     ("scs_finish", None, [C.c_void_p]),
@@ -257,6 +258,19 @@ class Work:
         ns = np.zeros(5)
         _check(lib().scs_profile(self.h, precision, reps, _ptr(ns)), self.h)
         return dict(zip(("A", "AT", "barrier", "reduce", "cg_iter"), ns.tolist()))
+
+    def spmv(self, v, op=0, precision=FP64, v2=None):
+        """op 0: A v; op 1: A^T v; op 2: (A^T v, A^T v2) in one fused pass --
+        the work's own matrix copy in the given bulk precision, widened to FP64."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty(self.m if op == 0 else self.n)
+        if op == 2:
+            v2 = np.ascontiguousarray(v2, dtype=np.float64)
+            out2 = np.empty(self.n)
+            _check(lib().scs_spmv(self.h, precision, op, _ptr(v), _ptr(v2), _ptr(out), _ptr(out2)), self.h)
+            return out, out2
+        _check(lib().scs_spmv(self.h, precision, op, _ptr(v), None, _ptr(out), None), self.h)
+        return out
 
     def apply_T(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)

@@ -9,6 +9,8 @@ namespace sscs {
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr int KMAX = 16;                       // max values in one team reduction
 constexpr int MAX_WARPS = 32;                  // 1024 threads per block at most
+constexpr int GRID_THREADS = 512;              // largest block of the grid team (one CTA per SM)
+constexpr int CB_MAX_STAGES = 4;               // deepest copy ring of the column-blocked products
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -62,6 +64,32 @@ __device__ __forceinline__ int ld_stream(const int* a, unsigned long long pol)
     return v;
 }
 
+__device__ __forceinline__ unsigned short ld_stream(const unsigned short* a, unsigned long long pol)
+{
+    unsigned short v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+// ---- asynchronous global -> shared copies (cp.async, L2 only) ---------------
+// 16-byte copy that bypasses L1, so it sees what other CTAs wrote before the
+// last grid barrier.  dst (shared) and src (global) 16-byte aligned.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// hint: pull [p, p + bytes) into L2 (p 16-byte aligned, bytes % 16 == 0)
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---- TMA bulk copies (cp.async.bulk) and mbarriers --------------------------
 __device__ __forceinline__ unsigned smem_addr(const void* p)
 {
@@ -79,6 +107,10 @@ __device__ __forceinline__ void fence_proxy_async()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -92,6 +124,15 @@ __device__ __forceinline__ void tma_load_1d(unsigned dst, const void* src, unsig
         "l"(src), "r"(bytes), "r"(bar), "l"(pol)
         : "memory");
 }
+// same without an L2 cache policy
+__device__ __forceinline__ void tma_load_1d_plain(unsigned dst, const void* src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// order this thread's earlier generic-proxy accesses (any state space) before its later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
 {
     unsigned ok;

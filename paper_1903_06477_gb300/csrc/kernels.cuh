@@ -18,21 +18,28 @@ struct SmemFixed {
     double t[AAMAX];
 };
 
+// One CTA per SM, at most GRID_THREADS threads: the bound gives every thread
+// 128 registers, which the solver's device functions need to run without
+// spilling to local memory.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_grid(const __grid_constant__ Args<T> a)
+__global__ void __launch_bounds__(GRID_THREADS, 1) k_grid(const __grid_constant__ Args<T> a)
 {
     __shared__ SmemFixed sf;
     extern __shared__ __align__(128) unsigned char dyn[];
     const bool tma = a.P.A.wbnd != nullptr;
-    if (tma && (threadIdx.x & 31) == 0) {
-        const int w = threadIdx.x >> 5;
-        mbar_init(smem_addr(&sf.mbar[2 * w]), 1);
-        mbar_init(smem_addr(&sf.mbar[2 * w + 1]), 1);
-        sf.ph[w] = 0;
-        fence_mbar_init();
+    // mbarriers of the TMA-staged products: per-warp pairs for the sliced ELL
+    // stream; for the column-blocked ring, "full" barriers (one arrival: the
+    // producer's) at [0, CB_MAX_STAGES) and "empty" barriers (one arrival per
+    // compute warp) at [CB_MAX_STAGES, 2 CB_MAX_STAGES)
+    const bool cb = a.P.A.cb.ncb > 0 || a.P.AT.cb.ncb > 0;
+    for (int i = threadIdx.x; i < 2 * MAX_WARPS; i += blockDim.x) {
+        const bool empty = cb && i >= CB_MAX_STAGES && i < 2 * CB_MAX_STAGES;
+        mbar_init(smem_addr(&sf.mbar[i]), empty ? (blockDim.x >> 5) - 1 : 1);
+        if (i < MAX_WARPS) sf.ph[i] = 0;
     }
+    fence_mbar_init();
     __syncthreads();
-    GridTeam tm{sf.red, tma ? dyn : nullptr, sf.mbar, sf.ph, a.W.partials, a.W.bar, a.W.abort_flag, 0};
+    GridTeam tm{sf.red, tma ? dyn : nullptr, dyn, sf.mbar, sf.ph, a.W.partials, a.W.bar, a.W.abort_flag, 0, 0ull};
     run_mode<T>(tm, a.P, a.W, a.S, a.mode, a.slot, sf.G, sf.rhs, sf.L, sf.t, dyn);
 }
 

@@ -20,7 +20,7 @@ constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared 
 constexpr int PSD_MAX = 64;  // largest PSD order
 
 enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5,
-            MODE_RESID = 6 };
+            MODE_RESID = 6, MODE_SPMV = 7 };
 enum { ST_SOLVED = 1, ST_INFEASIBLE = -1, ST_UNBOUNDED = -2, ST_MAX_ITERS = -3, ST_TIME_LIMIT = -4,
        ST_NUMERICAL = -5, ST_STALLED = -6 };
 
@@ -56,6 +56,57 @@ struct DevState {
     int pad2;
 };
 
+// Column-blocked sliced ELL, the grid team's layout for large matrices.  CTA b
+// owns the contiguous rows [rbnd[b], rbnd[b+1]); the columns are cut into ncb
+// blocks of cw.  A "segment" is one (CTA, column block) pair: the CTA's rows
+// that have entries in the block, sorted by their count there (descending),
+// packed as slices of H = 32 / V rows with element j of slice row r at
+// step (slice start + j / V), lane (j % V) * H + r, 32 entries per step, and
+// its column stored as a 16-bit offset inside the block (padding: value 0,
+// offset 0).  The slices of a segment are dealt to the CTA's warps (largest
+// first to the least-loaded warp) and stored warp by warp.  The entries of
+// segment g = b * ncb + k are contiguous, [E0, E1) of col / val.
+//
+// Each segment has ms 32-bit words of metadata at meta + g * ms:
+//   [0] E0   [1] E1   [2], [3] E0, E1 of the CTA's segment (k + S) mod ncb
+//   [4] ns: slices    [5 .. 5+nw] first slice of each warp (nw+1 values)
+//   [6+nw .. 6+nw+ns] slice start steps from E0 (ns+1 values)
+//   then ns * H 16-bit row indices inside the CTA's range (0xFFFF: none),
+//   two per word, low half first.
+//
+// The product streams segments through a ring of S shared-memory stages,
+// warp-specialised: the CTA's last warp is the producer, which copies a
+// segment's metadata, its slice of the multiplied vector and its entries with
+// bulk (TMA) copies completing on the stage's "full" mbarrier as soon as the
+// stage's "empty" mbarrier says every compute warp is done with it; the
+// other nw warps compute, so the random reads of the vector and the matrix
+// stream are all shared-memory reads.  The rows of one segment are distinct,
+// and the partial sums are double-buffered by segment parity: a compute warp
+// starts segment j once segment j-2 is finished by every warp (its "empty"
+// barrier), so warps may run one segment apart without two of them ever
+// updating the same sum, and each sum is accumulated in a fixed order
+// (deterministic).  CTA b visits the column blocks in the order b, b+1, ...
+// (mod ncb), so at any moment the CTAs read different slices of the vector.
+// The CTA adds its two partial-sum buffers after the last block.
+template <typename T>
+struct Cblk {
+    int ncb;          // column blocks (0: layout absent)
+    int cw;           // columns per block (multiple of 4)
+    int cols;         // columns of the matrix
+    int nw;           // compute warps per CTA (the CTA has nw + 1 warps)
+    int V;            // lanes per row
+    int acc_rows;     // partial-sum entries per buffer (largest row range); 2 buffers per vector
+    int ms;           // metadata words per segment (multiple of 4)
+    int S;            // stages in the copy ring (2..CB_MAX_STAGES)
+    int stage_off;    // byte offset of stage 0 in dynamic shared memory
+    int stage_bytes;  // bytes per stage (multiple of 16)
+    int off_x, off_col, off_val;  // byte offsets inside a stage
+    const int* rbnd;
+    const int* meta;
+    const unsigned short* col;
+    const T* val;
+};
+
 // Sliced ELL with row sorting (SELL-H-sigma) and V lanes per row, H = 32 / V
 // rows per slice: element j of the slice's row r sits at ptr[s] + j*H + r,
 // so lane q*H + r of a warp reads element t*V + q of row r at
@@ -69,6 +120,7 @@ struct Sell {
     const T* val;      // padded values (0 in padding)
     const int* perm;   // sorted position -> original row (nslices * H entries, -1 past the end)
     const int* wbnd;   // grid team only: warp w owns slices [wbnd[w], wbnd[w+1]) (nnz-balanced), else null
+    Cblk<T> cb;        // grid team only: column-blocked copy (cb.ncb > 0), used instead of the above
 };
 
 constexpr int TMA_CH = 8;  // t-steps (of 32 elements) per staged chunk
@@ -299,6 +351,194 @@ __device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& x
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// column-blocked product (grid team): y = M x (NV = 1) or M x1, M x2 (NV = 2)
+// ---------------------------------------------------------------------------
+
+// One segment from its stage: compute warp w runs its slices (matrix
+// entries, the vector slice and the metadata all in shared memory); row sums
+// are reduced over the V lanes of a row and added to acc (w's rows are its
+// own, so plain read-modify-writes do not race).
+template <typename T>
+__device__ __forceinline__ void cb_segment(const Cblk<T>& C, const int* mt, const T* xs, const unsigned short* scol,
+                                           const T* sval, T* acc)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int H = 32 / C.V;
+    const int ns = mt[4];
+    const int* wl = mt + 5;
+    const int* st = wl + C.nw + 1;
+    const unsigned short* sr = (const unsigned short*)(st + ns + 1);
+    const int s_hi = wl[w + 1];
+    constexpr int U = 8;  // steps in flight per lane: eight independent gather chains
+    for (int s = wl[w]; s < s_hi; ++s) {
+        const int t1 = st[s + 1];
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int t = st[s]; t < t1; t += U) {
+            int c[U];
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = t + u < t1;  // steps past the slice: offset 0, value 0
+                c[u] = ok ? (int)scol[(t + u) * 32 + lane] : 0;
+                v[u] = ok ? sval[(t + u) * 32 + lane] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u += 4) {
+                a0 = fmaT(v[u], xs[c[u]], a0);
+                a1 = fmaT(v[u + 1], xs[c[u + 1]], a1);
+                a2 = fmaT(v[u + 2], xs[c[u + 2]], a2);
+                a3 = fmaT(v[u + 3], xs[c[u + 3]], a3);
+            }
+        }
+        T a = (a0 + a1) + (a2 + a3);
+        for (int o = H; o < 32; o <<= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
+        if (lane < H) {
+            const int r = sr[s * H + lane];
+            if (r != 0xFFFF) acc[r] += a;
+        }
+    }
+}
+
+// acc[0, R) + acc[acc_rows, acc_rows + R) = (rows of this CTA's range) . x
+// over all column blocks (even segments into the first buffer, odd into the
+// second), through the ring of S stages: full barriers tm.mbar[0..S-1], empty barriers
+// tm.mbar[CB_MAX_STAGES + s]; tm.ph[s] counts the stage's past uses, so use u
+// of this pass waits on parity (ph[s] + u) & 1.  Returns false if a wait ran
+// out of time (the abort flag is then set and the copies still in flight are
+// waited for, bounded, before returning).
+template <typename T>
+__device__ bool cb_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* acc, unsigned long long pol)
+{
+    constexpr int E = 16 / (int)sizeof(T);
+    const int S = C.S, ncb = C.ncb;
+    const int g0 = blockIdx.x * ncb;
+    const int k0 = blockIdx.x % ncb;  // first column block of this CTA
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mis = (int)(((uintptr_t)x & 15) / sizeof(T));
+    unsigned char* st0 = tm.dsm + C.stage_off;
+    auto stage = [&](int s) { return st0 + (size_t)s * C.stage_bytes; };
+    auto full = [&](int s) { return smem_addr(&tm.mbar[s]); };
+    auto empty = [&](int s) { return smem_addr(&tm.mbar[CB_MAX_STAGES + s]); };
+    auto blk = [&](int j) { return (k0 + j) % ncb; };  // column block of the j-th segment visited
+    __syncthreads();  // stages free, acc zeroed, tm.ph current
+    unsigned base[CB_MAX_STAGES];
+#pragma unroll
+    for (int s = 0; s < CB_MAX_STAGES; ++s) base[s] = tm.ph[s];
+    bool ok = true;
+    int issued = 0;
+    if (w == C.nw) {
+        // producer warp: lane 0 issues every copy
+        if (lane == 0) {
+            auto issue = [&](int j, int e0, int e1) {
+                const int s = j % S, k = blk(j);
+                unsigned char* d = stage(s);
+                const int len = min(C.cw, C.cols - k * C.cw);
+                const unsigned xb = (unsigned)((mis + len + E - 1) / E) * 16u;
+                const unsigned ne = (unsigned)(e1 - e0);
+                const unsigned mb = (unsigned)C.ms * 4u;
+                mbar_expect_tx(full(s), mb + xb + ne * (2u + (unsigned)sizeof(T)));
+                tma_load_1d_plain(smem_addr(d), C.meta + (size_t)(g0 + k) * C.ms, mb, full(s));
+                tma_load_1d_plain(smem_addr(d + C.off_x), x + (size_t)k * C.cw - mis, xb, full(s));
+                if (ne) {
+                    tma_load_1d(smem_addr(d + C.off_col), C.col + e0, ne * 2u, full(s), pol);
+                    tma_load_1d(smem_addr(d + C.off_val), C.val + e0, ne * (unsigned)sizeof(T), full(s), pol);
+                }
+            };
+            // x was written by generic stores (other CTAs, before the last
+            // grid barrier) and is read here by the async proxy
+            fence_proxy_async_all();
+            const int npro = min(S, ncb);
+            int e0[CB_MAX_STAGES], e1[CB_MAX_STAGES];
+#pragma unroll
+            for (int j = 0; j < CB_MAX_STAGES; ++j)
+                if (j < npro) {
+                    e0[j] = ro(C.meta + (size_t)(g0 + blk(j)) * C.ms);
+                    e1[j] = ro(C.meta + (size_t)(g0 + blk(j)) * C.ms + 1);
+                }
+#pragma unroll
+            for (int j = 0; j < CB_MAX_STAGES; ++j)
+                if (j < npro) issue(j, e0[j], e1[j]);
+            issued = npro;
+            for (int j = S; j < ncb; ++j) {
+                const int s = j % S;
+                if (!mbar_wait(empty(s), (base[s] + j / S - 1) & 1u, tm.abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                // the stage's header names the segment visited S after its own
+                const int* h = (const int*)stage(s);
+                const int ne0 = h[2], ne1 = h[3];
+                fence_proxy_async();  // the stage was read through the generic proxy
+                issue(j, ne0, ne1);
+                issued = j + 1;
+            }
+        }
+    } else {
+        for (int j = 0; j < ncb; ++j) {
+            const int s = j % S;
+            if (!mbar_wait(full(s), (base[s] + j / S) & 1u, tm.abort_flag)) {
+                ok = false;
+                break;
+            }
+            if (j >= 2) {  // every warp is done with segment j-2 (same partial-sum buffer)
+                const int s2 = (j - 2) % S;
+                if (!mbar_wait(empty(s2), (base[s2] + (j - 2) / S) & 1u, tm.abort_flag)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const unsigned char* d = stage(s);
+            cb_segment<T>(C, (const int*)d, (const T*)(d + C.off_x) + mis, (const unsigned short*)(d + C.off_col),
+                          (const T*)(d + C.off_val), acc + (j & 1) * C.acc_rows);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty(s));
+        }
+    }
+    const bool all_ok = __syncthreads_and(ok);
+    if (!all_ok && w == C.nw && lane == 0) {
+        // copies of the last S issued segments may still be in flight
+        for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full(j % S), (base[j % S] + j / S) & 1u, nullptr);
+    }
+    if (threadIdx.x == 0 && all_ok)
+        for (int s = 0; s < S; ++s) tm.ph[s] += (unsigned)((ncb - s + S - 1) / S);
+    __syncthreads();
+    return all_ok;
+}
+
+// The product: one pass per multiplied vector (NV = 2: x1 into acc1, then x2
+// into acc2), then epi(row, sum) (or epi(row, sum1, sum2)) for every row of
+// the CTA's range.
+template <typename T, int NV, class Epi>
+__device__ void cb_spmv(const GridTeam& tm, const Cblk<T>& C, const T* x1, const T* x2, Epi& epi)
+{
+    const int b = blockIdx.x;
+    const int r0 = ro(C.rbnd + b), R = ro(C.rbnd + b + 1) - r0;
+    const int ar = C.acc_rows;
+    T* acc1 = (T*)tm.dsm;      // two buffers of ar
+    T* acc2 = acc1 + 2 * ar;   // two more for the second vector
+    const unsigned long long pol = evict_first_policy();
+    __syncthreads();  // shared memory is free (earlier users done)
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        acc1[r] = 0;
+        acc1[ar + r] = 0;
+        if constexpr (NV == 2) {
+            acc2[r] = 0;
+            acc2[ar + r] = 0;
+        }
+    }
+    if (!cb_pass<T>(tm, C, x1, acc1, pol)) return;
+    if constexpr (NV == 2) {
+        if (!cb_pass<T>(tm, C, x2, acc2, pol)) return;
+    }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        if constexpr (NV == 1)
+            epi(r0 + r, acc1[r] + acc1[ar + r]);
+        else
+            epi(r0 + r, acc1[r] + acc1[ar + r], acc2[r] + acc2[ar + r]);
+    }
+}
+
 template <typename T, class Team, class XF, class Epi>
 __device__ __forceinline__ void spmv_f(const Team& tm, const Sell<T>& S, XF xf, Epi epi)
 {
@@ -311,6 +551,12 @@ __device__ __forceinline__ void spmv_f(const Team& tm, const Sell<T>& S, XF xf, 
 template <typename T, class Team, class Epi>
 __device__ __forceinline__ void spmv(const Team& tm, const Sell<T>& S, const T* x, Epi epi)
 {
+    if constexpr (Team::kGrid) {
+        if (S.cb.ncb > 0) {
+            cb_spmv<T, 1>(tm, S.cb, x, x, epi);
+            return;
+        }
+    }
     auto f = [x](int c) { return x[c]; };
     spmv_f(tm, S, f, epi);
 }
@@ -318,6 +564,12 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sell<T>& S, const T* 
 template <typename T, class Team, class Epi>
 __device__ __forceinline__ void spmv2(const Team& tm, const Sell<T>& S, const T* x1, const T* x2, Epi epi)
 {
+    if constexpr (Team::kGrid) {
+        if (S.cb.ncb > 0) {
+            cb_spmv<T, 2>(tm, S.cb, x1, x2, epi);
+            return;
+        }
+    }
     auto f1 = [x1](int c) { return x1[c]; };
     auto f2 = [x2](int c) { return x2[c]; };
     sell2_v(tm, S, f1, f2, epi);
@@ -1516,6 +1768,37 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
             }
             tm.sync();
         }
+        return;
+    }
+    if (mode == MODE_SPMV) {
+        // sparse products in precision T.  slot 0: io_out = A io_in[0,n);
+        // slot 1: io_out = A^T io_in[0,m); slot 2: io_out = A^T io_in[0,m) and
+        // io_out2 = A^T io_out2[0,m) in one fused pass.  x is staged at u's
+        // start, y at u + n (the offset the solver's psi part has), the second
+        // y in tm.
+        T* xv = W.u.v;
+        T* yv = W.u.v + n;
+        T* y2 = W.tm;
+        if (slot == 0) {
+            for (int j = tm.rank(); j < n; j += tm.size()) xv[j] = (T)W.io_in[j];
+        } else {
+            for (int i = tm.rank(); i < m; i += tm.size()) {
+                yv[i] = (T)W.io_in[i];
+                if (slot == 2) y2[i] = (T)W.io_out2[i];
+            }
+        }
+        tm.sync();
+        if (slot == 0) {
+            spmv(tm, P.A, xv, [&](int i, T v) { W.io_out[i] = (double)v; });
+        } else if (slot == 1) {
+            spmv(tm, P.AT, yv, [&](int j, T v) { W.io_out[j] = (double)v; });
+        } else {
+            spmv2(tm, P.AT, yv, y2, [&](int j, T v1, T v2) {
+                W.io_out[j] = (double)v1;
+                W.io_out2[j] = (double)v2;
+            });
+        }
+        tm.sync();
         return;
     }
     if (mode == MODE_PROFILE) {

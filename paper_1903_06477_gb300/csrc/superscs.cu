@@ -19,6 +19,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/superscs.h"
@@ -73,6 +74,16 @@ struct HostProb {
         std::vector<double> val;
         std::vector<int> wbnd;  // per-warp slice ranges for the TMA-staged product (grid team)
     } SA, ST;
+    // column-blocked copies for the grid team (layout of Cblk in solver.cuh),
+    // one per matrix and bulk precision (the block width depends on it)
+    struct Cb {
+        int ncb = 0, cw = 0, cols = 0, nw = 0, V = 1, acc_rows = 0, ms = 0, S = 0, stage_off = 0, stage_bytes = 0,
+            off_x = 0, off_col = 0, off_val = 0, esize = 8;
+        std::vector<int> rbnd, meta;
+        std::vector<uint16_t> col;
+        std::vector<double> val;
+        size_t dyn() const { return ncb ? (size_t)stage_off + (size_t)S * stage_bytes : 0; }
+    } cA64, cAT64, cA32, cAT32;
 };
 
 // nnz-balanced contiguous slice ranges for W warps: warp w owns [b[w], b[w+1])
@@ -143,6 +154,283 @@ static void build_sell(int rows, const std::vector<int>& rp, const std::vector<i
     }
 }
 
+// ---------------------------------------------------------------------------
+// column-blocked layout (grid team)
+// ---------------------------------------------------------------------------
+
+// contiguous row ranges for G CTAs, balanced on (entries + 2) per row
+static std::vector<int> cb_row_bounds(int rows, const std::vector<int>& rp, int G)
+{
+    std::vector<int> rb(G + 1, 0);
+    const long long total = (long long)rp[rows] + 2LL * rows;
+    int r = 0;
+    for (int b = 1; b < G; ++b) {
+        const long long target = total * b / G;
+        while (r < rows && (long long)rp[r] + 2LL * r < target) ++r;
+        rb[b] = r;
+    }
+    rb[G] = rows;
+    return rb;
+}
+
+// The rows of CTA range [r0, r0 + R) bucketed by column block: cnt[k * R + lr]
+// entries of local row lr in block k, their CSR indices in
+// epos[start[k * R + lr] ...].
+struct CbBuckets {
+    std::vector<int> cnt, start, epos, fill;
+    void build(int r0, int R, int ncb, int cw, const std::vector<int>& rp, const std::vector<int>& ci)
+    {
+        cnt.assign((size_t)ncb * R, 0);
+        for (int lr = 0; lr < R; ++lr)
+            for (int e = rp[r0 + lr]; e < rp[r0 + lr + 1]; ++e) cnt[(size_t)(ci[e] / cw) * R + lr]++;
+        start.assign((size_t)ncb * R + 1, 0);
+        for (size_t i = 0; i < (size_t)ncb * R; ++i) start[i + 1] = start[i] + cnt[i];
+        epos.resize(start.back());
+        fill.assign(start.begin(), start.end() - 1);
+        for (int lr = 0; lr < R; ++lr)
+            for (int e = rp[r0 + lr]; e < rp[r0 + lr + 1]; ++e) epos[fill[(size_t)(ci[e] / cw) * R + lr]++] = e;
+    }
+    // rows of block k with entries, by count descending (ties: row order)
+    void sorted_rows(int k, int R, std::vector<int>& out) const
+    {
+        out.clear();
+        for (int lr = 0; lr < R; ++lr)
+            if (cnt[(size_t)k * R + lr] > 0) out.push_back(lr);
+        std::stable_sort(out.begin(), out.end(),
+                         [&](int a, int b) { return cnt[(size_t)k * R + a] > cnt[(size_t)k * R + b]; });
+    }
+};
+
+// Deal slices (work = steps) to nw warps, largest first to the least-loaded
+// warp.  Returns the warp of each slice; loads accumulate 2 * steps + 3.
+static void cb_deal(const std::vector<int>& steps, int nw, std::vector<int>& warp, std::vector<long long>& load)
+{
+    load.assign(nw, 0);
+    warp.resize(steps.size());
+    for (size_t s = 0; s < steps.size(); ++s) {
+        int best = 0;
+        for (int w = 1; w < nw; ++w)
+            if (load[w] < load[best]) best = w;
+        warp[s] = best;
+        load[best] += 2LL * steps[s] + 3;
+    }
+}
+
+static void cb_slice_steps(const CbBuckets& bk, int k, int R, const std::vector<int>& rows, int V,
+                           std::vector<int>& steps)
+{
+    const int H = 32 / V;
+    const int ns = ((int)rows.size() + H - 1) / H;
+    steps.resize(ns);
+    for (int sl = 0; sl < ns; ++sl) steps[sl] = (bk.cnt[(size_t)k * R + rows[(size_t)sl * H]] + V - 1) / V;
+}
+
+// Lanes per row for the column-blocked layout: the V in {1, 2, 4, 8} with the
+// least estimated time on a sample of CTAs -- per segment, the busiest
+// warp's load plus eight times the mean load.  Segments are computed from
+// shared memory while the matrix stream is the bound, so padding (the mean)
+// weighs more than imbalance.
+static int cb_pick_lanes(const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<int>& rb, int nw,
+                         int ncb, int cw)
+{
+    const int G = (int)rb.size() - 1;
+    const int stride = std::max(1, G / 16);
+    long long cost[4] = {0, 0, 0, 0};
+    CbBuckets bk;
+    std::vector<int> rows, steps, warp;
+    std::vector<long long> load;
+    for (int b = 0; b < G; b += stride) {
+        const int r0 = rb[b], R = rb[b + 1] - r0;
+        bk.build(r0, R, ncb, cw, rp, ci);
+        for (int k = 0; k < ncb; ++k) {
+            bk.sorted_rows(k, R, rows);
+            for (int vi = 0; vi < 4; ++vi) {
+                cb_slice_steps(bk, k, R, rows, 1 << vi, steps);
+                cb_deal(steps, nw, warp, load);
+                long long mx = 0, sum = 0;
+                for (long long l : load) {
+                    mx = std::max(mx, l);
+                    sum += l;
+                }
+                cost[vi] += mx + 8 * sum / nw;
+            }
+        }
+    }
+    int best = 0;
+    for (int vi = 1; vi < 4; ++vi)
+        if (cost[vi] < cost[best]) best = vi;
+    return 1 << best;
+}
+
+// metadata words per segment for ns slices of H rows (layout of Cblk)
+static int cb_meta_words(int nw, int ns, int H)
+{
+    return 5 + (nw + 1) + (ns + 1) + (ns * H + 1) / 2;
+}
+
+// Build the column-blocked layout of a CSR matrix (rows x cols) for the row
+// ranges rb, nw compute warps per CTA, blocks of cw columns and a ring of S
+// stages.
+// Returns the largest segment (entries) or -1 if the layout is too large.
+static long long build_cb(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
+                          const std::vector<double>& vx, const std::vector<int>& rb, int nw, int cw, int S,
+                          HostProb::Cb& C)
+{
+    (void)rows;
+    const int G = (int)rb.size() - 1;
+    const int ncb = (cols + cw - 1) / cw;
+    const int V = cb_pick_lanes(rp, ci, rb, nw, ncb, cw);
+    const int H = 32 / V;
+    C.ncb = ncb;
+    C.cw = cw;
+    C.cols = cols;
+    C.nw = nw;
+    C.V = V;
+    C.S = S;
+    C.rbnd = rb;
+    C.col.clear();
+    C.val.clear();
+    struct Seg {
+        long long e0, e1;
+        std::vector<int> words;  // [4] onwards of the segment's metadata
+    };
+    std::vector<Seg> segs((size_t)G * ncb);
+    CbBuckets bk;
+    std::vector<int> rows_k, steps, warp, order;
+    std::vector<long long> load;
+    int ms = 4;
+    long long max_e = 0;
+    for (int b = 0; b < G; ++b) {
+        const int r0 = rb[b], R = rb[b + 1] - r0;
+        bk.build(r0, R, ncb, cw, rp, ci);
+        for (int k = 0; k < ncb; ++k) {
+            bk.sorted_rows(k, R, rows_k);
+            cb_slice_steps(bk, k, R, rows_k, V, steps);
+            cb_deal(steps, nw, warp, load);
+            const int ns = (int)steps.size();
+            order.resize(ns);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return warp[a] < warp[c]; });
+            Seg& sg = segs[(size_t)b * ncb + k];
+            sg.e0 = (long long)C.col.size();
+            std::vector<int> wstart(nw + 1, 0), sstart(ns + 1, 0);
+            std::vector<uint16_t> srow((size_t)ns * H, 0xFFFF);
+            int w = 0, t = 0;
+            for (int oi = 0; oi < ns; ++oi) {
+                const int sl = order[oi];
+                while (w <= warp[sl]) wstart[w++] = oi;
+                sstart[oi] = t;
+                const size_t e0 = (size_t)C.col.size();
+                const size_t size = (size_t)steps[sl] * 32;
+                C.col.resize(e0 + size, 0);
+                C.val.resize(e0 + size, 0.0);
+                for (int rr = 0; rr < H; ++rr) {
+                    const size_t pos = (size_t)sl * H + rr;
+                    if (pos >= rows_k.size()) continue;
+                    const int lr = rows_k[pos];
+                    srow[(size_t)oi * H + rr] = (uint16_t)lr;
+                    const size_t q0 = (size_t)bk.start[(size_t)k * R + lr];
+                    const int len = bk.cnt[(size_t)k * R + lr];
+                    for (int j = 0; j < len; ++j) {
+                        const int e = bk.epos[q0 + j];
+                        const size_t idx = e0 + (size_t)(j / V) * 32 + (size_t)(j % V) * H + rr;
+                        C.col[idx] = (uint16_t)(ci[e] - k * cw);
+                        C.val[idx] = vx[e];
+                    }
+                }
+                t += steps[sl];
+            }
+            sstart[ns] = t;
+            while (w <= nw) wstart[w++] = ns;
+            sg.e1 = (long long)C.col.size();
+            max_e = std::max(max_e, sg.e1 - sg.e0);
+            sg.words.clear();
+            sg.words.push_back(ns);
+            sg.words.insert(sg.words.end(), wstart.begin(), wstart.end());
+            sg.words.insert(sg.words.end(), sstart.begin(), sstart.end());
+            for (int i = 0; i < ns * H; i += 2) {
+                const unsigned lo = srow[i], hi = i + 1 < ns * H ? srow[i + 1] : 0xFFFFu;
+                sg.words.push_back((int)(lo | (hi << 16)));
+            }
+            ms = std::max(ms, 4 + (int)sg.words.size());
+        }
+    }
+    if (C.col.size() >= (1ull << 31)) return -1;
+    ms = (ms + 3) & ~3;
+    C.ms = ms;
+    C.meta.assign((size_t)G * ncb * ms, 0);
+    for (int b = 0; b < G; ++b)
+        for (int k = 0; k < ncb; ++k) {
+            const Seg& sg = segs[(size_t)b * ncb + k];
+            int* m = C.meta.data() + ((size_t)b * ncb + k) * ms;
+            m[0] = (int)sg.e0;
+            m[1] = (int)sg.e1;
+            const int k2 = (k + S) % ncb;  // visited S segments later (visits wrap around)
+            m[2] = (int)segs[(size_t)b * ncb + k2].e0;
+            m[3] = (int)segs[(size_t)b * ncb + k2].e1;
+            std::copy(sg.words.begin(), sg.words.end(), m + 4);
+        }
+    return max_e;
+}
+
+// Plan (and build) the column-blocked copy of one matrix in one precision:
+// nv vectors per product, dyn_max bytes of dynamic shared memory laid out as
+// [2 nv partial-sum arrays | S stages of (metadata | vector slice | col | val)].
+// The block width is sized so a stage holds one segment; a segment that
+// turns out larger shrinks the width and the layout is rebuilt.  Leaves C
+// empty (ncb = 0) where nothing fits or, unless forced, where the segments
+// would be too short to pay for their per-segment cost.
+static void plan_cb(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
+                    const std::vector<double>& vx, int G, int nw, int esize, int nv, size_t dyn_max, bool force,
+                    HostProb::Cb& C)
+{
+    constexpr int S = 3;
+    C = HostProb::Cb();
+    C.esize = esize;
+    const std::vector<int> rb = cb_row_bounds(rows, rp, G);
+    int acc_rows = 0;
+    long long nnz_cta = 0;
+    for (int b = 0; b < G; ++b) {
+        acc_rows = std::max(acc_rows, rb[b + 1] - rb[b]);
+        nnz_cta = std::max<long long>(nnz_cta, rp[rb[b + 1]] - rp[rb[b]]);
+    }
+    if (acc_rows >= 0xFFFF || nw < 1) return;
+    const int E = 16 / esize;
+    // partial sums: two buffers (even / odd segments) per multiplied vector
+    const size_t acc_bytes = ((size_t)2 * nv * std::max(acc_rows, 1) * esize + 15) & ~size_t(15);
+    if (acc_bytes + 4096 > dyn_max) return;
+    const long long stage_avail = (long long)((dyn_max - acc_bytes) / S) & ~15LL;
+    // metadata bound: at most ceil(acc_rows / H) slices, H >= 4
+    const int ms_cap = (cb_meta_words(nw, (acc_rows + 3) / 4, 4) + 16 + 3) & ~3;
+    const double per_col = esize + 1.15 * (2 + esize) * (double)nnz_cta / std::max(cols, 1);
+    long long budget = stage_avail - 4LL * ms_cap - 64 - 2LL * E * esize;
+    int cw = (int)std::min<double>(65536.0, budget / per_col) & ~3;
+    const long long nnz = rp[rows];
+    for (int attempt = 0; attempt < 8 && cw >= 64; ++attempt) {
+        const int ncb = (cols + cw - 1) / cw;
+        const int cw2 = ((cols + ncb - 1) / ncb + 3) & ~3;
+        if (!force && nnz < 1024LL * G * ncb) return;
+        const long long max_e = build_cb(rows, cols, rp, ci, vx, rb, nw, cw2, S, C);
+        if (max_e < 0) break;
+        const long long off_x = 4LL * C.ms;
+        const long long off_col = off_x + (((long long)(cw2 + 2 * E) * esize + 15) & ~15LL);
+        const long long off_val = off_col + ((2 * max_e + 15) & ~15LL);
+        const long long bytes = off_val + ((max_e * esize + 15) & ~15LL);
+        if (bytes <= stage_avail) {
+            C.esize = esize;
+            C.acc_rows = acc_rows;
+            C.stage_off = (int)acc_bytes;
+            C.stage_bytes = (int)bytes;
+            C.off_x = (int)off_x;
+            C.off_col = (int)off_col;
+            C.off_val = (int)off_val;
+            return;
+        }
+        cw = (int)((double)cw2 * 0.95 * (double)stage_avail / (double)bytes) & ~3;
+    }
+    C = HostProb::Cb();
+}
+
 static int pick_lanes(long long nnz, int rows)
 {
     const double avg = rows > 0 ? (double)nnz / rows : 0.0;
@@ -151,7 +439,11 @@ static int pick_lanes(long long nnz, int rows)
     return v;
 }
 
-static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err)
+static void finish_layouts(HostProb& H, bool sell_A, bool sell_T);
+
+// Validate and copy the problem, build the CSR of A^T.  Unless keep_csr, also
+// build the sliced layouts and drop the CSR copies (finish_layouts).
+static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err, bool keep_csr = false)
 {
     if (!d || !k) { set_err(err, "data and cone must not be NULL"); return SCS_EINVAL; }
     if (d->m <= 0 || d->n <= 0) { set_err(err, "m and n must be positive (m=%d n=%d)", d->m, d->n); return SCS_EINVAL; }
@@ -233,20 +525,32 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err)
     H.nc = std::sqrt(s);
     H.vecA = pick_lanes(nnz, m);
     H.vecT = pick_lanes(nnz, n);
-    build_sell(m, H.Ap, H.Ai, H.Ax, H.vecA, H.SA);
-    build_sell(n, H.Tp, H.Ti, H.Tx, H.vecT, H.ST);
-    // the CSR copies are only needed to build the sliced layouts
+    if (keep_csr) return SCS_OK;
+    finish_layouts(H, true, true);
+    if ((long long)H.SA.ptr.back() >= (1ll << 31) || (long long)H.ST.ptr.back() >= (1ll << 31)) {
+        set_err(err, "padded matrix too large");
+        return SCS_EINVAL;
+    }
+    return SCS_OK;
+}
+
+// Build the sliced ELL copies that are needed (an empty one, with no slices,
+// stands for a matrix that only runs column-blocked) and drop the CSR copies.
+static void finish_layouts(HostProb& H, bool sell_A, bool sell_T)
+{
+    auto empty = [](int rows, HostProb::Sell& S) {
+        S = HostProb::Sell();
+        S.rows = rows;
+        S.ptr.assign(1, 0);
+    };
+    if (sell_A) build_sell(H.m, H.Ap, H.Ai, H.Ax, H.vecA, H.SA); else empty(H.m, H.SA);
+    if (sell_T) build_sell(H.n, H.Tp, H.Ti, H.Tx, H.vecT, H.ST); else empty(H.n, H.ST);
     std::vector<int>().swap(H.Ap);
     std::vector<int>().swap(H.Ai);
     std::vector<int>().swap(H.Tp);
     std::vector<int>().swap(H.Ti);
     std::vector<double>().swap(H.Ax);
     std::vector<double>().swap(H.Tx);
-    if ((long long)H.SA.ptr.back() >= (1ll << 31) || (long long)H.ST.ptr.back() >= (1ll << 31)) {
-        set_err(err, "padded matrix too large");
-        return SCS_EINVAL;
-    }
-    return SCS_OK;
 }
 
 static int check_settings(const scs_settings* S, char* err)
@@ -303,6 +607,29 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     };
     lay_sell(H.SA, P.A);
     lay_sell(H.ST, P.AT);
+    auto lay_cb = [&](const HostProb::Cb& hc, Cblk<T>& dc) {
+        dc = Cblk<T>{};
+        if (hc.ncb == 0) return;
+        dc.ncb = hc.ncb;
+        dc.cw = hc.cw;
+        dc.cols = hc.cols;
+        dc.nw = hc.nw;
+        dc.V = hc.V;
+        dc.acc_rows = hc.acc_rows;
+        dc.ms = hc.ms;
+        dc.S = hc.S;
+        dc.stage_off = hc.stage_off;
+        dc.stage_bytes = hc.stage_bytes;
+        dc.off_x = hc.off_x;
+        dc.off_col = hc.off_col;
+        dc.off_val = hc.off_val;
+        dc.rbnd = A.take<int>(hc.rbnd.size());
+        dc.meta = A.take<int>(hc.meta.size());
+        dc.col = A.take<unsigned short>(hc.col.size());
+        dc.val = A.take<T>(hc.val.size());
+    };
+    lay_cb(sizeof(T) == 8 ? H.cA64 : H.cA32, P.A.cb);
+    lay_cb(sizeof(T) == 8 ? H.cAT64 : H.cAT32, P.AT.cb);
     if (shared_idx == nullptr) {
         P.q_off = A.take<int>(H.q_off.size());
         P.s_dim = A.take<int>(H.s.size());
@@ -370,12 +697,27 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         }
         return SCS_OK;
     };
+    auto put_u16 = [&](const std::vector<uint16_t>& v, const unsigned short* dst) -> int {
+        if (!v.empty()) CU(cudaMemcpyAsync((void*)dst, v.data(), 2 * v.size(), cudaMemcpyHostToDevice, st), err);
+        return SCS_OK;
+    };
+    auto put_cb = [&](const HostProb::Cb& hc, const Cblk<T>& dc) -> int {
+        if (hc.ncb == 0) return SCS_OK;
+        int r;
+        if ((r = put_i(hc.rbnd, dc.rbnd)) || (r = put_i(hc.meta, dc.meta)) || (r = put_u16(hc.col, dc.col)) ||
+            (r = put_t(hc.val, dc.val)))
+            return r;
+        return SCS_OK;
+    };
     int rc;
     if (!matrix) {
         if ((rc = put_t(H.b, P.b)) || (rc = put_t(H.c, P.c))) return rc;
         CU(cudaStreamSynchronize(st), err);
         return SCS_OK;
     }
+    if ((rc = put_cb(sizeof(T) == 8 ? H.cA64 : H.cA32, P.A.cb)) ||
+        (rc = put_cb(sizeof(T) == 8 ? H.cAT64 : H.cAT32, P.AT.cb)))
+        return rc;
     if (idx) {
         if ((rc = put_i(H.SA.ptr, P.A.ptr)) || (rc = put_i(H.SA.col, P.A.col)) || (rc = put_i(H.SA.perm, P.A.perm)) ||
             (rc = put_i(H.ST.ptr, P.AT.ptr)) || (rc = put_i(H.ST.col, P.AT.col)) || (rc = put_i(H.ST.perm, P.AT.perm)) ||
@@ -424,6 +766,7 @@ struct DevInfo {
     int grid = 0;
     int sms = 0;
     size_t dyn64 = 0, dyn32 = 0;
+    bool maxl1 = false;  // grid of one CTA per SM without dynamic shared memory: prefer L1
 };
 
 template <typename T>
@@ -445,16 +788,19 @@ static int config_kernels(size_t dyn, char* err)
 }
 
 template <typename T>
-static int launch(int team, int threads, int grid, size_t dyn, const Args<T>& a, Args<T>* dev_args, int* queue,
-                  cudaStream_t st, char* err)
+static int launch(const DevInfo& D, size_t dyn, const Args<T>& a, Args<T>* dev_args, int* queue, cudaStream_t st,
+                  char* err)
 {
-    // The sparse products are bound by their random gathers: when the kernel
-    // needs little shared memory, give the rest of the SM's 256 KB to L1 so the
-    // gathered vector stays on chip.  (A per-kernel attribute of this process.)
-    const void* fn = team == SCS_TEAM_GRID ? kgrid_ptr<T>() : kblock_ptr<T>();
-    CU(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                            dyn == 0 ? (int)cudaSharedmemCarveoutMaxL1 : (int)cudaSharedmemCarveoutDefault), err);
+    const int team = D.team, threads = D.threads, grid = D.grid;
     if (team == SCS_TEAM_GRID) {
+        // Sliced-ELL products are bound by their random gathers: with one CTA
+        // per SM and no dynamic shared memory, give the rest of the SM's 256 KB
+        // to L1 so more of the gathered vector stays on chip.  (A per-kernel
+        // attribute of this process, so it is set before every launch.)
+        CU(cudaFuncSetAttribute(kgrid_ptr<T>(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                D.maxl1 && dyn == 0 ? (int)cudaSharedmemCarveoutMaxL1
+                                                    : (int)cudaSharedmemCarveoutDefault),
+           err);
         CU(cudaMemsetAsync(a.W.bar, 0, 4 * sizeof(unsigned), st), err);
         CU(cudaMemsetAsync(a.W.abort_flag, 0, 4 * sizeof(int), st), err);
         void* kargs[] = {(void*)&a};
@@ -547,7 +893,7 @@ static int run_setup_g(scs_work* w, const DevProb<T>& P, const DevWork<T>& W, Ar
     S.cg_max = std::max(10 * w->S.cg_max, 10000);
     S.cg_rtol = std::min(w->S.cg_rtol, sizeof(T) == 8 ? 1e-12 : 1e-7);
     Args<T> a = make_args(P, W, S, MODE_SETUP);
-    return launch<T>(w->D.team, w->D.threads, w->D.grid, dyn, a, dargs, w->queue, w->stream, w->err);
+    return launch<T>(w->D, dyn, a, dargs, w->queue, w->stream, w->err);
 }
 
 extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_settings* settings, void* cuda_stream,
@@ -560,7 +906,7 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     if (!w) { set_err(g_err, "host allocation failed"); return SCS_ENOMEM; }
     w->err[0] = 0;
     int rc = check_settings(settings, w->err);
-    if (!rc) rc = prepare(data, cone, w->H, w->err);
+    if (!rc) rc = prepare(data, cone, w->H, w->err, true);
     if (rc) { memcpy(g_err, w->err, 512); delete w; return rc; }
     w->S = *settings;
     w->stream = (cudaStream_t)cuda_stream;
@@ -576,13 +922,52 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     if (team == SCS_TEAM_AUTO) team = (work_size < 150000 || !coop) ? SCS_TEAM_BLOCK : SCS_TEAM_GRID;
     if (team == SCS_TEAM_GRID && !coop) { set_err(w->err, "device lacks cooperative launch"); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
     w->D.team = team;
-    w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? 1024 : 256);
+    w->D.threads = settings->threads ? settings->threads : (team == SCS_TEAM_GRID ? GRID_THREADS : 256);
+    if (team == SCS_TEAM_GRID && w->D.threads > GRID_THREADS) {
+        set_err(w->err, "the grid team runs at most %d threads per block (got %d)", GRID_THREADS, w->D.threads);
+        memcpy(g_err, w->err, 512);
+        delete w;
+        return SCS_EINVAL;
+    }
     w->has32 = settings->precision == SCS_MIXED;
     // the TMA-staged stream only on request: on the gather-bound products it
     // measured no faster than direct streaming loads
     const bool tma = team == SCS_TEAM_GRID && settings->spmv_path == 2;
-    w->D.dyn64 = dyn_smem<double>(H, w->D.threads, tma);
-    w->D.dyn32 = w->has32 ? dyn_smem<float>(H, w->D.threads, tma) : 0;
+    // column-blocked products for the grid team (one CTA per SM): built here,
+    // where the grid and the block size are known
+    bool cb = false;
+    if (team == SCS_TEAM_GRID && (settings->spmv_path == 0 || settings->spmv_path == 3)) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa64{}, fa32{};
+        cudaFuncGetAttributes(&fa64, kgrid_ptr<double>());
+        cudaFuncGetAttributes(&fa32, kgrid_ptr<float>());
+        const size_t stat = std::max(fa64.sharedSizeBytes, fa32.sharedSizeBytes);
+        if ((size_t)optin > stat + 2048) {
+            const size_t dyn_max = ((size_t)optin - stat - 1024) & ~size_t(15);
+            const int G = w->D.sms, nw = w->D.threads / 32 - 1;  // compute warps; the last warp copies
+            const bool force = settings->spmv_path == 3;
+            HostProb& Hm = w->H;
+            std::vector<std::thread> th;
+            th.emplace_back([&] { plan_cb(Hm.m, Hm.n, Hm.Ap, Hm.Ai, Hm.Ax, G, nw, 8, 1, dyn_max, force, Hm.cA64); });
+            th.emplace_back([&] { plan_cb(Hm.n, Hm.m, Hm.Tp, Hm.Ti, Hm.Tx, G, nw, 8, 2, dyn_max, force, Hm.cAT64); });
+            if (w->has32) {
+                th.emplace_back([&] { plan_cb(Hm.m, Hm.n, Hm.Ap, Hm.Ai, Hm.Ax, G, nw, 4, 1, dyn_max, force, Hm.cA32); });
+                th.emplace_back([&] { plan_cb(Hm.n, Hm.m, Hm.Tp, Hm.Ti, Hm.Tx, G, nw, 4, 2, dyn_max, force, Hm.cAT32); });
+            }
+            for (auto& t : th) t.join();
+            cb = H.cA64.ncb || H.cAT64.ncb || H.cA32.ncb || H.cAT32.ncb;
+        }
+    }
+    finish_layouts(w->H, !(H.cA64.ncb && (!w->has32 || H.cA32.ncb)), !(H.cAT64.ncb && (!w->has32 || H.cAT32.ncb)));
+    if ((long long)H.SA.ptr.back() >= (1ll << 31) || (long long)H.ST.ptr.back() >= (1ll << 31)) {
+        set_err(w->err, "padded matrix too large");
+        memcpy(g_err, w->err, 512);
+        delete w;
+        return SCS_EINVAL;
+    }
+    w->D.dyn64 = std::max({dyn_smem<double>(H, w->D.threads, tma), H.cA64.dyn(), H.cAT64.dyn()});
+    w->D.dyn32 = w->has32 ? std::max({dyn_smem<float>(H, w->D.threads, tma), H.cA32.dyn(), H.cAT32.dyn()}) : 0;
     int rc2 = config_kernels<double>(w->D.dyn64, w->err);
     if (!rc2 && w->has32) rc2 = config_kernels<float>(w->D.dyn32, w->err);
     if (rc2) { memcpy(g_err, w->err, 512); delete w; return rc2; }
@@ -595,7 +980,9 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
             nb = std::min(nb64, nb32);
         }
         if (nb < 1) { set_err(w->err, "solver kernel cannot be resident with %d threads", w->D.threads); memcpy(g_err, w->err, 512); delete w; return SCS_ECUDA; }
-        w->D.grid = w->D.sms * std::min(nb, 4);
+        // the column-blocked layout was cut for exactly one CTA per SM
+        w->D.grid = w->D.sms * (cb ? 1 : std::min(nb, 4));
+        w->D.maxl1 = !cb && std::min(nb, 4) == 1;
         if (tma) {
             warp_bounds(w->H.SA, w->D.grid * (w->D.threads / 32));
             warp_bounds(w->H.ST, w->D.grid * (w->D.threads / 32));
@@ -712,7 +1099,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         if (S.use_warm) CU(cudaMemcpyAsync(w->W32.warm, w->W64.warm, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
         Args<float> a32 = make_args(w->P32, w->W32, S32, MODE_SOLVE);
         CU(cudaEventRecord(w->ev[2], w->stream), w->err);
-        if ((rc = launch<float>(w->D.team, w->D.threads, w->D.grid, w->D.dyn32, a32, w->dargs32, w->queue, w->stream, w->err))) return rc;
+        if ((rc = launch<float>(w->D, w->D.dyn32, a32, w->dargs32, w->queue, w->stream, w->err))) return rc;
         CU(cudaEventRecord(w->ev[3], w->stream), w->err);
         // FP64 phase starts from the FP32 iterate and CG warm starts
         CU(cudaMemcpyAsync(w->W64.warm, w->W32.u_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
@@ -726,7 +1113,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
     }
     Args<double> a = make_args(w->P64, w->W64, S, MODE_SOLVE);
     CU(cudaEventRecord(w->ev[0], w->stream), w->err);
-    if ((rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
+    if ((rc = launch<double>(w->D, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
     CU(cudaEventRecord(w->ev[1], w->stream), w->err);
     DevState st{};
     int abort_flag = 0;
@@ -840,7 +1227,7 @@ static int single_op(scs_work* w, int mode, int slot, const double* in, double* 
     CU(cudaMemcpyAsync(w->W64.io_in, in, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     DevSettings S = dev_settings(&w->S);
     Args<double> a = make_args(w->P64, w->W64, S, mode, slot);
-    int rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
+    int rc = launch<double>(w->D, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
     if (rc) return rc;
     if (out) CU(cudaMemcpyAsync(out, w->W64.io_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     if (out2) CU(cudaMemcpyAsync(out2, w->W64.io_out2, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
@@ -856,13 +1243,45 @@ extern "C" int scs_profile(scs_work* w, int32_t precision, int32_t reps, double*
     if (precision == SCS_MIXED) {
         if (!w->has32) { set_err(w->err, "work was not set up with SCS_MIXED"); return SCS_EINVAL; }
         Args<float> a = make_args(w->P32, w->W32, S, MODE_PROFILE, reps);
-        if ((rc = launch<float>(w->D.team, w->D.threads, w->D.grid, w->D.dyn32, a, w->dargs32, w->queue, w->stream, w->err))) return rc;
+        if ((rc = launch<float>(w->D, w->D.dyn32, a, w->dargs32, w->queue, w->stream, w->err))) return rc;
         CU(cudaMemcpyAsync(ns, w->W32.io_out, 5 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
     } else {
         Args<double> a = make_args(w->P64, w->W64, S, MODE_PROFILE, reps);
-        if ((rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
+        if ((rc = launch<double>(w->D, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err))) return rc;
         CU(cudaMemcpyAsync(ns, w->W64.io_out, 5 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
     }
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_spmv(scs_work* w, int32_t precision, int32_t op, const double* in, const double* in2, double* out,
+                        double* out2)
+{
+    if (!w || !in || !out || op < 0 || op > 2 || (op == 2 && (!in2 || !out2))) {
+        set_err(w ? w->err : g_err, "bad arguments");
+        return SCS_EINVAL;
+    }
+    if (precision != SCS_FP64 && precision != SCS_MIXED) { set_err(w->err, "bad precision"); return SCS_EINVAL; }
+    if (precision == SCS_MIXED && !w->has32) { set_err(w->err, "work was not set up with SCS_MIXED"); return SCS_EINVAL; }
+    const int n = w->H.n, m = w->H.m;
+    const int nin = op == 0 ? n : m, nout = op == 0 ? m : n;
+    double* io_in = precision == SCS_MIXED ? w->W32.io_in : w->W64.io_in;
+    double* io_out = precision == SCS_MIXED ? w->W32.io_out : w->W64.io_out;
+    double* io_out2 = precision == SCS_MIXED ? w->W32.io_out2 : w->W64.io_out2;
+    CU(cudaMemcpyAsync(io_in, in, sizeof(double) * nin, cudaMemcpyDefault, w->stream), w->err);
+    if (op == 2) CU(cudaMemcpyAsync(io_out2, in2, sizeof(double) * m, cudaMemcpyDefault, w->stream), w->err);
+    DevSettings S = dev_settings(&w->S);
+    int rc;
+    if (precision == SCS_MIXED) {
+        Args<float> a = make_args(w->P32, w->W32, S, MODE_SPMV, op);
+        rc = launch<float>(w->D, w->D.dyn32, a, w->dargs32, w->queue, w->stream, w->err);
+    } else {
+        Args<double> a = make_args(w->P64, w->W64, S, MODE_SPMV, op);
+        rc = launch<double>(w->D, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
+    }
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, io_out, sizeof(double) * nout, cudaMemcpyDefault, w->stream), w->err);
+    if (op == 2) CU(cudaMemcpyAsync(out2, io_out2, sizeof(double) * nout, cudaMemcpyDefault, w->stream), w->err);
     CU(cudaStreamSynchronize(w->stream), w->err);
     return SCS_OK;
 }
@@ -876,7 +1295,7 @@ extern "C" int scs_residuals(scs_work* w, const double* x, const double* y, cons
     CU(cudaMemcpyAsync(w->W64.io_out2, s, sizeof(double) * m, cudaMemcpyDefault, w->stream), w->err);
     DevSettings S = dev_settings(&w->S);
     Args<double> a = make_args(w->P64, w->W64, S, MODE_RESID);
-    int rc = launch<double>(w->D.team, w->D.threads, w->D.grid, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
+    int rc = launch<double>(w->D, w->D.dyn64, a, w->dargs64, w->queue, w->stream, w->err);
     if (rc) return rc;
     CU(cudaMemcpyAsync(out, w->W64.io_out, 3 * sizeof(double), cudaMemcpyDefault, w->stream), w->err);
     CU(cudaStreamSynchronize(w->stream), w->err);

@@ -8,7 +8,7 @@
 //
 //   BlockTeam : one CTA solves one instance (small problems, batched solves).
 //   GridTeam  : every CTA of a cooperative launch solves one large instance;
-//               barriers are a generation-counting grid barrier whose waits
+//               barriers count arrivals on one 64-bit counter and their waits
 //               are bounded by a 10 s timer (on expiry an abort flag is set,
 //               every later barrier returns at once and the solver exits).
 //
@@ -34,6 +34,7 @@ __device__ __forceinline__ void block_partial(double (&v)[K], double* red)
 }
 
 struct BlockTeam {
+    static constexpr bool kGrid = false;
     double* red;
     unsigned char* stage;      // TMA staging (unused by this team: null)
     unsigned long long* mbar;  // per-warp mbarriers
@@ -63,14 +64,17 @@ struct BlockTeam {
 };
 
 struct GridTeam {
+    static constexpr bool kGrid = true;
     double* red;          // shared memory
     unsigned char* stage;      // dynamic shared memory: per-warp TMA staging (null when off)
+    unsigned char* dsm;        // dynamic shared memory base (column-blocked products)
     unsigned long long* mbar;  // shared: 2 mbarriers per warp
     unsigned* ph;              // shared: phase bits per warp
     double* partials;     // global, [2][KMAX][gridDim.x]
-    unsigned* bar;        // global, [0] arrival count, [1] generation
+    unsigned* bar;        // global, 16 bytes zeroed before the launch: [0..1] 64-bit arrival count
     int* abort_flag;      // global
     int parity;
+    unsigned long long epoch;  // barriers passed so far (the same in every thread of the grid)
 
     __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
@@ -79,71 +83,22 @@ struct GridTeam {
     __device__ __forceinline__ int nblocks() const { return gridDim.x; }
     __device__ __forceinline__ bool aborted() const { return *(volatile int*)abort_flag != 0; }
 
+    // Grid barrier on one monotonically increasing 64-bit arrival count: the
+    // e-th barrier is passed once the count reaches e * gridDim.x, so no
+    // reset or separate release write is needed.  The wait is bounded.
     __device__ void sync()
     {
         __syncthreads();
         if (threadIdx.x == 0) {
-            volatile unsigned* vgen = bar + 1;
+            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(bar);
             if (*(volatile int*)abort_flag == 0) {
-                unsigned gen = *vgen;
+                const unsigned long long target = (epoch + 1) * gridDim.x;
                 __threadfence();
-                unsigned prev = atomicAdd(bar, 1u);
-                if (prev == gridDim.x - 1) {
-                    atomicExch(bar, 0u);
-                    __threadfence();
-                    atomicAdd(bar + 1, 1u);
-                } else {
-                    unsigned long long t0 = gtimer();
-                    unsigned ns = 16;
-                    while (*vgen == gen) {
-                        if (*(volatile int*)abort_flag != 0) break;
-                        if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
-                            atomicExch(abort_flag, 1);
-                            break;
-                        }
-                        __nanosleep(ns);
-                        if (ns < 128) ns <<= 1;
-                    }
-                }
-                __threadfence();
-            }
-        }
-        __syncthreads();
-    }
-
-    // Team-wide sum of K values.  Every block writes its partial, then arrives
-    // at the grid barrier; the last block to arrive sums the partials in
-    // block order, publishes the K results and only then releases the
-    // barrier, so every block reads the same K numbers (deterministic).
-    template <int K>
-    __device__ void reduce(double (&v)[K])
-    {
-        __shared__ int s_last;
-        block_partial<K>(v, red);
-        const int nw = blockDim.x >> 5;
-        const int B = gridDim.x;
-        double* P = partials + (size_t)parity * KMAX * B;
-        double* R = partials + (size_t)2 * KMAX * B + (size_t)parity * KMAX;
-        if (threadIdx.x < K) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
-            P[(size_t)threadIdx.x * B + blockIdx.x] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int last = 0;
-            volatile unsigned* vgen = bar + 1;
-            if (*(volatile int*)abort_flag == 0) {
-                const unsigned gen = *vgen;
-                __threadfence();
-                const unsigned prev = atomicAdd(bar, 1u);
-                if (prev == gridDim.x - 1) {
-                    __threadfence();
-                    last = 1;
-                } else {
+                const unsigned long long prev = atomicAdd(cnt, 1ull);
+                if (prev + 1 < target) {
                     const unsigned long long t0 = gtimer();
-                    unsigned ns = 16;
-                    while (*vgen == gen) {
+                    unsigned ns = 8;
+                    while (*(volatile unsigned long long*)cnt < target) {
                         if (*(volatile int*)abort_flag != 0) break;
                         if (gtimer() - t0 > BARRIER_TIMEOUT_NS) {
                             atomicExch(abort_flag, 1);
@@ -152,35 +107,45 @@ struct GridTeam {
                         __nanosleep(ns);
                         if (ns < 64) ns <<= 1;
                     }
-                    __threadfence();
                 }
+                __threadfence();
             }
-            s_last = last;
         }
+        ++epoch;
         __syncthreads();
-        if (s_last) {
-            // all threads of the last block: thread j loads block j's K partials
-            double pv[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) pv[k] = 0.0;
-            for (int j = threadIdx.x; j < B; j += blockDim.x)
-#pragma unroll
-                for (int k = 0; k < K; ++k) pv[k] += __ldcg(P + (size_t)k * B + j);
-            block_partial<K>(pv, red);
-            if (threadIdx.x < K) {
-                double s = 0.0;
-                for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
-                R[threadIdx.x] = s;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            }
+    }
+
+    // Team-wide sum of K values.  Every block writes its K partials, passes
+    // the grid barrier, then reads all blocks' partials and sums them in
+    // block order with the same fixed tree, so every block gets the same K
+    // numbers (deterministic).  Partials are double-buffered: a block can
+    // only overwrite a buffer after the next barrier, which every block
+    // reaches only once it has read this one.
+    template <int K>
+    __device__ void reduce(double (&v)[K])
+    {
+        block_partial<K>(v, red);
+        const int nw = blockDim.x >> 5;
+        const int B = gridDim.x;
+        double* P = partials + (size_t)parity * KMAX * B;
+        if (threadIdx.x < K) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
+            P[(size_t)threadIdx.x * B + blockIdx.x] = s;
         }
-        if (threadIdx.x < K) red[MAX_WARPS * KMAX + threadIdx.x] = __ldcg(R + threadIdx.x);
+        sync();
+        double pv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) pv[k] = 0.0;
+        for (int j = threadIdx.x; j < B; j += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < K; ++k) pv[k] += __ldcg(P + (size_t)k * B + j);
+        block_partial<K>(pv, red);
+        if (threadIdx.x < K) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
+            red[MAX_WARPS * KMAX + threadIdx.x] = s;
+        }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = red[MAX_WARPS * KMAX + k];

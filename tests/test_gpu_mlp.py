@@ -24,7 +24,8 @@ def _blocks(dims):
     return np.cumsum([0] + sizes)
 
 
-@pytest.mark.parametrize("dims,batch", [((40, 64, 50), 32), ((300, 128, 1001), 77), ((2000, 256, 2203), 256)])
+@pytest.mark.parametrize("dims,batch", [((40, 64, 50), 32), ((300, 128, 1001), 77), ((2000, 256, 2203), 256),
+                                        ((2000, 1024, 22004), 256)])  # the last: the warm-start network itself
 def test_gradients_vs_oracle(dims, batch):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(sum(dims))
