@@ -357,41 +357,31 @@ __device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& x
 
 // One segment from its stage: compute warp w runs its slices (matrix
 // entries, the vector slice and the metadata all in shared memory); row sums
-// are reduced over the V lanes of a row and added to acc (w's rows are its
-// own, so plain read-modify-writes do not race).
+// are reduced over the V = 32 / H lanes of a row and added to acc (rows of a
+// segment are distinct, so plain read-modify-writes do not race).  Takes
+// plain values, so the hot loop touches no local memory.
 template <typename T>
-__device__ __forceinline__ void cb_segment(const Cblk<T>& C, const int* mt, const T* xs, const unsigned short* scol,
+__device__ __forceinline__ void cb_segment(int nw, int H, const int* mt, const T* xs, const unsigned short* scol,
                                            const T* sval, T* acc)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int H = 32 / C.V;
     const int ns = mt[4];
     const int* wl = mt + 5;
-    const int* st = wl + C.nw + 1;
+    const int* st = wl + nw + 1;
     const unsigned short* sr = (const unsigned short*)(st + ns + 1);
     const int s_hi = wl[w + 1];
-    constexpr int U = 8;  // steps in flight per lane: eight independent gather chains
     for (int s = wl[w]; s < s_hi; ++s) {
         const int t1 = st[s + 1];
-        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int t = st[s]; t < t1; t += U) {
-            int c[U];
-            T v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = t + u < t1;  // steps past the slice: offset 0, value 0
-                c[u] = ok ? (int)scol[(t + u) * 32 + lane] : 0;
-                v[u] = ok ? sval[(t + u) * 32 + lane] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < U; u += 4) {
-                a0 = fmaT(v[u], xs[c[u]], a0);
-                a1 = fmaT(v[u + 1], xs[c[u + 1]], a1);
-                a2 = fmaT(v[u + 2], xs[c[u + 2]], a2);
-                a3 = fmaT(v[u + 3], xs[c[u + 3]], a3);
-            }
+        int t = st[s];
+        T a0 = 0, a1 = 0;
+        for (; t + 2 <= t1; t += 2) {
+            const int c0 = scol[t * 32 + lane], c1 = scol[t * 32 + 32 + lane];
+            const T v0 = sval[t * 32 + lane], v1 = sval[t * 32 + 32 + lane];
+            a0 = fmaT(v0, xs[c0], a0);
+            a1 = fmaT(v1, xs[c1], a1);
         }
-        T a = (a0 + a1) + (a2 + a3);
+        if (t < t1) a0 = fmaT(sval[t * 32 + lane], xs[scol[t * 32 + lane]], a0);
+        T a = a0 + a1;
         for (int o = H; o < 32; o <<= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
         if (lane < H) {
             const int r = sr[s * H + lane];
@@ -402,67 +392,83 @@ __device__ __forceinline__ void cb_segment(const Cblk<T>& C, const int* mt, cons
 
 // acc[0, R) + acc[acc_rows, acc_rows + R) = (rows of this CTA's range) . x
 // over all column blocks (even segments into the first buffer, odd into the
-// second), through the ring of S stages: full barriers tm.mbar[0..S-1], empty barriers
-// tm.mbar[CB_MAX_STAGES + s]; tm.ph[s] counts the stage's past uses, so use u
-// of this pass waits on parity (ph[s] + u) & 1.  Returns false if a wait ran
-// out of time (the abort flag is then set and the copies still in flight are
-// waited for, bounded, before returning).
+// second), through the ring of S stages: full barriers tm.mbar[0..S-1], empty
+// barriers tm.mbar[CB_MAX_STAGES + s]; tm.ph[s] counts the stage's past uses,
+// so use u of this pass waits on parity (ph[s] + u) & 1.  Every field the
+// loops need is read once into registers (the structs live in local memory,
+// which misses the small L1 left beside the stages).  Returns false if a wait
+// ran out of time (the abort flag is then set and the copies still in
+// flight are waited for, bounded, before returning).
 template <typename T>
 __device__ bool cb_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* acc, unsigned long long pol)
 {
     constexpr int E = 16 / (int)sizeof(T);
-    const int S = C.S, ncb = C.ncb;
+    const int S = C.S, ncb = C.ncb, nw = C.nw, H = 32 / C.V, ms = C.ms, cw = C.cw, cols = C.cols;
+    const int off_x = C.off_x, off_col = C.off_col, off_val = C.off_val, ar = C.acc_rows;
+    const int* meta = C.meta;
+    const unsigned short* gcol = C.col;
+    const T* gval = C.val;
+    unsigned char* st0 = tm.dsm + C.stage_off;
+    const int stage_bytes = C.stage_bytes;
+    unsigned long long* mbar = tm.mbar;
+    unsigned* ph = tm.ph;
+    int* abort_flag = tm.abort_flag;
     const int g0 = blockIdx.x * ncb;
     const int k0 = blockIdx.x % ncb;  // first column block of this CTA
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mis = (int)(((uintptr_t)x & 15) / sizeof(T));
-    unsigned char* st0 = tm.dsm + C.stage_off;
-    auto stage = [&](int s) { return st0 + (size_t)s * C.stage_bytes; };
-    auto full = [&](int s) { return smem_addr(&tm.mbar[s]); };
-    auto empty = [&](int s) { return smem_addr(&tm.mbar[CB_MAX_STAGES + s]); };
-    auto blk = [&](int j) { return (k0 + j) % ncb; };  // column block of the j-th segment visited
-    __syncthreads();  // stages free, acc zeroed, tm.ph current
-    unsigned base[CB_MAX_STAGES];
-#pragma unroll
-    for (int s = 0; s < CB_MAX_STAGES; ++s) base[s] = tm.ph[s];
+    auto stage = [=](int s) { return st0 + (size_t)s * stage_bytes; };
+    auto full = [=](int s) { return smem_addr(&mbar[s]); };
+    auto empty = [=](int s) { return smem_addr(&mbar[CB_MAX_STAGES + s]); };
+    auto blk = [=](int j) { return (k0 + j) % ncb; };  // column block of the j-th segment visited
+    __syncthreads();  // stages free, acc zeroed, ph current
     bool ok = true;
     int issued = 0;
-    if (w == C.nw) {
+    if (w == nw) {
         // producer warp: lane 0 issues every copy
         if (lane == 0) {
-            auto issue = [&](int j, int e0, int e1) {
+            auto issue = [=](int j, int e0, int e1) {
                 const int s = j % S, k = blk(j);
                 unsigned char* d = stage(s);
-                const int len = min(C.cw, C.cols - k * C.cw);
+                const int len = min(cw, cols - k * cw);
                 const unsigned xb = (unsigned)((mis + len + E - 1) / E) * 16u;
                 const unsigned ne = (unsigned)(e1 - e0);
-                const unsigned mb = (unsigned)C.ms * 4u;
+                const unsigned mb = (unsigned)ms * 4u;
                 mbar_expect_tx(full(s), mb + xb + ne * (2u + (unsigned)sizeof(T)));
-                tma_load_1d_plain(smem_addr(d), C.meta + (size_t)(g0 + k) * C.ms, mb, full(s));
-                tma_load_1d_plain(smem_addr(d + C.off_x), x + (size_t)k * C.cw - mis, xb, full(s));
+                tma_load_1d_plain(smem_addr(d), meta + (size_t)(g0 + k) * ms, mb, full(s));
+                tma_load_1d_plain(smem_addr(d + off_x), x + (size_t)k * cw - mis, xb, full(s));
                 if (ne) {
-                    tma_load_1d(smem_addr(d + C.off_col), C.col + e0, ne * 2u, full(s), pol);
-                    tma_load_1d(smem_addr(d + C.off_val), C.val + e0, ne * (unsigned)sizeof(T), full(s), pol);
+                    tma_load_1d(smem_addr(d + off_col), gcol + e0, ne * 2u, full(s), pol);
+                    tma_load_1d(smem_addr(d + off_val), gval + e0, ne * (unsigned)sizeof(T), full(s), pol);
                 }
             };
             // x was written by generic stores (other CTAs, before the last
             // grid barrier) and is read here by the async proxy
             fence_proxy_async_all();
             const int npro = min(S, ncb);
-            int e0[CB_MAX_STAGES], e1[CB_MAX_STAGES];
-#pragma unroll
-            for (int j = 0; j < CB_MAX_STAGES; ++j)
-                if (j < npro) {
-                    e0[j] = ro(C.meta + (size_t)(g0 + blk(j)) * C.ms);
-                    e1[j] = ro(C.meta + (size_t)(g0 + blk(j)) * C.ms + 1);
-                }
-#pragma unroll
-            for (int j = 0; j < CB_MAX_STAGES; ++j)
-                if (j < npro) issue(j, e0[j], e1[j]);
+            int e0a = 0, e1a = 0, e0b = 0, e1b = 0, e0c = 0, e1c = 0, e0d = 0, e1d = 0;
+            e0a = ro(meta + (size_t)(g0 + blk(0)) * ms);
+            e1a = ro(meta + (size_t)(g0 + blk(0)) * ms + 1);
+            if (npro > 1) {
+                e0b = ro(meta + (size_t)(g0 + blk(1)) * ms);
+                e1b = ro(meta + (size_t)(g0 + blk(1)) * ms + 1);
+            }
+            if (npro > 2) {
+                e0c = ro(meta + (size_t)(g0 + blk(2)) * ms);
+                e1c = ro(meta + (size_t)(g0 + blk(2)) * ms + 1);
+            }
+            if (npro > 3) {
+                e0d = ro(meta + (size_t)(g0 + blk(3)) * ms);
+                e1d = ro(meta + (size_t)(g0 + blk(3)) * ms + 1);
+            }
+            issue(0, e0a, e1a);
+            if (npro > 1) issue(1, e0b, e1b);
+            if (npro > 2) issue(2, e0c, e1c);
+            if (npro > 3) issue(3, e0d, e1d);
             issued = npro;
             for (int j = S; j < ncb; ++j) {
                 const int s = j % S;
-                if (!mbar_wait(empty(s), (base[s] + j / S - 1) & 1u, tm.abort_flag)) {
+                if (!mbar_wait(empty(s), (ph[s] + j / S - 1) & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -477,32 +483,32 @@ __device__ bool cb_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* acc
     } else {
         for (int j = 0; j < ncb; ++j) {
             const int s = j % S;
-            if (!mbar_wait(full(s), (base[s] + j / S) & 1u, tm.abort_flag)) {
+            if (!mbar_wait(full(s), (ph[s] + j / S) & 1u, abort_flag)) {
                 ok = false;
                 break;
             }
             if (j >= 2) {  // every warp is done with segment j-2 (same partial-sum buffer)
                 const int s2 = (j - 2) % S;
-                if (!mbar_wait(empty(s2), (base[s2] + (j - 2) / S) & 1u, tm.abort_flag)) {
+                if (!mbar_wait(empty(s2), (ph[s2] + (j - 2) / S) & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
             }
             const unsigned char* d = stage(s);
-            cb_segment<T>(C, (const int*)d, (const T*)(d + C.off_x) + mis, (const unsigned short*)(d + C.off_col),
-                          (const T*)(d + C.off_val), acc + (j & 1) * C.acc_rows);
+            cb_segment<T>(nw, H, (const int*)d, (const T*)(d + off_x) + mis, (const unsigned short*)(d + off_col),
+                          (const T*)(d + off_val), acc + (j & 1) * ar);
             __syncwarp();
             if (lane == 0) mbar_arrive(empty(s));
         }
     }
     const bool all_ok = __syncthreads_and(ok);
-    if (!all_ok && w == C.nw && lane == 0) {
+    if (!all_ok && w == nw && lane == 0) {
         // copies of the last S issued segments may still be in flight
-        for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full(j % S), (base[j % S] + j / S) & 1u, nullptr);
+        for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full(j % S), (ph[j % S] + j / S) & 1u, nullptr);
     }
+    __syncthreads();  // everyone has read ph for this pass
     if (threadIdx.x == 0 && all_ok)
-        for (int s = 0; s < S; ++s) tm.ph[s] += (unsigned)((ncb - s + S - 1) / S);
-    __syncthreads();
+        for (int s = 0; s < S; ++s) ph[s] += (unsigned)((ncb - s + S - 1) / S);
     return all_ok;
 }
 
