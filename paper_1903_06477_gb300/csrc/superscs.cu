@@ -300,6 +300,61 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
     std::vector<long long> load;
     int ms = 4;
     long long max_e = 0;
+    // Entry placement inside a slice.  Every lane of a step gathers one
+    // element of the vector slice from shared memory; lanes whose elements
+    // share a bank are served one after another.  The row of each lane is
+    // fixed, but which of its entries goes to which step is free, so each
+    // step takes, lane by lane, the row's remaining entry in the least-used
+    // bank (FP32: column mod 32 over the warp; FP64: column mod 16 within each
+    // half-warp, which is served separately).  Padding lanes point at a
+    // column in a free bank (value 0).  A staged slice starts at a shift that
+    // is the same for all its elements, so distinct banks stay distinct.
+    const int nbank = C.esize == 8 ? 16 : 32;
+    std::vector<std::vector<int>> rem(32);
+    auto place_slice = [&](size_t e0, int nsteps, int k) {
+        const int len_k = std::min(cw, cols - k * cw);
+        for (int t = 0; t < nsteps; ++t) {
+            int cnt[2][32] = {};
+            bool pad[32] = {};
+            for (int q = 0; q < V; ++q)
+                for (int rr = 0; rr < H; ++rr) {
+                    const int lane = q * H + rr, half = nbank == 16 ? lane >> 4 : 0;
+                    std::vector<int>& rl = rem[rr];
+                    if (rl.empty()) {
+                        pad[lane] = true;
+                        continue;
+                    }
+                    size_t best = 0;
+                    int bc = 1 << 30;
+                    for (size_t i = 0; i < rl.size(); ++i) {
+                        const int c = cnt[half][(ci[rl[i]] - k * cw) % nbank];
+                        if (c < bc) {
+                            bc = c;
+                            best = i;
+                        }
+                    }
+                    const int e = rl[best];
+                    rl[best] = rl.back();
+                    rl.pop_back();
+                    const int lc = ci[e] - k * cw;
+                    cnt[half][lc % nbank]++;
+                    const size_t idx = e0 + (size_t)t * 32 + lane;
+                    C.col[idx] = (uint16_t)lc;
+                    C.val[idx] = vx[e];
+                }
+            for (int lane = 0; lane < 32; ++lane) {
+                if (!pad[lane]) continue;
+                const int half = nbank == 16 ? lane >> 4 : 0;
+                int bb = 0;
+                for (int b2 = 1; b2 < nbank && b2 < len_k; ++b2)
+                    if (cnt[half][b2] < cnt[half][bb]) bb = b2;
+                cnt[half][bb]++;
+                const size_t idx = e0 + (size_t)t * 32 + lane;
+                C.col[idx] = (uint16_t)bb;
+                C.val[idx] = 0.0;
+            }
+        }
+    };
     for (int b = 0; b < G; ++b) {
         const int r0 = rb[b], R = rb[b + 1] - r0;
         bk.build(r0, R, ncb, cw, rp, ci);
@@ -326,18 +381,15 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
                 C.val.resize(e0 + size, 0.0);
                 for (int rr = 0; rr < H; ++rr) {
                     const size_t pos = (size_t)sl * H + rr;
+                    rem[rr].clear();
                     if (pos >= rows_k.size()) continue;
                     const int lr = rows_k[pos];
                     srow[(size_t)oi * H + rr] = (uint16_t)lr;
                     const size_t q0 = (size_t)bk.start[(size_t)k * R + lr];
                     const int len = bk.cnt[(size_t)k * R + lr];
-                    for (int j = 0; j < len; ++j) {
-                        const int e = bk.epos[q0 + j];
-                        const size_t idx = e0 + (size_t)(j / V) * 32 + (size_t)(j % V) * H + rr;
-                        C.col[idx] = (uint16_t)(ci[e] - k * cw);
-                        C.val[idx] = vx[e];
-                    }
+                    for (int j = 0; j < len; ++j) rem[rr].push_back(bk.epos[q0 + j]);
                 }
+                place_slice(e0, steps[sl], k);
                 t += steps[sl];
             }
             sstart[ns] = t;
