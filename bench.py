@@ -377,6 +377,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
     ap.add_argument("--cg-adapt", type=float, default=None)
     ap.add_argument("--mixed-switch", type=float, default=None)
+    ap.add_argument("--mixed-stall", type=int, default=None)
     ap.add_argument("--c5-train", type=int, default=16384, help="training instances of the learned warm start")
     ap.add_argument("--c5-epochs", type=int, default=60)
     ap.add_argument("--c5-family", default="random", choices=["random", "smooth"],
@@ -413,6 +414,11 @@ def main():
         kw["cg_adapt"] = args.cg_adapt
     if args.mixed_switch is not None:
         kw["mixed_switch"] = args.mixed_switch
+    if args.mixed_stall is not None:
+        kw["mixed_stall"] = args.mixed_stall
+    for key in ("cg_adapt", "mixed_switch", "mixed_stall"):
+        if key in kw:
+            cfg[key] = kw[key]
     prec = B.MIXED if args.precision == "mixed" else B.FP64
     n, m = prob["A"].shape[1], prob["A"].shape[0]
     work = B.Work(prob, stream=stream, precision=prec, **kw)

@@ -358,12 +358,20 @@ __device__ __forceinline__ void sell_tma(const Team& tm, const Sell<T>& S, XF& x
 // One segment from its stage: compute warp w runs its slices (matrix
 // entries, the vector slice and the metadata all in shared memory); row sums
 // are reduced over the V = 32 / H lanes of a row and added to acc (rows of a
-// segment are distinct, so plain read-modify-writes do not race).  Takes
-// plain values, so the hot loop touches no local memory.
+// segment are distinct, so plain read-modify-writes do not race).  Operands
+// are byte offsets into the dynamic shared memory, indexed through the
+// shared array itself so the loads are 32-bit-addressed shared loads and the
+// hot loop touches no local memory.
 template <typename T>
-__device__ __forceinline__ void cb_segment(int nw, int H, const int* mt, const T* xs, const unsigned short* scol,
-                                           const T* sval, T* acc)
+__device__ __forceinline__ void cb_segment(int nw, int H, unsigned mt_off, unsigned xs_off, unsigned col_off,
+                                           unsigned val_off, unsigned acc_off)
 {
+    extern __shared__ __align__(128) unsigned char cb_sm[];
+    const int* mt = (const int*)(cb_sm + mt_off);
+    const T* xs = (const T*)(cb_sm + xs_off);
+    const unsigned short* scol = (const unsigned short*)(cb_sm + col_off);
+    const T* sval = (const T*)(cb_sm + val_off);
+    T* acc = (T*)(cb_sm + acc_off);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ns = mt[4];
     const int* wl = mt + 5;
@@ -408,7 +416,9 @@ __device__ bool cb_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* acc
     const int* meta = C.meta;
     const unsigned short* gcol = C.col;
     const T* gval = C.val;
-    unsigned char* st0 = tm.dsm + C.stage_off;
+    unsigned char* const tm_dsm = tm.dsm;
+    unsigned char* st0 = tm_dsm + C.stage_off;
+    const unsigned acc_off = (unsigned)((unsigned char*)acc - tm_dsm);
     const int stage_bytes = C.stage_bytes;
     unsigned long long* mbar = tm.mbar;
     unsigned* ph = tm.ph;
@@ -494,9 +504,9 @@ __device__ bool cb_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* acc
                     break;
                 }
             }
-            const unsigned char* d = stage(s);
-            cb_segment<T>(nw, H, (const int*)d, (const T*)(d + off_x) + mis, (const unsigned short*)(d + off_col),
-                          (const T*)(d + off_val), acc + (j & 1) * ar);
+            const unsigned so = (unsigned)(stage(s) - tm_dsm);
+            cb_segment<T>(nw, H, so, so + off_x + mis * (unsigned)sizeof(T), so + off_col, so + off_val,
+                          acc_off + (unsigned)((j & 1) * ar * (int)sizeof(T)));
             __syncwarp();
             if (lane == 0) mbar_arrive(empty(s));
         }
