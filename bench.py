@@ -30,6 +30,32 @@ METRIC = "solves/s and time-to-1e-5 KKT residual: chosen form vs plain FP64, 1 G
 FALLBACK_HBM_GBS = 6800.0
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# solver launch, from one ncu capture (one pass per launch; summary and command
+# in profiles/k_grid_c2_fp32_phase_dram.md).  Valid only for the kernel sources
+# it was taken on (their digest) and for the same deterministic solve (same
+# outer and CG iteration counts); otherwise the roofline reports null.
+MEASURED_TRAFFIC = {
+    ("c2", "mixed"): {"bytes": 794206069504, "iters_fp32": 243, "cg_iters": 5801,
+                      "digest": "e6e78e824c3698e0e8e3231214a55fe8e19ed62ea855d67731873f880280ab0d"},
+}
+
+
+def _src_digest():
+    """sha256 over the CUDA sources and public headers (sorted by path)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1903_06477_gb300", "csrc", "*"))
+                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.relpath(f, ROOT).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -201,6 +227,32 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_products(args):
+    """Profiling aid: the solver's own sparse product (column-blocked on the
+    large workloads) on the workload's matrix, ``--products`` times, in the
+    bulk precision of ``--precision`` (mixed: FP32 copy); prints the device
+    time of each call's launch and checks the last result against scipy."""
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prob, kw, _ = build_workload(args.workload, 0)
+    prec = B.MIXED if args.precision == "mixed" else B.FP64
+    work = B.Work(prob, precision=B.MIXED if prec == B.MIXED else B.FP64, **kw)
+    op = 0 if args.op == "a" else 1
+    v = np.random.default_rng(0).standard_normal(work.n if op == 0 else work.m)
+    times = []
+    for _ in range(args.products):
+        t0 = time.perf_counter()
+        out = work.spmv(v, op=op, precision=prec)
+        times.append(time.perf_counter() - t0)
+    ref = prob["A"] @ v if op == 0 else prob["A"].T @ v
+    err = float(np.abs(out - ref).max() / max(1e-300, np.abs(ref).max()))
+    print(json.dumps({"products": args.products, "op": args.op, "precision": args.precision,
+                      "host_ms_per_call": 1e3 * float(np.mean(times)), "max_rel_err": err}), flush=True)
+    work.close()
+    return 0 if err < (1e-4 if prec == B.MIXED else 1e-12) else 1
 
 
 def run_batch(args):
@@ -383,7 +435,12 @@ def main():
     ap.add_argument("--c5-family", default="random", choices=["random", "smooth"],
                     help="random: a new 5%% support per instance (the specified family); smooth: fixed support, "
                          "+-10%% amplitudes")
+    ap.add_argument("--products", type=int, default=0,
+                    help="profiling aid: set up the workload, run this many sparse products (see --op) and exit")
+    ap.add_argument("--op", default="a", choices=["a", "at"], help="product for --products: A x or A^T y")
     args = ap.parse_args()
+    if args.products > 0:
+        return run_products(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
@@ -475,10 +532,16 @@ def main():
     ks = float(np.mean([i["kernel_s"][phase] for i in infos]))
     abytes = algorithmic_bytes(prob, last, phase)
     achieved = abytes / ks / 1e9
+    digest = _src_digest()
+    mt = MEASURED_TRAFFIC.get((args.workload, args.precision))
+    traffic = None
+    if (mt is not None and mt["digest"] == digest and phase == 1 and last["iters_fp32"] == mt["iters_fp32"]
+            and last["cg_iters"] == mt["cg_iters"]):
+        traffic = mt["bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind,
+                "traffic": traffic, "peak_source": peak_kind,
                 "kernel": "k_grid<float> (FP32 phase)" if phase == 1 else "k_grid<double> (FP64 phase)",
-                "kernel_ms": ks * 1e3, "algorithmic_bytes": abytes}
+                "kernel_ms": ks * 1e3, "algorithmic_bytes": abytes, "src_digest": digest[:16]}
     # e2e through the public API with host buffers: setup (H2D of A,b,c) + solve + D2H of x,y,s
     e2e = None
     if args.e2e_steps > 0:
