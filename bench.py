@@ -232,8 +232,8 @@ def run_reference(args):
 def run_products(args):
     """Profiling aid: the solver's own sparse product (column-blocked on the
     large workloads) on the workload's matrix, ``--products`` times, in the
-    bulk precision of ``--precision`` (mixed: FP32 copy); prints the device
-    time of each call's launch and checks the last result against scipy."""
+    bulk precision of ``--precision`` (mixed: FP32 copy); prints the mean
+    host time per call and checks the last result against scipy."""
     import torch
     from paper_1903_06477_gb300 import binding as B
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -371,7 +371,12 @@ def run_c5(args):
     warm_b = batch_of(gte)
     for _ in range(max(1, args.warmup)):
         cold_b.solve()
-        net.forward(Xt, Yt)
+        net.forward(Xt, Yt)  # the whole inference path, so one-time initialisation stays out of the timing
+        Yd = Yt.double()
+        Yd[:, -1] = 1.0
+        warm_b.set_warm([Yd[j] for j in range(256)])
+        warm_b.solve()
+        torch.cuda.synchronize()
     cold_t, warm_t, inf_t = [], [], []
     cold_i = warm_i = None
     with Clocks(0) as clk:

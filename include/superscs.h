@@ -103,16 +103,17 @@ typedef struct {
                             block team: 256, or the batch autotuner's choice) */
     double mixed_cg_rtol;   /* CG tolerance of the FP32 phase (SCS_MIXED) */
     int32_t mixed_stall;    /* FP32 phase ends after this many iterations without a
-                               10% drop of max(pr,dr,gap) (SCS_MIXED) */
+                               10% drop of ||Ru|| below its best value (SCS_MIXED) */
     int32_t mixed_max_iters;/* cap on FP32-phase iterations (SCS_MIXED) */
     double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
     int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- the column-blocked
                                layout (vector slices staged in shared memory, one CTA per SM) where
-                               each CTA gets at least 2048 entries per column block, else sliced
-                               ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL, TMA-staged
-                               stream; 3: column-blocked wherever the layout fits shared memory.
+                               each (CTA, column block) holds at least 1024 entries on average, else
+                               sliced ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL,
+                               TMA-staged stream; 3: column-blocked wherever the layout fits shared
+                               memory.
                                The block team always uses sliced ELL. */
     int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
                                after this many iterations is abandoned for the cold start */
@@ -137,6 +138,8 @@ typedef struct {
                               eigensolves (SCS_MIXED with PSD cones) */
     int32_t threads_per_block; /* launch shape used (batches: chosen by the autotuner unless set) */
     int32_t warm_fallback_taken; /* 1 if the warm start was abandoned for the cold start */
+    double kkt_fp32;        /* max(pr, dr, gap) of the FP32 phase's last termination test, evaluated
+                               on FP32 data (SCS_MIXED; 0 otherwise) */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
@@ -252,7 +255,12 @@ int scs_batch_setup(int32_t B, const scs_data *const *data, const scs_cone *cons
 /* x[i], y[i], s[i] (host pointers; any may be NULL, as may the arrays)
  * receive instance i's result as in scs_solve; infos may be NULL or hold B
  * entries.  Results are gathered on the device and copied back in one
- * transfer. */
+ * transfer.  The device work of a solve (both precision phases, the hand-
+ * over, the packing and the copies) is captured once into a CUDA graph on a
+ * stream the batch owns and replayed by one graph launch per solve, ordered
+ * after the work already queued on cuda_stream (captured again when the
+ * warm-start mode changes); if capture is unavailable it is enqueued on
+ * cuda_stream directly. */
 int scs_batch_solve(scs_batch *batch, double *const *x, double *const *y, double *const *s,
                     scs_info *infos);
 void scs_batch_finish(scs_batch *batch);

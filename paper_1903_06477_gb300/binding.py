@@ -56,6 +56,7 @@ class Info(C.Structure):
         ("err_vs_fp64", C.c_double), ("iters_fp32", C.c_int32), ("device_error", C.c_int32),
         ("kernel_s", C.c_double * 2), ("mat_passes", C.c_int64 * 2), ("cg_iters_fp32", C.c_int64),
         ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32), ("warm_fallback_taken", C.c_int32),
+        ("kkt_fp32", C.c_double),
     ]
 
     def as_dict(self):

@@ -382,13 +382,35 @@ __device__ __forceinline__ void cb_segment(int nw, int H, unsigned mt_off, unsig
         const int t1 = st[s + 1];
         int t = st[s];
         T a0 = 0, a1 = 0;
-        for (; t + 2 <= t1; t += 2) {
-            const int c0 = scol[t * 32 + lane], c1 = scol[t * 32 + 32 + lane];
-            const T v0 = sval[t * 32 + lane], v1 = sval[t * 32 + 32 + lane];
-            a0 = fmaT(v0, xs[c0], a0);
-            a1 = fmaT(v1, xs[c1], a1);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: four steps per trip, the tail predicated (offset 0, value 0)
+            T a2 = 0, a3 = 0;
+            for (; t < t1; t += 4) {
+                const bool o1 = t + 1 < t1, o2 = t + 2 < t1, o3 = t + 3 < t1;
+                const int c0 = scol[t * 32 + lane];
+                const int c1 = o1 ? (int)scol[t * 32 + 32 + lane] : 0;
+                const int c2 = o2 ? (int)scol[t * 32 + 64 + lane] : 0;
+                const int c3 = o3 ? (int)scol[t * 32 + 96 + lane] : 0;
+                const T v0 = sval[t * 32 + lane];
+                const T v1 = o1 ? sval[t * 32 + 32 + lane] : T(0);
+                const T v2 = o2 ? sval[t * 32 + 64 + lane] : T(0);
+                const T v3 = o3 ? sval[t * 32 + 96 + lane] : T(0);
+                a0 = fmaT(v0, xs[c0], a0);
+                a1 = fmaT(v1, xs[c1], a1);
+                a2 = fmaT(v2, xs[c2], a2);
+                a3 = fmaT(v3, xs[c3], a3);
+            }
+            a0 += a2;
+            a1 += a3;
+        } else {
+            for (; t + 2 <= t1; t += 2) {
+                const int c0 = scol[t * 32 + lane], c1 = scol[t * 32 + 32 + lane];
+                const T v0 = sval[t * 32 + lane], v1 = sval[t * 32 + 32 + lane];
+                a0 = fmaT(v0, xs[c0], a0);
+                a1 = fmaT(v1, xs[c1], a1);
+            }
+            if (t < t1) a0 = fmaT(sval[t * 32 + lane], xs[scol[t * 32 + lane]], a0);
         }
-        if (t < t1) a0 = fmaT(sval[t * 32 + lane], xs[scol[t * 32 + lane]], a0);
         T a = a0 + a1;
         for (int o = H; o < 32; o <<= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
         if (lane < H) {

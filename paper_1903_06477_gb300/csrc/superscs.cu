@@ -1184,6 +1184,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
             info->warm_fallback_taken |= st32.fallback;
             info->iters += st32.iters;
             info->iters_fp32 = st32.iters;
+            info->kkt_fp32 = std::max(st32.pr, std::max(st32.dr, st32.gap));
             info->k0 += st32.k0;
             info->k1 += st32.k1;
             info->k2 += st32.k2;
@@ -1196,9 +1197,11 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         info->threads_per_block = w->D.threads;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w->ev[0], w->ev[1]) == cudaSuccess) info->kernel_s[0] = ms * 1e-3;
+        cudaGetLastError();
         info->mat_passes[0] = st.mat_passes;
         if (w->has32) {
             if (cudaEventElapsedTime(&ms, w->ev[2], w->ev[3]) == cudaSuccess) info->kernel_s[1] = ms * 1e-3;
+            cudaGetLastError();  // a failed timing query must not surface in a later error check
             info->mat_passes[1] = st32.mat_passes;
             info->cg_iters_fp32 = st32.cg_iters;
             info->psd_resid_fp32 = st32.psd_resid;
@@ -1379,6 +1382,11 @@ struct scs_batch {
     std::vector<int> order;  // queue position -> instance
     scs_settings S;
     cudaStream_t stream = nullptr;
+    // the device work of one batch solve, captured once and replayed
+    cudaStream_t gstream = nullptr;   // capture stream (the caller's stream cannot be captured when it is the legacy default)
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gev = nullptr;        // orders the graph after the caller's stream
+    int graph_warm = -1;              // use_warm the graph was captured with
     char* arena = nullptr;
     int threads = 256, grid = 1, sms = 1;
     bool autotuned = false;
@@ -1693,6 +1701,9 @@ extern "C" int scs_batch_set_warm(scs_batch* b, const double* const* u)
 extern "C" void scs_batch_finish(scs_batch* b)
 {
     if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->gev) cudaEventDestroy(b->gev);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->hpacked) cudaFreeHost(b->hpacked);
@@ -1701,21 +1712,26 @@ extern "C" void scs_batch_finish(scs_batch* b)
     delete b;
 }
 
-extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y, double* const* s, scs_info* infos)
+// The device work of one batch solve, enqueued on st: FP32 phase (SCS_MIXED),
+// hand-over, FP64 phase, packing of the outputs, copies of outputs and
+// states to the pinned host staging buffers.  No synchronisation, so it can
+// be captured in a CUDA graph.
+static int batch_enqueue(scs_batch* b, cudaStream_t st, int g32, int g64, bool capturing)
 {
-    if (!b) { set_err(g_err, "batch is NULL"); return SCS_EINVAL; }
-    const double t0 = now_s();
     const int B = b->B;
-    float ms32 = 0.f, ms64 = 0.f;
+    // timing events: inside a capture they must be external record nodes so
+    // they can be read after the graph runs
+    auto rec = [&](cudaEvent_t e) {
+        return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+    };
     if (b->has32) {
         DevSettings S32 = batch_settings<float>(b, true);
         S32.use_warm = b->use_warm ? 1 : 0;
-        const int g32 = occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B);
-        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
-        CU(cudaEventRecord(b->ev[2], b->stream), b->err);
-        CU(launch_block<float>(g32, b->threads, b->dyn32, b->stream, b->d32, B, b->queue, S32, MODE_SOLVE), b->err);
-        CU(cudaEventRecord(b->ev[3], b->stream), b->err);
-        CU(launch_batch_handoff(b->d32, b->d64, B, b->stream), b->err);
+        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), st), b->err);
+        CU(rec(b->ev[2]), b->err);
+        CU(launch_block<float>(g32, b->threads, b->dyn32, st, b->d32, B, b->queue, S32, MODE_SOLVE), b->err);
+        CU(rec(b->ev[3]), b->err);
+        CU(launch_batch_handoff(b->d32, b->d64, B, st), b->err);
     }
     DevSettings S = batch_settings<double>(b, false);
     if (b->has32) {
@@ -1725,19 +1741,81 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
     } else {
         S.use_warm = b->use_warm ? 1 : 0;
     }
+    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), st), b->err);
+    CU(rec(b->ev[0]), b->err);
+    CU(launch_block<double>(g64, b->threads, b->dyn64, st, b->d64, B, b->queue, S, MODE_SOLVE), b->err);
+    CU(rec(b->ev[1]), b->err);
+    CU(launch_batch_pack(b->d64, B, b->off, b->packed, st), b->err);
+    CU(cudaMemcpyAsync(b->hpacked, b->packed, sizeof(double) * b->packed_len, cudaMemcpyDeviceToHost, st), b->err);
+    CU(cudaMemcpyAsync(b->hst, b->st64, sizeof(DevState) * B, cudaMemcpyDeviceToHost, st), b->err);
+    if (b->has32) CU(cudaMemcpyAsync(b->hst + B, b->st32, sizeof(DevState) * B, cudaMemcpyDeviceToHost, st), b->err);
+    return SCS_OK;
+}
+
+// Capture batch_enqueue into a CUDA graph on the batch's private capture
+// stream (again whenever the warm-start mode changes, which changes the
+// kernels' parameters).  Returns non-zero if capture is unavailable; the
+// caller then enqueues directly.
+static int batch_graph(scs_batch* b, int g32, int g64)
+{
+    const int warm = b->use_warm ? 1 : 0;
+    if (b->gexec && b->graph_warm == warm) return SCS_OK;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if ((!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) ||
+        (!b->gev && cudaEventCreateWithFlags(&b->gev, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        return SCS_ECUDA;
+    }
+    if (cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SCS_ECUDA;
+    }
+    const int rc = batch_enqueue(b, b->gstream, g32, g64, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->gstream, &g);
+    if (rc || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return SCS_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        b->gexec = nullptr;
+        cudaGetLastError();
+        return SCS_ECUDA;
+    }
+    b->graph_warm = warm;
+    return SCS_OK;
+}
+
+extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y, double* const* s, scs_info* infos)
+{
+    if (!b) { set_err(g_err, "batch is NULL"); return SCS_EINVAL; }
+    const double t0 = now_s();
+    const int B = b->B;
+    float ms32 = 0.f, ms64 = 0.f;
+    const int g32 = b->has32 ? occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B) : 0;
     const int g64 = occupancy_grid(kblock_ptr<double>(), b->threads, b->dyn64, b->sms, B);
     b->grid = g64;
-    CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
-    CU(cudaEventRecord(b->ev[0], b->stream), b->err);
-    CU(launch_block<double>(g64, b->threads, b->dyn64, b->stream, b->d64, B, b->queue, S, MODE_SOLVE), b->err);
-    CU(cudaEventRecord(b->ev[1], b->stream), b->err);
-    CU(launch_batch_pack(b->d64, B, b->off, b->packed, b->stream), b->err);
-    CU(cudaMemcpyAsync(b->hpacked, b->packed, sizeof(double) * b->packed_len, cudaMemcpyDeviceToHost, b->stream), b->err);
-    CU(cudaMemcpyAsync(b->hst, b->st64, sizeof(DevState) * B, cudaMemcpyDeviceToHost, b->stream), b->err);
-    if (b->has32) CU(cudaMemcpyAsync(b->hst + B, b->st32, sizeof(DevState) * B, cudaMemcpyDeviceToHost, b->stream), b->err);
+    // One graph launch replays the whole batch solve.  The graph runs on the
+    // batch's capture stream, ordered after the caller's stream by an event.
+    if (batch_graph(b, g32, g64) == SCS_OK) {
+        CU(cudaEventRecord(b->gev, b->stream), b->err);
+        CU(cudaStreamWaitEvent(b->gstream, b->gev, 0), b->err);
+        CU(cudaGraphLaunch(b->gexec, b->gstream), b->err);
+        CU(cudaStreamSynchronize(b->gstream), b->err);
+    } else {
+        int rc = batch_enqueue(b, b->stream, g32, g64, false);
+        if (rc) return rc;
+    }
     CU(cudaStreamSynchronize(b->stream), b->err);
-    cudaEventElapsedTime(&ms64, b->ev[0], b->ev[1]);
-    if (b->has32) cudaEventElapsedTime(&ms32, b->ev[2], b->ev[3]);
+    if (cudaEventElapsedTime(&ms64, b->ev[0], b->ev[1]) != cudaSuccess) ms64 = 0.f;
+    if (b->has32 && cudaEventElapsedTime(&ms32, b->ev[2], b->ev[3]) != cudaSuccess) ms32 = 0.f;
+    cudaGetLastError();  // a failed timing query must not surface in a later error check
     for (int qi = 0; qi < B; ++qi) {
         const int i = b->order[qi];
         const HostProb& h = b->H[i];
@@ -1760,6 +1838,7 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
                 info->warm_fallback_taken |= t.fallback;
                 info->iters += t.iters;
                 info->iters_fp32 = t.iters;
+                info->kkt_fp32 = std::max(t.pr, std::max(t.dr, t.gap));
                 info->k0 += t.k0;
                 info->k1 += t.k1;
                 info->k2 += t.k2;
