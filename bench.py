@@ -33,26 +33,28 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # solver launch, from one ncu capture (one pass per launch; summary and command
 # in profiles/k_grid_c2_fp32_phase_dram.md).  Valid only for the kernel sources
-# it was taken on (their digest) and for the same deterministic solve (same
-# outer and CG iteration counts); otherwise the roofline reports null.
+# it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
+# solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {
-    ("c2", "mixed"): {"bytes": 794206069504, "iters_fp32": 243, "cg_iters": 5801,
-                      "digest": "e6e78e824c3698e0e8e3231214a55fe8e19ed62ea855d67731873f880280ab0d"},
+    ("c2", "mixed"): {"bytes": 563422445568, "iters_fp32": 165, "cg_iters": 4254,
+                      "digest": "e9fd9e742640cc01fea934fb7836092f75d95ed24f6a2b9ef68f72205554b0de"},
 }
 
 
+# the sources that decide what the solver kernels do and which bytes they move:
+# the device code and the host builder of the column-blocked layout
+KERNEL_SOURCES = ("common.cuh", "team.cuh", "solver.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu",
+                  "cb_layout.h")
+
+
 def _src_digest():
-    """sha256 over the CUDA sources and public headers (sorted by path)."""
-    import glob
+    """sha256 over KERNEL_SOURCES (in that order)."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1903_06477_gb300", "csrc", "*"))
-                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
-    for f in files:
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.relpath(f, ROOT).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1903_06477_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 

@@ -229,6 +229,20 @@ int scs_apply_T(scs_work *work, const double *u, double *Tu, double *Ru);
 int scs_spmv(scs_work *work, int32_t precision, int32_t op, const double *in, const double *in2, double *out,
              double *out2);
 
+/* Host-only diagnostic of the column-blocked layout the grid team uses for
+ * large matrices (no counterpart in the paper; no GPU needed): builds the
+ * layout of the rows x cols CSR matrix (Ap, Ai, Ax) for `ctas` CTAs of
+ * `compute_warps` compute warps, elem_bytes 4 (FP32 copy) or 8 (FP64),
+ * `vectors` 1 or 2 multiplied vectors, smem_bytes of dynamic shared memory,
+ * checks its invariants, and replays y = A x (x: cols, y: rows, host) the way
+ * the device loop walks the layout, in FP64.  stats[8] (host): [0] violated
+ * invariants, [1] column blocks (0: the layout does not fit), [2] block
+ * width, [3] lanes per row, [4] stored entries, [5] dynamic shared memory,
+ * [6] ring stages, [7] metadata words per segment.  SCS_EINVAL on bad input. */
+int scs_cb_layout_check(int32_t rows, int32_t cols, const int64_t *Ap, const int32_t *Ai, const double *Ax,
+                        int32_t ctas, int32_t compute_warps, int32_t elem_bytes, int32_t vectors,
+                        int64_t smem_bytes, const double *x, double *y, int64_t *stats);
+
 /* Device-side timing (globaltimer between team barriers, inside one launch)
  * of the solver's building blocks on this problem, for roofline measurement:
  * ns[0] one product with A, ns[1] one with A^T, ns[2] one team barrier,

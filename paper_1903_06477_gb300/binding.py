@@ -85,6 +85,9 @@ _SIGS = [
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("scs_spmv", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_cb_layout_check", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     ("scs_residuals", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_residuals_noalloc", C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 10),
     ("scs_finish", None, [C.c_void_p]),
@@ -278,6 +281,23 @@ class Work:
         Tu, Ru = np.empty(self.N), np.empty(self.N)
         _check(lib().scs_apply_T(self.h, _ptr(u), _ptr(Tu), _ptr(Ru)), self.h)
         return Tu, Ru
+
+
+def cb_layout_check(A, x, ctas=152, compute_warps=15, elem_bytes=4, vectors=1, smem_bytes=209536):
+    """Host-only check of the column-blocked layout of the CSR matrix A (see
+    scs_cb_layout_check): returns (y = A x replayed through the layout,
+    stats dict)."""
+    A = A.tocsr()
+    Ap = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    Ai = np.ascontiguousarray(A.indices, dtype=np.int32)
+    Ax = np.ascontiguousarray(A.data, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(A.shape[0])
+    st = np.zeros(8, dtype=np.int64)
+    _check(lib().scs_cb_layout_check(A.shape[0], A.shape[1], _ptr(Ap), _ptr(Ai), _ptr(Ax), ctas, compute_warps,
+                                     elem_bytes, vectors, smem_bytes, _ptr(x), _ptr(y), _ptr(st)))
+    keys = ("violations", "column_blocks", "block_width", "lanes", "entries", "smem_bytes", "stages", "meta_words")
+    return y, dict(zip(keys, st.tolist()))
 
 
 class Batch:

@@ -1,0 +1,350 @@
+// cb_layout.h -- host-side builder of the column-blocked sparse layout the
+// grid team uses for large matrices (device side: Cblk, cb_spmv in
+// solver.cuh).  Host code only; included by superscs.cu.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <numeric>
+#include <vector>
+
+// One column-blocked copy of a matrix in one bulk precision (esize bytes per
+// value); field meanings as in Cblk.
+struct CbLayout {
+    int ncb = 0, cw = 0, cols = 0, nw = 0, V = 1, acc_rows = 0, ms = 0, S = 0, stage_off = 0, stage_bytes = 0,
+        off_x = 0, off_col = 0, off_val = 0, esize = 8;
+    std::vector<int> rbnd, meta;
+    std::vector<uint16_t> col;
+    std::vector<double> val;
+    size_t dyn() const { return ncb ? (size_t)stage_off + (size_t)S * stage_bytes : 0; }
+};
+
+// ---------------------------------------------------------------------------
+// column-blocked layout (grid team)
+// ---------------------------------------------------------------------------
+
+// contiguous row ranges for G CTAs, balanced on (entries + 2) per row
+static std::vector<int> cb_row_bounds(int rows, const std::vector<int>& rp, int G)
+{
+    std::vector<int> rb(G + 1, 0);
+    const long long total = (long long)rp[rows] + 2LL * rows;
+    int r = 0;
+    for (int b = 1; b < G; ++b) {
+        const long long target = total * b / G;
+        while (r < rows && (long long)rp[r] + 2LL * r < target) ++r;
+        rb[b] = r;
+    }
+    rb[G] = rows;
+    return rb;
+}
+
+// The rows of CTA range [r0, r0 + R) bucketed by column block: cnt[k * R + lr]
+// entries of local row lr in block k, their CSR indices in
+// epos[start[k * R + lr] ...].
+struct CbBuckets {
+    std::vector<int> cnt, start, epos, fill;
+    void build(int r0, int R, int ncb, int cw, const std::vector<int>& rp, const std::vector<int>& ci)
+    {
+        cnt.assign((size_t)ncb * R, 0);
+        for (int lr = 0; lr < R; ++lr)
+            for (int e = rp[r0 + lr]; e < rp[r0 + lr + 1]; ++e) cnt[(size_t)(ci[e] / cw) * R + lr]++;
+        start.assign((size_t)ncb * R + 1, 0);
+        for (size_t i = 0; i < (size_t)ncb * R; ++i) start[i + 1] = start[i] + cnt[i];
+        epos.resize(start.back());
+        fill.assign(start.begin(), start.end() - 1);
+        for (int lr = 0; lr < R; ++lr)
+            for (int e = rp[r0 + lr]; e < rp[r0 + lr + 1]; ++e) epos[fill[(size_t)(ci[e] / cw) * R + lr]++] = e;
+    }
+    // rows of block k with entries, by count descending (ties: row order)
+    void sorted_rows(int k, int R, std::vector<int>& out) const
+    {
+        out.clear();
+        for (int lr = 0; lr < R; ++lr)
+            if (cnt[(size_t)k * R + lr] > 0) out.push_back(lr);
+        std::stable_sort(out.begin(), out.end(),
+                         [&](int a, int b) { return cnt[(size_t)k * R + a] > cnt[(size_t)k * R + b]; });
+    }
+};
+
+// Deal slices (work = steps) to nw warps, largest first to the least-loaded
+// warp.  Returns the warp of each slice; loads accumulate 2 * steps + 3.
+static void cb_deal(const std::vector<int>& steps, int nw, std::vector<int>& warp, std::vector<long long>& load)
+{
+    load.assign(nw, 0);
+    warp.resize(steps.size());
+    for (size_t s = 0; s < steps.size(); ++s) {
+        int best = 0;
+        for (int w = 1; w < nw; ++w)
+            if (load[w] < load[best]) best = w;
+        warp[s] = best;
+        load[best] += 2LL * steps[s] + 3;
+    }
+}
+
+static void cb_slice_steps(const CbBuckets& bk, int k, int R, const std::vector<int>& rows, int V,
+                           std::vector<int>& steps)
+{
+    const int H = 32 / V;
+    const int ns = ((int)rows.size() + H - 1) / H;
+    steps.resize(ns);
+    for (int sl = 0; sl < ns; ++sl) steps[sl] = (bk.cnt[(size_t)k * R + rows[(size_t)sl * H]] + V - 1) / V;
+}
+
+// Lanes per row for the column-blocked layout: the V in {1, 2, 4, 8} with the
+// least estimated time on a sample of CTAs -- per segment, the busiest
+// warp's load plus eight times the mean load.  Segments are computed from
+// shared memory while the matrix stream is the bound, so padding (the mean)
+// weighs more than imbalance.
+static int cb_pick_lanes(const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<int>& rb, int nw,
+                         int ncb, int cw)
+{
+    const int G = (int)rb.size() - 1;
+    const int stride = std::max(1, G / 16);
+    long long cost[4] = {0, 0, 0, 0};
+    CbBuckets bk;
+    std::vector<int> rows, steps, warp;
+    std::vector<long long> load;
+    for (int b = 0; b < G; b += stride) {
+        const int r0 = rb[b], R = rb[b + 1] - r0;
+        bk.build(r0, R, ncb, cw, rp, ci);
+        for (int k = 0; k < ncb; ++k) {
+            bk.sorted_rows(k, R, rows);
+            for (int vi = 0; vi < 4; ++vi) {
+                cb_slice_steps(bk, k, R, rows, 1 << vi, steps);
+                cb_deal(steps, nw, warp, load);
+                long long mx = 0, sum = 0;
+                for (long long l : load) {
+                    mx = std::max(mx, l);
+                    sum += l;
+                }
+                cost[vi] += mx + 8 * sum / nw;
+            }
+        }
+    }
+    int best = 0;
+    for (int vi = 1; vi < 4; ++vi)
+        if (cost[vi] < cost[best]) best = vi;
+    return 1 << best;
+}
+
+// metadata words per segment for ns slices of H rows (layout of Cblk)
+static int cb_meta_words(int nw, int ns, int H)
+{
+    return 5 + (nw + 1) + (ns + 1) + (ns * H + 1) / 2;
+}
+
+// Build the column-blocked layout of a CSR matrix (rows x cols) for the row
+// ranges rb, nw compute warps per CTA, blocks of cw columns and a ring of S
+// stages.
+// Returns the largest segment (entries) or -1 if the layout is too large.
+static long long build_cb(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
+                          const std::vector<double>& vx, const std::vector<int>& rb, int nw, int cw, int S,
+                          CbLayout& C)
+{
+    (void)rows;
+    const int G = (int)rb.size() - 1;
+    const int ncb = (cols + cw - 1) / cw;
+    const int V = cb_pick_lanes(rp, ci, rb, nw, ncb, cw);
+    const int H = 32 / V;
+    C.ncb = ncb;
+    C.cw = cw;
+    C.cols = cols;
+    C.nw = nw;
+    C.V = V;
+    C.S = S;
+    C.rbnd = rb;
+    C.col.clear();
+    C.val.clear();
+    struct Seg {
+        long long e0, e1;
+        std::vector<int> words;  // [4] onwards of the segment's metadata
+    };
+    std::vector<Seg> segs((size_t)G * ncb);
+    CbBuckets bk;
+    std::vector<int> rows_k, steps, warp, order;
+    std::vector<long long> load;
+    int ms = 4;
+    long long max_e = 0;
+    // Entry placement inside a slice.  Every lane of a step gathers one
+    // element of the vector slice from shared memory; lanes whose elements
+    // share a bank are served one after another.  The row of each lane is
+    // fixed, but which of its entries goes to which step is free, so each
+    // step takes, lane by lane, the row's remaining entry in the least-used
+    // bank (FP32: column mod 32 over the warp; FP64: column mod 16 within each
+    // half-warp, which is served separately).  Padding lanes point at a
+    // column in a free bank (value 0).  A staged slice starts at a shift that
+    // is the same for all its elements, so distinct banks stay distinct.
+    const int nbank = C.esize == 8 ? 16 : 32;
+    std::vector<std::vector<int>> rem(32);
+    auto place_slice = [&](size_t e0, int nsteps, int k) {
+        const int len_k = std::min(cw, cols - k * cw);
+        for (int t = 0; t < nsteps; ++t) {
+            int cnt[2][32] = {};
+            bool pad[32] = {};
+            for (int q = 0; q < V; ++q)
+                for (int rr = 0; rr < H; ++rr) {
+                    const int lane = q * H + rr, half = nbank == 16 ? lane >> 4 : 0;
+                    std::vector<int>& rl = rem[rr];
+                    if (rl.empty()) {
+                        pad[lane] = true;
+                        continue;
+                    }
+                    size_t best = 0;
+                    int bc = 1 << 30;
+                    for (size_t i = 0; i < rl.size(); ++i) {
+                        const int c = cnt[half][(ci[rl[i]] - k * cw) % nbank];
+                        if (c < bc) {
+                            bc = c;
+                            best = i;
+                        }
+                    }
+                    const int e = rl[best];
+                    rl[best] = rl.back();
+                    rl.pop_back();
+                    const int lc = ci[e] - k * cw;
+                    cnt[half][lc % nbank]++;
+                    const size_t idx = e0 + (size_t)t * 32 + lane;
+                    C.col[idx] = (uint16_t)lc;
+                    C.val[idx] = vx[e];
+                }
+            for (int lane = 0; lane < 32; ++lane) {
+                if (!pad[lane]) continue;
+                const int half = nbank == 16 ? lane >> 4 : 0;
+                int bb = 0;
+                for (int b2 = 1; b2 < nbank && b2 < len_k; ++b2)
+                    if (cnt[half][b2] < cnt[half][bb]) bb = b2;
+                cnt[half][bb]++;
+                const size_t idx = e0 + (size_t)t * 32 + lane;
+                C.col[idx] = (uint16_t)bb;
+                C.val[idx] = 0.0;
+            }
+        }
+    };
+    for (int b = 0; b < G; ++b) {
+        const int r0 = rb[b], R = rb[b + 1] - r0;
+        bk.build(r0, R, ncb, cw, rp, ci);
+        for (int k = 0; k < ncb; ++k) {
+            bk.sorted_rows(k, R, rows_k);
+            cb_slice_steps(bk, k, R, rows_k, V, steps);
+            cb_deal(steps, nw, warp, load);
+            const int ns = (int)steps.size();
+            order.resize(ns);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return warp[a] < warp[c]; });
+            Seg& sg = segs[(size_t)b * ncb + k];
+            sg.e0 = (long long)C.col.size();
+            std::vector<int> wstart(nw + 1, 0), sstart(ns + 1, 0);
+            std::vector<uint16_t> srow((size_t)ns * H, 0xFFFF);
+            int w = 0, t = 0;
+            for (int oi = 0; oi < ns; ++oi) {
+                const int sl = order[oi];
+                while (w <= warp[sl]) wstart[w++] = oi;
+                sstart[oi] = t;
+                const size_t e0 = (size_t)C.col.size();
+                const size_t size = (size_t)steps[sl] * 32;
+                C.col.resize(e0 + size, 0);
+                C.val.resize(e0 + size, 0.0);
+                for (int rr = 0; rr < H; ++rr) {
+                    const size_t pos = (size_t)sl * H + rr;
+                    rem[rr].clear();
+                    if (pos >= rows_k.size()) continue;
+                    const int lr = rows_k[pos];
+                    srow[(size_t)oi * H + rr] = (uint16_t)lr;
+                    const size_t q0 = (size_t)bk.start[(size_t)k * R + lr];
+                    const int len = bk.cnt[(size_t)k * R + lr];
+                    for (int j = 0; j < len; ++j) rem[rr].push_back(bk.epos[q0 + j]);
+                }
+                place_slice(e0, steps[sl], k);
+                t += steps[sl];
+            }
+            sstart[ns] = t;
+            while (w <= nw) wstart[w++] = ns;
+            sg.e1 = (long long)C.col.size();
+            max_e = std::max(max_e, sg.e1 - sg.e0);
+            sg.words.clear();
+            sg.words.push_back(ns);
+            sg.words.insert(sg.words.end(), wstart.begin(), wstart.end());
+            sg.words.insert(sg.words.end(), sstart.begin(), sstart.end());
+            for (int i = 0; i < ns * H; i += 2) {
+                const unsigned lo = srow[i], hi = i + 1 < ns * H ? srow[i + 1] : 0xFFFFu;
+                sg.words.push_back((int)(lo | (hi << 16)));
+            }
+            ms = std::max(ms, 4 + (int)sg.words.size());
+        }
+    }
+    if (C.col.size() >= (1ull << 31)) return -1;
+    ms = (ms + 3) & ~3;
+    C.ms = ms;
+    C.meta.assign((size_t)G * ncb * ms, 0);
+    for (int b = 0; b < G; ++b)
+        for (int k = 0; k < ncb; ++k) {
+            const Seg& sg = segs[(size_t)b * ncb + k];
+            int* m = C.meta.data() + ((size_t)b * ncb + k) * ms;
+            m[0] = (int)sg.e0;
+            m[1] = (int)sg.e1;
+            const int k2 = (k + S) % ncb;  // visited S segments later (visits wrap around)
+            m[2] = (int)segs[(size_t)b * ncb + k2].e0;
+            m[3] = (int)segs[(size_t)b * ncb + k2].e1;
+            std::copy(sg.words.begin(), sg.words.end(), m + 4);
+        }
+    return max_e;
+}
+
+// Plan (and build) the column-blocked copy of one matrix in one precision:
+// nv vectors per product, dyn_max bytes of dynamic shared memory laid out as
+// [2 nv partial-sum arrays | S stages of (metadata | vector slice | col | val)].
+// The block width is sized so a stage holds one segment; a segment that
+// turns out larger shrinks the width and the layout is rebuilt.  Leaves C
+// empty (ncb = 0) where nothing fits or, unless forced, where the segments
+// would be too short to pay for their per-segment cost.
+static void plan_cb(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
+                    const std::vector<double>& vx, int G, int nw, int esize, int nv, size_t dyn_max, bool force,
+                    CbLayout& C)
+{
+    constexpr int S = 3;
+    C = CbLayout();
+    C.esize = esize;
+    const std::vector<int> rb = cb_row_bounds(rows, rp, G);
+    int acc_rows = 0;
+    long long nnz_cta = 0;
+    for (int b = 0; b < G; ++b) {
+        acc_rows = std::max(acc_rows, rb[b + 1] - rb[b]);
+        nnz_cta = std::max<long long>(nnz_cta, rp[rb[b + 1]] - rp[rb[b]]);
+    }
+    if (acc_rows >= 0xFFFF || nw < 1) return;
+    const int E = 16 / esize;
+    // partial sums: two buffers (even / odd segments) per multiplied vector
+    const size_t acc_bytes = ((size_t)2 * nv * std::max(acc_rows, 1) * esize + 15) & ~size_t(15);
+    if (acc_bytes + 4096 > dyn_max) return;
+    const long long stage_avail = (long long)((dyn_max - acc_bytes) / S) & ~15LL;
+    // metadata bound: at most ceil(acc_rows / H) slices, H >= 4
+    const int ms_cap = (cb_meta_words(nw, (acc_rows + 3) / 4, 4) + 16 + 3) & ~3;
+    const double per_col = esize + 1.15 * (2 + esize) * (double)nnz_cta / std::max(cols, 1);
+    long long budget = stage_avail - 4LL * ms_cap - 64 - 2LL * E * esize;
+    int cw = (int)std::min<double>(65536.0, budget / per_col) & ~3;
+    const long long nnz = rp[rows];
+    for (int attempt = 0; attempt < 8 && cw >= 64; ++attempt) {
+        const int ncb = (cols + cw - 1) / cw;
+        const int cw2 = ((cols + ncb - 1) / ncb + 3) & ~3;
+        if (!force && nnz < 1024LL * G * ncb) return;
+        const long long max_e = build_cb(rows, cols, rp, ci, vx, rb, nw, cw2, S, C);
+        if (max_e < 0) break;
+        const long long off_x = 4LL * C.ms;
+        const long long off_col = off_x + (((long long)(cw2 + 2 * E) * esize + 15) & ~15LL);
+        const long long off_val = off_col + ((2 * max_e + 15) & ~15LL);
+        const long long bytes = off_val + ((max_e * esize + 15) & ~15LL);
+        if (bytes <= stage_avail) {
+            C.esize = esize;
+            C.acc_rows = acc_rows;
+            C.stage_off = (int)acc_bytes;
+            C.stage_bytes = (int)bytes;
+            C.off_x = (int)off_x;
+            C.off_col = (int)off_col;
+            C.off_val = (int)off_val;
+            return;
+        }
+        cw = (int)((double)cw2 * 0.95 * (double)stage_avail / (double)bytes) & ~3;
+    }
+    C = CbLayout();
+}
+
