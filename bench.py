@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
 # solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {
-    ("c2", "mixed"): {"bytes": 563422445568, "iters_fp32": 165, "cg_iters": 4254,
-                      "digest": "e9fd9e742640cc01fea934fb7836092f75d95ed24f6a2b9ef68f72205554b0de"},
+    ("c2", "mixed"): {"bytes": 426058066432, "iters_fp32": 113, "cg_iters": 4139,
+                      "digest": "8c1f202d4df42427f56174b13714db292b52c0e818bce6e34e2b80bfd63c0047"},
 }
 
 

@@ -301,7 +301,10 @@ static void plan_cb(int rows, int cols, const std::vector<int>& rp, const std::v
                     const std::vector<double>& vx, int G, int nw, int esize, int nv, size_t dyn_max, bool force,
                     CbLayout& C)
 {
-    constexpr int S = 3;
+    // two stages of the largest size: measured against three and four, the
+    // per-segment cost (metadata, waits, one flush per row and segment)
+    // outweighs the deeper look-ahead
+    constexpr int S = 2;
     C = CbLayout();
     C.esize = esize;
     const std::vector<int> rb = cb_row_bounds(rows, rp, G);
