@@ -86,7 +86,7 @@ def _check_products(work, prob, precision, u, seed):
 
 
 @pytest.mark.parametrize("name", list(PROBS))
-@pytest.mark.parametrize("path", [3, 1])
+@pytest.mark.parametrize("path", [3, 1, 2])  # column-blocked, sliced ELL, sliced ELL with a TMA-staged stream
 def test_products_match_definition(name, path):
     prob = PROBS[name]
     work = B.Work(prob, team=B.TEAM_GRID, precision=B.MIXED, spmv_path=path)
