@@ -21,9 +21,12 @@
  * Cone rows of s are ordered [ f zero | l orthant | q SOCs... | s PSDs... ].
  * A is CSR with m rows: Ap[m+1] (int64), Ai[nnz] (int32), Ax[nnz].
  *
- * Parity status of each function is stated in the tests that pin it; the
- * exact iterate path of Algorithm 1 is "parity unpinned" (only its end result,
- * its KM limit and its branch invariants are pinned).
+ * Parity status of each function is stated in the tests that pin it.  The
+ * iterate path of Algorithm 1 is pinned step by step where every step takes
+ * the same branch: all K0 (Anderson acceleration in Walker and Ni's form, or
+ * a dense safeguarded Broyden iteration) and all K2 (the KM iteration).  Paths
+ * that mix K1, K2 and backtracking are "parity unpinned": only their end
+ * results and branch invariants are pinned.
  */
 #ifndef SUPERSCS_ORACLE_H
 #define SUPERSCS_ORACLE_H

@@ -3,6 +3,13 @@
 - KM limit: with d = 0 and K0 off, every step is K2 with rho = ||Ru||^2, i.e.
   the Krasnosel'skii-Mann iteration u+ = (1-lambda) u + lambda T u (Eq. km);
   compared with an independent 5-line loop over T.
+- K0 path: with c0 so large that every step is K0, Algorithm 1 is the
+  undamped quasi-Newton iteration u+ = u + d on R = I - T.  With Anderson
+  directions that is Anderson acceleration of the fixed-point map T in
+  Walker and Ni's form (window mem, least squares by numpy.linalg.lstsq);
+  with restarted Broyden it is the Broyden iteration with Powell's theta
+  safeguard carried out on a dense inverse-Jacobian estimate H.  Both are
+  compared with the oracle's iterate after each of a dozen steps.
 - Branch invariants: K1 steps satisfy ||Ru+|| <= c1 ||Ru||; K2 steps are
   Fejer monotone with respect to the planted fixed point.
 - End results: planted optima (objective c^T x*), LASSO against an independent
@@ -31,6 +38,85 @@ def test_km_limit():
             Tu, _ = ref.apply_T(u)
             u = (1 - lam) * u + lam * Tu
         np.testing.assert_allclose(out["u"], u, atol=1e-9 * (1 + np.abs(u).max()))
+
+
+def _k0_oracle_path(prob, direction, mem, iters, **extra):
+    """The oracle's iterate after 1, 2, ..., iters steps of Algorithm 1 with
+    every step forced to K0 (c0 = 1e300)."""
+    path = []
+    for k in range(1, iters + 1):
+        orc = O.Oracle(prob, direction=direction, mem=mem, c0=1e300, max_iters=k, eps=1e-30,
+                       cg_rtol=1e-15, cg_max=10000, **extra)
+        out = orc.solve()
+        assert out["info"].k0 == k and out["info"].k1 == 0 and out["info"].k2 == 0
+        path.append(out["u"])
+        orc.close()
+    return path
+
+
+@pytest.mark.parametrize("mem", [1, 3, 5])
+def test_k0_path_is_anderson_acceleration(mem):
+    prob = W.planted(seed=21, n=40, l=30, soc=[4, 4], f=2, nnz=500)
+    iters = 12
+    path = _k0_oracle_path(prob, O.DIR_AA, mem, iters, aa_reg=1e-15)
+    ref = O.Oracle(prob, cg_rtol=1e-15, cg_max=10000)
+    # Anderson acceleration (Walker and Ni) of g = T: f = g(u) - u = -Ru,
+    # u+ = g(u) - G gamma with gamma = argmin ||f - F gamma|| over the last
+    # mem differences F (of f) and G (of g)
+    u = np.zeros(ref.N)
+    u[-1] = 1.0
+    Tu, Ru = ref.apply_T(u)
+    dF, dG = [], []
+    for k in range(iters):
+        f, g = -Ru, Tu
+        if dF:
+            F = np.array(dF[-mem:]).T
+            G = np.array(dG[-mem:]).T
+            gamma = np.linalg.lstsq(F, f, rcond=None)[0]
+            u_new = g - G @ gamma
+        else:
+            u_new = g
+        Tn, Rn = ref.apply_T(u_new)
+        dF.append(-Rn - f)
+        dG.append(Tn - g)
+        u, Tu, Ru = u_new, Tn, Rn
+        scale = 1 + np.abs(u).max()
+        np.testing.assert_allclose(path[k], u, rtol=0, atol=1e-10 * scale, err_msg=f"step {k + 1}")
+
+
+@pytest.mark.parametrize("mem", [2, 4])
+def test_k0_path_is_safeguarded_broyden(mem):
+    prob = W.planted(seed=22, n=30, l=24, soc=[4], f=1, nnz=300)
+    iters, tb = 12, 0.1
+    path = _k0_oracle_path(prob, O.DIR_RB, mem, iters, thetabar=tb)
+    ref = O.Oracle(prob, cg_rtol=1e-15, cg_max=10000)
+    N = ref.N
+    u = np.zeros(N)
+    u[-1] = 1.0
+    _, Ru = ref.apply_T(u)
+    H, stored = np.eye(N), 0
+    for k in range(iters):
+        if k > 0:
+            # Broyden update of the inverse estimate with the pair (z, xi),
+            # xi~ = (1 - theta) B z + theta xi (Powell), H B = I
+            Hxi = H @ xi
+            gam = Hxi @ z / (z @ z)
+            th = 1.0 if abs(gam) >= tb else (1 - (1.0 if gam >= 0 else -1.0) * tb) / (1 - gam)
+            Hxi_t = (1 - th) * z + th * Hxi
+            Hn = H + np.outer(z - Hxi_t, z @ H) / (z @ Hxi_t)
+            d = -Hn @ Ru
+            if stored == mem:  # memory full: restart, the current pair is not kept
+                H, stored = np.eye(N), 0
+            else:
+                H, stored = Hn, stored + 1
+        else:
+            d = -Ru
+        u_new = u + d
+        _, Rn = ref.apply_T(u_new)
+        z, xi = d, Rn - Ru
+        u, Ru = u_new, Rn
+        scale = 1 + np.abs(u).max()
+        np.testing.assert_allclose(path[k], u, rtol=0, atol=1e-10 * scale, err_msg=f"step {k + 1}")
 
 
 @pytest.mark.parametrize("direction,mem", [(O.DIR_AA, 10), (O.DIR_RB, 10), (O.DIR_AA, 3)])
