@@ -120,22 +120,26 @@ def test_km_iterates_match_oracle():
         np.testing.assert_allclose(u, ref["u"], rtol=0, atol=1e-8 * (1 + np.abs(ref["u"]).max()))
 
 
+@pytest.mark.parametrize("branch", ["K0", "K1"])
 @pytest.mark.parametrize("direction,mem", [(B.DIR_AA, 3), (B.DIR_RB, 2)])
-def test_k0_iterates_match_oracle(direction, mem):
-    """c0 = 1e300: every step is K0, u+ = u + d with Anderson or restarted
-    Broyden directions (on the oracle side that path is pinned step by step
-    against textbook Anderson acceleration and a dense Broyden iteration);
-    after a dozen steps the GPU's iterate equals the oracle's to CG accuracy."""
+def test_k0_k1_iterates_match_oracle(direction, mem, branch):
+    """Every step forced to K0 (c0 = 1e300) or to K1 at alpha = 1 (c0 = 0,
+    c1 = 1e300): u+ = u + d with Anderson or restarted Broyden directions (on
+    the oracle side that path is pinned step by step against textbook
+    Anderson acceleration and a dense Broyden iteration); after a dozen steps
+    the GPU's iterate equals the oracle's to CG accuracy."""
     prob = PROBS["planted_mixed_cones"]
     iters = 12
-    kw = dict(direction=direction, mem=mem, c0=1e300, eps=1e-30, max_iters=iters, cg_rtol=1e-14, cg_max=5000)
+    forced = dict(c0=1e300) if branch == "K0" else dict(c0=0.0, c1=1e300)
+    kw = dict(direction=direction, mem=mem, eps=1e-30, max_iters=iters, cg_rtol=1e-14, cg_max=5000, **forced)
     okw = dict(kw, direction=O.DIR_AA if direction == B.DIR_AA else O.DIR_RB)
     ref = O.Oracle(prob, **okw).solve()
-    assert ref["info"].k0 == iters
+    key = "k0" if branch == "K0" else "k1"
+    assert getattr(ref["info"], key) == iters
     for team in TEAMS:
         work = B.Work(prob, team=team, **kw)
         _, _, _, info = work.solve()
-        assert info["k0"] == iters, info
+        assert info[key] == iters and info["backtracks"] == 0, info
         u = work.get_u()
         np.testing.assert_allclose(u, ref["u"], rtol=0, atol=1e-8 * (1 + np.abs(ref["u"]).max()))
 

@@ -9,7 +9,8 @@
   Walker and Ni's form (window mem, least squares by numpy.linalg.lstsq);
   with restarted Broyden it is the Broyden iteration with Powell's theta
   safeguard carried out on a dense inverse-Jacobian estimate H.  Both are
-  compared with the oracle's iterate after each of a dozen steps.
+  compared with the oracle's iterate after each of a dozen steps; the same
+  path forced through K1 at alpha = 1 (c0 = 0, c1 = 1e300) must match too.
 - Branch invariants: K1 steps satisfy ||Ru+|| <= c1 ||Ru||; K2 steps are
   Fejer monotone with respect to the planted fixed point.
 - End results: planted optima (objective c^T x*), LASSO against an independent
@@ -40,25 +41,30 @@ def test_km_limit():
         np.testing.assert_allclose(out["u"], u, atol=1e-9 * (1 + np.abs(u).max()))
 
 
-def _k0_oracle_path(prob, direction, mem, iters, **extra):
+def _k0_oracle_path(prob, direction, mem, iters, branch="K0", **extra):
     """The oracle's iterate after 1, 2, ..., iters steps of Algorithm 1 with
-    every step forced to K0 (c0 = 1e300)."""
+    every step forced to K0 (c0 = 1e300), or to K1 at alpha = 1 (c0 = 0,
+    c1 = 1e300: the safeguard ||Ru|| <= r_safe then holds at every step).
+    Both branches then take u+ = u + d and store the pair (d, Ru+ - Ru)."""
     path = []
+    forced = dict(c0=1e300) if branch == "K0" else dict(c0=0.0, c1=1e300)
     for k in range(1, iters + 1):
-        orc = O.Oracle(prob, direction=direction, mem=mem, c0=1e300, max_iters=k, eps=1e-30,
-                       cg_rtol=1e-15, cg_max=10000, **extra)
+        orc = O.Oracle(prob, direction=direction, mem=mem, max_iters=k, eps=1e-30,
+                       cg_rtol=1e-15, cg_max=10000, **forced, **extra)
         out = orc.solve()
-        assert out["info"].k0 == k and out["info"].k1 == 0 and out["info"].k2 == 0
+        info = out["info"]
+        assert (info.k0, info.k1, info.k2, info.backtracks) == ((k, 0, 0, 0) if branch == "K0" else (0, k, 0, 0))
         path.append(out["u"])
         orc.close()
     return path
 
 
+@pytest.mark.parametrize("branch", ["K0", "K1"])
 @pytest.mark.parametrize("mem", [1, 3, 5])
-def test_k0_path_is_anderson_acceleration(mem):
+def test_k0_path_is_anderson_acceleration(mem, branch):
     prob = W.planted(seed=21, n=40, l=30, soc=[4, 4], f=2, nnz=500)
     iters = 12
-    path = _k0_oracle_path(prob, O.DIR_AA, mem, iters, aa_reg=1e-15)
+    path = _k0_oracle_path(prob, O.DIR_AA, mem, iters, branch=branch, aa_reg=1e-15)
     ref = O.Oracle(prob, cg_rtol=1e-15, cg_max=10000)
     # Anderson acceleration (Walker and Ni) of g = T: f = g(u) - u = -Ru,
     # u+ = g(u) - G gamma with gamma = argmin ||f - F gamma|| over the last
@@ -84,11 +90,12 @@ def test_k0_path_is_anderson_acceleration(mem):
         np.testing.assert_allclose(path[k], u, rtol=0, atol=1e-10 * scale, err_msg=f"step {k + 1}")
 
 
+@pytest.mark.parametrize("branch", ["K0", "K1"])
 @pytest.mark.parametrize("mem", [2, 4])
-def test_k0_path_is_safeguarded_broyden(mem):
+def test_k0_path_is_safeguarded_broyden(mem, branch):
     prob = W.planted(seed=22, n=30, l=24, soc=[4], f=1, nnz=300)
     iters, tb = 12, 0.1
-    path = _k0_oracle_path(prob, O.DIR_RB, mem, iters, thetabar=tb)
+    path = _k0_oracle_path(prob, O.DIR_RB, mem, iters, branch=branch, thetabar=tb)
     ref = O.Oracle(prob, cg_rtol=1e-15, cg_max=10000)
     N = ref.N
     u = np.zeros(N)
