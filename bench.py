@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
 # solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {
-    ("c2", "mixed"): {"bytes": 426058066432, "iters_fp32": 113, "cg_iters": 4139,
-                      "digest": "8c1f202d4df42427f56174b13714db292b52c0e818bce6e34e2b80bfd63c0047"},
+    ("c2", "mixed"): {"bytes": 425705552128, "iters_fp32": 113, "cg_iters": 4139,
+                      "digest": "5ea3b0a25362c6a1cdfb9de4102c16f72342206e58ebfdec06cfa898cc008754"},
 }
 
 
@@ -424,6 +424,68 @@ def run_c5(args):
     return 0
 
 
+def run_gemm(args):
+    """Profiling aid for the warm-start network's GEMMs: both kernels
+    (m16n8k16 and tcgen05) on the products of the 2000-1024-1024-22004
+    network at batch 256 and a 4096^3 square, then a training step and a
+    forward pass with each kernel; CUDA-event times, one JSON line."""
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    shapes = [(256, 1024, 2000), (256, 1024, 1024), (256, 22004, 1024), (22004, 1024, 256), (256, 1024, 22004),
+              (1024, 2000, 256), (4096, 4096, 4096)]
+    st = torch.cuda.current_stream()
+    out = {"products": {}}
+    for (M, N, K) in shapes:
+        ld = (K + 7) // 8 * 8  # row strides a multiple of 8 elements (16 bytes)
+        A = torch.randn(M, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+        Bm = torch.randn(N, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+        row = {}
+        res = []
+        for impl, name in ((B.GEMM_MMA, "mma_m16n8k16"), (B.GEMM_TCGEN05, "tcgen05")):
+            ts = []
+            for r in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                C = B.gemm_nt(A, Bm, impl=impl)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res.append(C)
+            row[name + "_ms_incl_call"] = float(np.median(ts[2:]))
+        row["bitwise_equal"] = bool(torch.equal(res[0], res[1]))
+        out["products"][f"{M}x{N}x{K}"] = row
+    for impl, name in ((B.GEMM_MMA, "mma_m16n8k16"), (B.GEMM_TCGEN05, "tcgen05")):
+        net = B.MLP(2000, 1024, 22004, max_batch=256, seed=1, gemm=impl)
+        X = torch.randn(256, 2000, device="cuda", generator=g)
+        Y = torch.randn(256, 22004, device="cuda", generator=g)
+        net.fit_normalization(X, Y)
+        for _ in range(3):
+            net.train_step(X, Y, 1e-4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(10):
+            net.train_step(X, Y, 1e-4)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name + "_train_step_ms"] = e0.elapsed_time(e1) / 10
+        Yo = torch.empty(256, 22004, device="cuda")
+        for _ in range(3):
+            net.forward(X, Yo)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(20):
+            net.forward(X, Yo)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name + "_forward_ms"] = e0.elapsed_time(e1) / 20
+        net.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,9 +511,13 @@ def main():
     ap.add_argument("--products", type=int, default=0,
                     help="profiling aid: set up the workload, run this many sparse products (see --op) and exit")
     ap.add_argument("--op", default="a", choices=["a", "at"], help="product for --products: A x or A^T y")
+    ap.add_argument("--gemm", action="store_true",
+                    help="profiling aid: time the warm-start network's GEMM kernels (both) and exit")
     args = ap.parse_args()
     if args.products > 0:
         return run_products(args)
+    if args.gemm:
+        return run_gemm(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":

@@ -16,7 +16,9 @@
  *
  * Matrices are row-major, one sample per row.  Every pointer argument of
  * the per-batch calls is a device pointer.  All calls are queued on the
- * stream given at creation; the ones that return a loss synchronise it.
+ * stream given at creation; the ones that return a loss synchronise it and
+ * report (SCS_ECUDA) a tensor-core GEMM of an earlier call whose bounded
+ * wait expired.
  */
 #ifndef SUPERSCS_MLP_H
 #define SUPERSCS_MLP_H
@@ -60,6 +62,27 @@ int scs_mlp_get_params(scs_mlp *mlp, float *params);
 int scs_mlp_set_params(scs_mlp *mlp, const float *params);
 
 void scs_mlp_destroy(scs_mlp *mlp);
+
+/* GEMM kernels of the network.  SCS_MLP_GEMM_MMA: warp-level BF16 MMA
+ * (m16n8k16) from shared memory.  SCS_MLP_GEMM_TCGEN05: fifth-generation
+ * tensor cores (tcgen05.mma, accumulator in tensor memory), 128 x 128 tiles.
+ * Both compute C = A B^T in FP32 from BF16 operands; their results differ
+ * only in FP32 summation order. */
+#define SCS_MLP_GEMM_MMA 0
+#define SCS_MLP_GEMM_TCGEN05 1
+
+/* Choose the GEMM kernel of a network (default SCS_MLP_GEMM_MMA). */
+int scs_mlp_set_gemm(scs_mlp *mlp, int32_t impl);
+
+/* C (M x N, FP32, row stride ldc) = A (M x K, BF16, row stride lda) times
+ * B (N x K, BF16, row stride ldb) transposed, by the chosen kernel; device
+ * pointers, A and B 16-byte aligned (null allowed when K = 0: C = 0), lda and
+ * ldb multiples of 8 and >= K.
+ * Synchronises the stream.  For checking the kernels against a reference;
+ * allocates a 4-byte flag on the device per call.  SCS_EINVAL on bad
+ * arguments, SCS_ECUDA if a launch failed or a tensor-core wait timed out. */
+int scs_mlp_gemm_nt(int32_t impl, int32_t M, int32_t N, int32_t K, const void *A, int32_t lda, const void *B,
+                    int32_t ldb, float *C, int32_t ldc, void *cuda_stream);
 
 #ifdef __cplusplus
 }

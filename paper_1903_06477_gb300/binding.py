@@ -113,6 +113,9 @@ _SIGS = [
     ("scs_mlp_get_params", C.c_int, [C.c_void_p, C.c_void_p]),
     ("scs_mlp_set_params", C.c_int, [C.c_void_p, C.c_void_p]),
     ("scs_mlp_destroy", None, [C.c_void_p]),
+    ("scs_mlp_set_gemm", C.c_int, [C.c_void_p, C.c_int32]),
+    ("scs_mlp_gemm_nt", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                  C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
 ]
 
 
@@ -359,16 +362,35 @@ class Batch:
             pass
 
 
+GEMM_MMA, GEMM_TCGEN05 = 0, 1
+
+
+def gemm_nt(A, B, impl=GEMM_MMA, stream=None):
+    """C = A @ B.T (FP32) from CUDA bf16 tensors A (M x K) and B (N x K) whose
+    row strides are multiples of 8 (scs_mlp_gemm_nt); returns a new CUDA
+    float32 tensor."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    out = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    st = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(lib().scs_mlp_gemm_nt(impl, M, N, K, C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(B.data_ptr()),
+                                 B.stride(0), C.c_void_p(out.data_ptr()), N, st))
+    return out
+
+
 class MLP:
     """The learned warm-start network (include/superscs_mlp.h).  Batches are
     CUDA torch tensors (float32, row-major)."""
 
-    def __init__(self, d_in, d_hidden, d_out, max_batch, seed=0, stream=None):
+    def __init__(self, d_in, d_hidden, d_out, max_batch, seed=0, stream=None, gemm=None):
         h = C.c_void_p()
         st = None if stream is None else C.c_void_p(stream.cuda_stream)
         _check(lib().scs_mlp_create(d_in, d_hidden, d_out, max_batch, seed, st, C.byref(h)))
         self.h = h
         self.dims = (d_in, d_hidden, d_out)
+        if gemm is not None:
+            _check(lib().scs_mlp_set_gemm(self.h, gemm))
 
     @property
     def num_params(self):

@@ -1,14 +1,16 @@
 // mlp.cu -- the learned warm start: a 3-layer MLP trained and evaluated
 // entirely by the kernels in this file (see include/superscs_mlp.h).
 //
-// GEMMs use the BF16 tensor-core MMA (m16n8k16, FP32 accumulation) on
-// 128x128x32 block tiles staged through shared memory by cp.async; every
-// product is written as C = A B^T with both operands K-contiguous, so the
-// backward pass works on transposed copies made by a tiled transpose kernel.
+// Every product is written as C = A B^T with both operands K-contiguous (the
+// backward pass works on transposed copies made by a tiled transpose kernel)
+// and runs on one of two BF16 kernels with FP32 accumulation: gemm_nt, the
+// warp-level MMA (m16n8k16) on 128x128x32 tiles staged by cp.async, or
+// gemm_nt_tc, tcgen05.mma with the accumulator in tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -155,6 +157,200 @@ __global__ void __launch_bounds__(NTH) gemm_nt(int M, int N, int K, const bf16* 
                     if (e.C16) e.C16[(size_t)m * e.ldc16 + n] = __float2bfloat16(v);
                 }
             }
+}
+
+// ---------------------------------------------------------------------------
+// The same product C = A B^T on the fifth-generation tensor cores.
+//
+// Both operands are staged in shared memory in the K-major layout without
+// swizzle that tcgen05.mma reads through a matrix descriptor: core matrices
+// of 8 rows x 16 bytes (8 BF16 along K) stored contiguously, LBO = 128 bytes
+// between the core matrices of one 8-row group along K, SBO = 1024 bytes
+// between 8-row groups (a 64-wide K block per stage).  One thread issues the
+// four 128 x 128 x 16 MMAs of a K block and commits them to that stage's
+// mbarrier; the accumulator tile (FP32, 128 lanes x 128 columns) lives in
+// tensor memory and the four warps read their 32 lanes back with tcgen05.ld
+// for the epilogue.  While the tensor core works on one stage, all threads
+// fill the other by cp.async (zero fill gives the tails in M, N and K).
+// Every wait is bounded; on expiry *err is set and the tile is not written.
+// ---------------------------------------------------------------------------
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_NTH = 128;
+constexpr int TC_TILE = TC_BM * TC_BK * 2;  // bytes of one operand block (16 KB)
+constexpr int TC_SMEM = 2 * 2 * TC_TILE;    // two stages of A and B
+constexpr unsigned TC_LBO = 128, TC_SBO = 1024;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
+// kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_BN >> 3) << 17) |
+                              ((unsigned)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ unsigned long long tc_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool tc_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ bool tc_wait(unsigned bar, unsigned parity)
+{
+    if (tc_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = tc_now();
+    while (!tc_try_wait(bar, parity))
+        if (tc_now() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
+// SBO >> 4 (32-45), descriptor version 1 (bits 46-47), no swizzle (61-63 = 0)
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr)
+{
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)(TC_LBO >> 4) << 16) |
+           ((unsigned long long)(TC_SBO >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_cp16(unsigned dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void tc_mma(unsigned tmem, unsigned long long ad, unsigned long long bd, unsigned acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const bf16* __restrict__ A, int lda,
+                                                      const bf16* __restrict__ Bm, int ldb, Epi e, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_sm[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ unsigned tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const unsigned sbase = sa(tc_sm);
+    const unsigned bar0 = sa(&bar[0]);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_slot)),
+                     "r"(TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_slot;
+
+    auto load = [&](int st, int k0) {
+        const unsigned a_s = sbase + (unsigned)st * 2u * TC_TILE, b_s = a_s + TC_TILE;
+        for (int c = tid; c < TC_BM * (TC_BK / 8); c += TC_NTH) {
+            const int r = c >> 3, kc = c & 7;
+            const unsigned off = (unsigned)(r >> 3) * TC_SBO + (unsigned)kc * TC_LBO + (unsigned)(r & 7) * 16u;
+            const int gk = k0 + kc * 8;
+            const int gm = m0 + r;
+            int bytes = (gm < M && gk < K) ? min(16, (K - gk) * 2) : 0;
+            tc_cp16(a_s + off, bytes ? A + (size_t)gm * lda + gk : A, bytes);
+            const int gn = n0 + r;
+            bytes = (gn < N && gk < K) ? min(16, (K - gk) * 2) : 0;
+            tc_cp16(b_s + off, bytes ? Bm + (size_t)gn * ldb + gk : Bm, bytes);
+        }
+    };
+
+    const int KT = (K + TC_BK - 1) / TC_BK;
+    bool ok = true;
+    if (KT > 0) load(0, 0);
+    cp_commit();
+    for (int kt = 0; kt < KT; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < KT) {
+            // stage st^1 is free once the MMAs of block kt-1 (its last reader) completed
+            if (kt >= 1 && !tc_wait(bar0 + 8u * (unsigned)(st ^ 1), (unsigned)((kt - 1) >> 1) & 1u)) ok = false;
+            if (ok) load(st ^ 1, (kt + 1) * TC_BK);
+            cp_commit();
+            cp_wait1();
+        } else {
+            cp_wait0();
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor-core reads
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a_s = sbase + (unsigned)st * 2u * TC_TILE, b_s = a_s + TC_TILE;
+#pragma unroll
+            for (int j = 0; j < TC_BK / 16; ++j)
+                tc_mma(tmem, tc_desc(a_s + (unsigned)j * 2u * TC_LBO), tc_desc(b_s + (unsigned)j * 2u * TC_LBO),
+                       (kt | j) != 0);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8u * (unsigned)st)
+                         : "memory");
+        }
+    }
+    cp_wait0();
+    const unsigned last_bar = bar0 + 8u * (unsigned)((KT - 1) & 1), last_par = (unsigned)((KT - 1) >> 1) & 1u;
+    if (ok && KT > 0 && !tc_wait(last_bar, last_par)) ok = false;
+    ok = !__syncthreads_or(!ok);
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+            unsigned v[32];
+            if (KT > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0u;
+            }
+            if (m < M) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int n = n0 + c0 + q;
+                    if (n >= N) break;
+                    float x = __uint_as_float(v[q]);
+                    if (e.bias) x += e.bias[n];
+                    if (e.mask && !((float)e.mask[(size_t)m * e.ldm + n] > 0.f)) x = 0.f;
+                    if (e.relu) x = fmaxf(x, 0.f);
+                    if (e.C32) e.C32[(size_t)m * e.ldc + n] = x;
+                    if (e.C16) e.C16[(size_t)m * e.ldc16 + n] = __float2bfloat16(x);
+                }
+            }
+        }
+    } else {
+        // give MMAs still in flight a second bounded wait before the tensor memory is released
+        if (KT > 0) tc_wait(last_bar, last_par);
+        if (tid == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
 }
 
 // out (C x R, ld_out) = in (R x C, ld_in)^T, BF16, 32 x 32 tiles
@@ -340,7 +536,9 @@ struct scs_mlp {
     bf16 *Xn, *Xnt, *h1, *h1t, *h2, *h2t, *dy16, *dyt, *dh2_16, *dh2t, *dh1_16, *dh1t;
     float *y, *dy32, *dh2_32, *dh1_32;
     double *part, *loss;
+    int* err;  // set by a tensor-core GEMM whose bounded wait expired
     int step;
+    int gemm_impl;  // SCS_MLP_GEMM_MMA or SCS_MLP_GEMM_TCGEN05
     char* arena;
 };
 
@@ -357,11 +555,41 @@ static int mlp_err(const char* what, cudaError_t e)
         if (e_ != cudaSuccess) return mlp_err(#x, e_); \
     } while (0)
 
+static int launch_gemm(int impl, cudaStream_t st, int* err, int M, int N, int K, const bf16* A, int lda,
+                       const bf16* B, int ldb, const Epi& e)
+{
+    if (impl == SCS_MLP_GEMM_TCGEN05) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            MCU(cudaFuncSetAttribute(gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+            attr_set = true;
+        }
+        dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
+        gemm_nt_tc<<<grid, TC_NTH, TC_SMEM, st>>>(M, N, K, A, lda, B, ldb, e, err);
+        const cudaError_t ce = cudaGetLastError();
+        return ce == cudaSuccess ? SCS_OK : mlp_err("gemm_nt_tc launch", ce);
+    }
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_nt<<<grid, NTH, 0, st>>>(M, N, K, A, lda, B, ldb, e);
+    const cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? SCS_OK : mlp_err("gemm_nt launch", ce);
+}
 static int gemm(scs_mlp* n, int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const Epi& e)
 {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_nt<<<grid, NTH, 0, n->st>>>(M, N, K, A, lda, B, ldb, e);
-    return cudaGetLastError() == cudaSuccess ? SCS_OK : mlp_err("gemm_nt launch", cudaGetLastError());
+    return launch_gemm(n->gemm_impl, n->st, n->err, M, N, K, A, lda, B, ldb, e);
+}
+// reads (and clears) the tensor-core GEMM's timeout flag; the stream must be synchronised
+static int check_err_flag(scs_mlp* n)
+{
+    int h = 0;
+    MCU(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->st));
+    MCU(cudaStreamSynchronize(n->st));
+    if (h) {
+        MCU(cudaMemsetAsync(n->err, 0, sizeof(int), n->st));
+        sscs::record_error("mlp: a tensor-core GEMM wait timed out; its output tile was not written");
+        return SCS_ECUDA;
+    }
+    return SCS_OK;
 }
 static void transpose(scs_mlp* n, const bf16* in, int R, int C, int ld_in, bf16* out, int ld_out)
 {
@@ -399,6 +627,7 @@ extern "C" int scs_mlp_create(int32_t din, int32_t dh, int32_t dout, int32_t max
     n->maxB = maxB;
     n->ldin = pad8(din);
     n->ldout = pad8(dout);
+    n->gemm_impl = SCS_MLP_GEMM_MMA;
     n->st = (cudaStream_t)stream;
     const int Bp = pad8(maxB);
     n->oW1 = 0;
@@ -445,6 +674,7 @@ extern "C" int scs_mlp_create(int32_t din, int32_t dh, int32_t dout, int32_t max
     take((void**)&n->dh1_32, sizeof(float) * (size_t)maxB * dh);
     take((void**)&n->part, sizeof(double) * 8192);
     take((void**)&n->loss, sizeof(double) * 2);
+    take((void**)&n->err, sizeof(int) * 4);
     for (auto& pl : plan) off += (pl.second + 255) & ~size_t(255);
     cudaError_t e = cudaMalloc((void**)&n->arena, off);
     if (e != cudaSuccess) {
@@ -567,6 +797,7 @@ static int backward(scs_mlp* n, const float* Y, int B, float* loss_host)
         MCU(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->st));
         MCU(cudaStreamSynchronize(n->st));
         *loss_host = (float)l;
+        if ((rc = check_err_flag(n))) return rc;
     }
     return SCS_OK;
 }
@@ -595,7 +826,7 @@ extern "C" int scs_mlp_gradients(scs_mlp* n, const float* X, const float* Y, int
     if (rc) return rc;
     if (grad) MCU(cudaMemcpyAsync(grad, n->g, sizeof(float) * n->np, cudaMemcpyDefault, n->st));
     MCU(cudaStreamSynchronize(n->st));
-    return SCS_OK;
+    return check_err_flag(n);
 }
 
 extern "C" int scs_mlp_train_step(scs_mlp* n, const float* X, const float* Y, int32_t B, float lr, float* loss)
@@ -621,6 +852,53 @@ extern "C" int scs_mlp_train_step(scs_mlp* n, const float* X, const float* Y, in
     transpose(n, n->W3, n->dout, n->dh, n->dh, n->W3t, n->ldout);
     MCU(cudaGetLastError());
     return SCS_OK;
+}
+
+extern "C" int scs_mlp_set_gemm(scs_mlp* n, int32_t impl)
+{
+    if (!n || (impl != SCS_MLP_GEMM_MMA && impl != SCS_MLP_GEMM_TCGEN05)) {
+        sscs::record_error("scs_mlp_set_gemm: bad arguments");
+        return SCS_EINVAL;
+    }
+    n->gemm_impl = impl;
+    return SCS_OK;
+}
+
+extern "C" int scs_mlp_gemm_nt(int32_t impl, int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                               const void* B, int32_t ldb, float* C, int32_t ldc, void* stream)
+{
+    // with K = 0 the operands are never read (C = 0) and may be null
+    const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+    const bool operands_ok = K == 0 || (A && B && aligned);
+    if ((impl != SCS_MLP_GEMM_MMA && impl != SCS_MLP_GEMM_TCGEN05) || M < 0 || N < 0 || K < 0 || !operands_ok ||
+        !C || lda < K || ldb < K || lda % 8 || ldb % 8 || ldc < N) {
+        sscs::record_error("scs_mlp_gemm_nt: bad arguments");
+        return SCS_EINVAL;
+    }
+    if (M == 0 || N == 0) return SCS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (K == 0) {  // empty sum: no kernel reads the (possibly null) operands
+        MCU(cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st));
+        MCU(cudaStreamSynchronize(st));
+        return SCS_OK;
+    }
+    int* err = nullptr;
+    MCU(cudaMalloc((void**)&err, sizeof(int)));
+    int rc = SCS_OK;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) rc = mlp_err("memset", cudaGetLastError());
+    if (!rc)
+        rc = launch_gemm(impl, st, err, M, N, K, static_cast<const bf16*>(A), lda, static_cast<const bf16*>(B), ldb,
+                         epi(nullptr, nullptr, 0, 0, C, ldc, nullptr, 0));
+    int h = 0;
+    if (!rc && cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = mlp_err("copy", cudaGetLastError());
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = mlp_err("gemm", cudaGetLastError());
+    cudaFree(err);
+    if (!rc && h) {
+        sscs::record_error("scs_mlp_gemm_nt: a tensor-core wait timed out");
+        rc = SCS_ECUDA;
+    }
+    return rc;
 }
 
 extern "C" void scs_mlp_destroy(scs_mlp* n)

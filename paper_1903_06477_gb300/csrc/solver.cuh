@@ -18,6 +18,7 @@ namespace sscs {
 constexpr int MAXMEM = 64;   // direction memory cap (RB)
 constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared memory)
 constexpr int PSD_MAX = 64;  // largest PSD order
+constexpr int PSD_LD = PSD_MAX + 1;  // row stride bound of a block's matrices in shared memory
 
 enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5,
             MODE_RESID = 6, MODE_SPMV = 7 };
@@ -762,19 +763,30 @@ __device__ __forceinline__ double block_sum(double x, double* red)
 // round) on the dp x dp matrix X in shared memory; V receives the
 // eigenvectors as columns.  Rotation formula as in the textbook cyclic method.
 template <typename T>
-__device__ void jacobi_block(T* X, T* V, int dp, int* pp, int* qq, T* cs, T* sn, double* red, double tol2, int max_sweeps)
+__device__ void jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs, T* sn, double* red, double tol2,
+                             int max_sweeps)
 {
+    // X and V are dp x dp with row stride ld = dp + 1 (odd): a warp walking a
+    // column touches 32 different banks
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int idx = tid; idx < dp * dp; idx += nt) V[idx] = (idx / dp == idx % dp) ? T(1) : T(0);
+    for (int idx = tid; idx < dp * dp; idx += nt) {
+        const int i = idx / dp, j = idx % dp;
+        V[i * ld + j] = (i == j) ? T(1) : T(0);
+    }
     double total = 0.0;
-    for (int idx = tid; idx < dp * dp; idx += nt) total += (double)X[idx] * (double)X[idx];
+    for (int idx = tid; idx < dp * dp; idx += nt) {
+        const T x = X[(idx / dp) * ld + idx % dp];
+        total += (double)x * (double)x;
+    }
     __syncthreads();
     total = block_sum(total, red);
     const int half = dp / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         double off = 0.0;
-        for (int idx = tid; idx < dp * dp; idx += nt)
-            if (idx / dp != idx % dp) off += (double)X[idx] * (double)X[idx];
+        for (int idx = tid; idx < dp * dp; idx += nt) {
+            const int i = idx / dp, j = idx % dp;
+            if (i != j) off += (double)X[i * ld + j] * (double)X[i * ld + j];
+        }
         off = block_sum(off, red);
         if (off <= tol2 * total || off == 0.0) break;
         for (int rnd = 0; rnd < dp - 1; ++rnd) {
@@ -788,10 +800,10 @@ __device__ void jacobi_block(T* X, T* V, int dp, int* pp, int* qq, T* cs, T* sn,
                     b = (rnd - k + dp - 1) % (dp - 1);
                 }
                 const int p = a < b ? a : b, qd = a < b ? b : a;
-                const T apq = X[p * dp + qd];
+                const T apq = X[p * ld + qd];
                 T c = 1, s = 0;
                 if (apq != T(0)) {
-                    const T theta = (X[qd * dp + qd] - X[p * dp + p]) / (T(2) * apq);
+                    const T theta = (X[qd * ld + qd] - X[p * ld + p]) / (T(2) * apq);
                     const T at = theta < T(0) ? -theta : theta;
                     T t;
                     if (at > T(1e18))
@@ -812,12 +824,12 @@ __device__ void jacobi_block(T* X, T* V, int dp, int* pp, int* qq, T* cs, T* sn,
                 const int k = idx / dp, i = idx % dp;
                 const int p = pp[k], qd = qq[k];
                 const T c = cs[k], s = sn[k];
-                const T xp = X[i * dp + p], xq = X[i * dp + qd];
-                X[i * dp + p] = c * xp - s * xq;
-                X[i * dp + qd] = s * xp + c * xq;
-                const T vp = V[i * dp + p], vq = V[i * dp + qd];
-                V[i * dp + p] = c * vp - s * vq;
-                V[i * dp + qd] = s * vp + c * vq;
+                const T xp = X[i * ld + p], xq = X[i * ld + qd];
+                X[i * ld + p] = c * xp - s * xq;
+                X[i * ld + qd] = s * xp + c * xq;
+                const T vp = V[i * ld + p], vq = V[i * ld + qd];
+                V[i * ld + p] = c * vp - s * vq;
+                V[i * ld + qd] = s * vp + c * vq;
             }
             __syncthreads();
             // rows: X <- J^T X
@@ -825,9 +837,9 @@ __device__ void jacobi_block(T* X, T* V, int dp, int* pp, int* qq, T* cs, T* sn,
                 const int k = idx / dp, j = idx % dp;
                 const int p = pp[k], qd = qq[k];
                 const T c = cs[k], s = sn[k];
-                const T xp = X[p * dp + j], xq = X[qd * dp + j];
-                X[p * dp + j] = c * xp - s * xq;
-                X[qd * dp + j] = s * xp + c * xq;
+                const T xp = X[p * ld + j], xq = X[qd * ld + j];
+                X[p * ld + j] = c * xp - s * xq;
+                X[qd * ld + j] = s * xp + c * xq;
             }
             __syncthreads();
         }
@@ -850,8 +862,8 @@ struct PsdSmem {
 template <typename T>
 __host__ __device__ constexpr size_t psd_smem_bytes()
 {
-    return sizeof(T) * (2 * PSD_MAX * PSD_MAX + 3 * PSD_MAX) + sizeof(int) * PSD_MAX + 64 * sizeof(double) +
-           (sizeof(T) == 4 ? sizeof(double) * PSD_MAX * PSD_MAX : 0);
+    return sizeof(T) * (2 * PSD_MAX * PSD_LD + 3 * PSD_MAX) + sizeof(int) * PSD_MAX + 64 * sizeof(double) +
+           (sizeof(T) == 4 ? sizeof(double) * PSD_MAX * PSD_LD : 0);
 }
 
 template <typename T>
@@ -859,8 +871,8 @@ __device__ PsdSmem<T> psd_smem(unsigned char* base)
 {
     PsdSmem<T> s;
     s.X = (T*)base;
-    s.V = s.X + PSD_MAX * PSD_MAX;
-    s.cs = s.V + PSD_MAX * PSD_MAX;
+    s.V = s.X + PSD_MAX * PSD_LD;
+    s.cs = s.V + PSD_MAX * PSD_LD;
     s.sn = s.cs + PSD_MAX / 2;
     s.lam = s.sn + PSD_MAX / 2;
     s.red = (double*)(s.lam + 2 * PSD_MAX);
@@ -928,6 +940,7 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
             const int d = ro(P.s_dim + k);
             const int o = n + ro(P.s_off + k);
             const int dp = d + (d & 1);
+            const int ld = dp + 1;  // odd row stride: column walks are free of bank conflicts
             const double isq2 = 0.70710678118654752440;
             __syncthreads();
             for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
@@ -940,21 +953,21 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                     const T v = T(2) * wt - w;
                     val = (ii == jj) ? v : (T)((double)v * isq2);
                 }
-                sm.X[idx] = val;
-                if constexpr (sizeof(T) == 4) sm.X0[idx] = (double)val;
+                sm.X[i * ld + j] = val;
+                if constexpr (sizeof(T) == 4) sm.X0[i * ld + j] = (double)val;
             }
             __syncthreads();
             const double tol2 = sizeof(T) == 8 ? 1e-26 : 1e-11;
-            jacobi_block<T>(sm.X, sm.V, dp, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2, sizeof(T) == 8 ? 20 : 15);
+            jacobi_block<T>(sm.X, sm.V, dp, ld, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2, sizeof(T) == 8 ? 20 : 15);
             if constexpr (sizeof(T) == 4) {
                 // FP64 recheck of the FP32 eigenpairs: ||X V - V diag(l)||_F / ||X||_F
                 double r2 = 0.0, x2 = 0.0;
                 for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
                     const int i = idx / dp, k = idx % dp;
-                    double acc = -(double)sm.V[i * dp + k] * (double)sm.X[k * dp + k];
-                    for (int j = 0; j < dp; ++j) acc += sm.X0[i * dp + j] * (double)sm.V[j * dp + k];
+                    double acc = -(double)sm.V[i * ld + k] * (double)sm.X[k * ld + k];
+                    for (int j = 0; j < dp; ++j) acc += sm.X0[i * ld + j] * (double)sm.V[j * ld + k];
                     r2 += acc * acc;
-                    x2 += sm.X0[idx] * sm.X0[idx];
+                    x2 += sm.X0[i * ld + k] * sm.X0[i * ld + k];
                 }
                 r2 = block_sum(r2, sm.red);
                 x2 = block_sum(x2, sm.red);
@@ -964,7 +977,7 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                 }
             }
             for (int i = threadIdx.x; i < dp; i += blockDim.x) {
-                const T l = sm.X[i * dp + i];
+                const T l = sm.X[i * ld + i];
                 sm.lam[i] = l > T(0) ? l : T(0);
             }
             __syncthreads();
@@ -972,7 +985,7 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                 const int i = idx / d, j = idx % d;
                 if (i < j) continue;
                 T s = 0;
-                for (int kk = 0; kk < dp; ++kk) s += sm.V[i * dp + kk] * sm.lam[kk] * sm.V[j * dp + kk];
+                for (int kk = 0; kk < dp; ++kk) s += sm.V[i * ld + kk] * sm.lam[kk] * sm.V[j * ld + kk];
                 const int e = o + svec_index(d, i, j);
                 T w, wt;
                 op.load(e, w, wt);

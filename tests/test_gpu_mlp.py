@@ -24,12 +24,13 @@ def _blocks(dims):
     return np.cumsum([0] + sizes)
 
 
+@pytest.mark.parametrize("gemm", [B.GEMM_MMA, B.GEMM_TCGEN05])
 @pytest.mark.parametrize("dims,batch", [((40, 64, 50), 32), ((300, 128, 1001), 77), ((2000, 256, 2203), 256),
                                         ((2000, 1024, 22004), 256)])  # the last: the warm-start network itself
-def test_gradients_vs_oracle(dims, batch):
+def test_gradients_vs_oracle(dims, batch, gemm):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(sum(dims))
-    net = B.MLP(*dims, max_batch=max(batch, 64), seed=3)
+    net = B.MLP(*dims, max_batch=max(batch, 64), seed=3, gemm=gemm)
     X = rng.standard_normal((batch, dims[0])).astype(np.float32)
     T = rng.standard_normal((batch, dims[2])).astype(np.float32)
     Xd = torch.as_tensor(X, device="cuda")
