@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
 # solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {
-    ("c2", "mixed"): {"bytes": 425705552128, "iters_fp32": 113, "cg_iters": 4139,
-                      "digest": "5ea3b0a25362c6a1cdfb9de4102c16f72342206e58ebfdec06cfa898cc008754"},
+    ("c2", "mixed"): {"bytes": 425713904128, "iters_fp32": 113, "cg_iters": 4139,
+                      "digest": "47a187fd46921fb33de81f12604fa6a68f82a27f2f50bce314a4bf248832967a"},
 }
 
 

@@ -11,7 +11,7 @@ namespace sscs {
 struct SmemFixed {
     unsigned long long mbar[2 * MAX_WARPS];
     unsigned ph[MAX_WARPS];
-    double red[(MAX_WARPS + 1) * KMAX];
+    double red[(MAX_WARPS + 2) * KMAX];  // reduction rows, final sums, one row of broadcast slots
     double G[AAMAX * AAMAX];
     double L[AAMAX * AAMAX];
     double rhs[AAMAX];

@@ -672,14 +672,27 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
             });
             double red[4] = {(double)pq, (double)rq, (double)qq, (double)rr_part};
             tm.reduce(red);
-            if (have_part) rr = red[3];
-            const double alpha = rr / red[0];
-            double rr_new = rr - 2.0 * alpha * red[1] + alpha * alpha * red[2];
-            if (rr_new < 0.0) rr_new = 0.0;
             ++it;
-            const bool done = !(sqrt(rr_new) > tol) || it >= cg_max;
-            const T ta = (T)alpha;
-            const T tb = (T)(rr_new / rr);
+            // The scalar step (two FP64 divisions, a square root) is evaluated by
+            // one thread per CTA and handed to the others through shared memory:
+            // the FP64 pipe is a small fraction of the FP32 one, and every thread
+            // of every warp evaluating it costs more than the extra CTA barrier.
+            // The values are the same bits either way (rr lives in thread 0).
+            double* bc = tm.bcast();
+            if (threadIdx.x == 0) {
+                if (have_part) rr = red[3];
+                const double alpha = rr / red[0];
+                double rr_new = rr - 2.0 * alpha * red[1] + alpha * alpha * red[2];
+                if (rr_new < 0.0) rr_new = 0.0;
+                reinterpret_cast<T*>(bc)[0] = (T)alpha;
+                reinterpret_cast<T*>(bc)[1] = (T)(rr_new / rr);
+                reinterpret_cast<int*>(bc + 2)[0] = (!(sqrt(rr_new) > tol) || it >= cg_max) ? 1 : 0;
+                rr = rr_new;
+            }
+            __syncthreads();
+            const T ta = reinterpret_cast<const T*>(bc)[0];
+            const T tb = reinterpret_cast<const T*>(bc)[1];
+            const bool done = reinterpret_cast<const int*>(bc + 2)[0] != 0;
             rr_part = 0;
             if (done) {
                 for (int j = tm.rank(); j < n; j += tm.size()) x[j] += ta * p[j];
@@ -694,7 +707,6 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
                 }
             }
             have_part = true;
-            rr = rr_new;
             tm.sync();
             if (done) break;
         }

@@ -20,7 +20,8 @@
 
 namespace sscs {
 
-// Sum K doubles over the block; result in every thread.  red: smem of (MAX_WARPS+1)*KMAX doubles.
+// Sum K doubles over the block; result in every thread.  red: smem of (MAX_WARPS+2)*KMAX doubles
+// (the last row holds the broadcast slots of bcast()).
 template <int K>
 __device__ __forceinline__ void block_partial(double (&v)[K], double* red)
 {
@@ -47,6 +48,8 @@ struct BlockTeam {
     __device__ __forceinline__ int nblocks() const { return 1; }
     __device__ __forceinline__ void sync() { __syncthreads(); }
     __device__ __forceinline__ bool aborted() const { return false; }
+    // shared-memory slots through which one thread hands scalars to its CTA
+    __device__ __forceinline__ double* bcast() const { return red + (MAX_WARPS + 1) * KMAX; }
     template <int K>
     __device__ __forceinline__ void reduce(double (&v)[K])
     {
@@ -82,6 +85,8 @@ struct GridTeam {
     __device__ __forceinline__ int block() const { return blockIdx.x; }
     __device__ __forceinline__ int nblocks() const { return gridDim.x; }
     __device__ __forceinline__ bool aborted() const { return *(volatile int*)abort_flag != 0; }
+    // shared-memory slots through which one thread hands scalars to its CTA
+    __device__ __forceinline__ double* bcast() const { return red + (MAX_WARPS + 1) * KMAX; }
 
     // Grid barrier on one monotonically increasing 64-bit arrival count: the
     // e-th barrier is passed once the count reaches e * gridDim.x, so no
