@@ -34,6 +34,53 @@ __device__ __forceinline__ void block_partial(double (&v)[K], double* red)
     __syncthreads();
 }
 
+// The same sums with fewer FP64 instructions, used by the grid team (in the
+// batch kernel, limited to 64 registers a thread, the larger code made the
+// compiler outline the solver loop with more spills).
+//
+// Each warp's sum of value k is the butterfly tree of warp_sum (pairs of
+// lanes l, l+16, then l, l+8, ..., l, l+1, as seen from lane 0), but the
+// trees of several values share instructions: at the first level the lower
+// half-warp adds the pairs of one value and the upper half those of the
+// next, at the second level groups of 8 lanes take four values.  Every node
+// of every tree is the same sum of the same two operands (addition is
+// commutative), so the results are bitwise those of warp_sum, with about a
+// third of the FP64 additions (6 instead of 20 for four values).
+template <int K>
+__device__ __forceinline__ void block_partial_packed(double (&v)[K], double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* row = red + wid * KMAX;
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+#pragma unroll
+    for (int k = 0; k + 4 <= K; k += 4) {
+        // level 16: lanes 0-15 value k (a) / k+2 (b), lanes 16-31 value k+1 (a) / k+3 (b)
+        const double a = (hi16 ? v[k + 1] : v[k]) + __shfl_xor_sync(FULL_MASK, hi16 ? v[k] : v[k + 1], 16);
+        const double b = (hi16 ? v[k + 3] : v[k + 2]) + __shfl_xor_sync(FULL_MASK, hi16 ? v[k + 2] : v[k + 3], 16);
+        // level 8: lanes 0-7 value k, 8-15 value k+2, 16-23 value k+1, 24-31 value k+3
+        double s = (hi8 ? b : a) + __shfl_xor_sync(FULL_MASK, hi8 ? a : b, 8);
+        s += __shfl_xor_sync(FULL_MASK, s, 4);
+        s += __shfl_xor_sync(FULL_MASK, s, 2);
+        s += __shfl_xor_sync(FULL_MASK, s, 1);
+        if ((lane & 7) == 0) row[k + ((lane >> 4) & 1) + ((lane >> 2) & 2)] = s;
+    }
+    constexpr int k2 = K - K % 4;
+    if constexpr (K % 4 >= 2) {
+        // two values: lanes 0-15 value k2, lanes 16-31 value k2+1
+        double a = (hi16 ? v[k2 + 1] : v[k2]) + __shfl_xor_sync(FULL_MASK, hi16 ? v[k2] : v[k2 + 1], 16);
+        a += __shfl_xor_sync(FULL_MASK, a, 8);
+        a += __shfl_xor_sync(FULL_MASK, a, 4);
+        a += __shfl_xor_sync(FULL_MASK, a, 2);
+        a += __shfl_xor_sync(FULL_MASK, a, 1);
+        if ((lane & 15) == 0) row[k2 + (lane >> 4)] = a;
+    }
+    if constexpr (K % 2 == 1) {
+        const double x = warp_sum(v[K - 1]);
+        if (lane == 0) row[K - 1] = x;
+    }
+    __syncthreads();
+}
+
 struct BlockTeam {
     static constexpr bool kGrid = false;
     double* red;
@@ -129,7 +176,7 @@ struct GridTeam {
     template <int K>
     __device__ void reduce(double (&v)[K])
     {
-        block_partial<K>(v, red);
+        block_partial_packed<K>(v, red);
         const int nw = blockDim.x >> 5;
         const int B = gridDim.x;
         double* P = partials + (size_t)parity * KMAX * B;
@@ -145,7 +192,7 @@ struct GridTeam {
         for (int j = threadIdx.x; j < B; j += blockDim.x)
 #pragma unroll
             for (int k = 0; k < K; ++k) pv[k] += __ldcg(P + (size_t)k * B + j);
-        block_partial<K>(pv, red);
+        block_partial_packed<K>(pv, red);
         if (threadIdx.x < K) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += red[w * KMAX + threadIdx.x];
