@@ -263,7 +263,8 @@ const char *scs_last_error(const scs_work *work);
  * largest first.  The settings apply to every instance (team is ignored: one
  * block each).  With settings->threads = 0 and B >= 64 the setup times the
  * first solve phase on a sample of instances for 128, 256, 512 and 1024 threads
- * per block and keeps the fastest. */
+ * per block and keeps the fastest; the sample holds enough instances for two
+ * waves of the largest resident grid among the four (at most all B). */
 int scs_batch_setup(int32_t B, const scs_data *const *data, const scs_cone *const *cones,
                     const scs_settings *settings, void *cuda_stream, scs_batch **out);
 /* x[i], y[i], s[i] (host pointers; any may be NULL, as may the arrays)

@@ -1202,21 +1202,28 @@ static DevSettings batch_settings(const scs_batch* b, bool first_phase_of_mixed)
 }
 
 // Autotuner: time the first solve phase on an evenly spaced sample of the
-// (size-sorted) instances for 128, 256 and 512 threads per CTA and keep the
-// fastest; the sample's results are discarded (the real solve overwrites them).
+// (size-sorted) instances for 128, 256, 512 and 1024 threads per CTA and keep
+// the fastest; the sample's results are discarded (the real solve overwrites
+// them).
 template <typename T>
 static int autotune(scs_batch* b, const std::vector<Args<T>>& host_args, size_t dyn, const DevSettings& S,
                     Args<T>* scratch_args)
 {
-    const int nsamp = std::min(b->B, 2 * b->sms);
+    const int cand[4] = {128, 256, 512, 1024};
+    // The sample must keep every candidate's resident CTAs busy for two waves:
+    // with only a couple of instances per SM, large CTAs look fast (each
+    // instance gets more threads) although the whole batch runs best with more,
+    // smaller CTAs in flight.
+    const void* fn = sizeof(T) == 8 ? kblock_ptr<double>() : kblock_ptr<float>();
+    int resident = 1;
+    for (int c = 0; c < 4; ++c) resident = std::max(resident, occupancy_grid(fn, cand[c], dyn, b->sms, b->B));
+    const int nsamp = std::min(b->B, std::max(2 * b->sms, 2 * resident));
     std::vector<Args<T>> samp(nsamp);
     for (int i = 0; i < nsamp; ++i) samp[i] = host_args[(size_t)i * b->B / nsamp];
     CU(cudaMemcpyAsync(scratch_args, samp.data(), sizeof(Args<T>) * nsamp, cudaMemcpyHostToDevice, b->stream), b->err);
-    const int cand[4] = {128, 256, 512, 1024};
     float best = 1e30f;
     for (int c = 0; c < 4; ++c) {
-        const int grid = occupancy_grid(sizeof(T) == 8 ? kblock_ptr<double>() : kblock_ptr<float>(), cand[c], dyn,
-                                        b->sms, nsamp);
+        const int grid = occupancy_grid(fn, cand[c], dyn, b->sms, nsamp);
         CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
         CU(cudaEventRecord(b->ev[0], b->stream), b->err);
         CU(launch_block<T>(grid, cand[c], dyn, b->stream, scratch_args, nsamp, b->queue, S, MODE_SOLVE), b->err);
@@ -1334,8 +1341,8 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
         }
         Args<double>* d64 = A.take<Args<double>>(B);
         Args<float>* d32 = A.take<Args<float>>(B);
-        Args<double>* t64 = A.take<Args<double>>(2 * b->sms);
-        Args<float>* t32 = A.take<Args<float>>(2 * b->sms);
+        Args<double>* t64 = A.take<Args<double>>(B);  // the autotuner's sample: at most B instances
+        Args<float>* t32 = A.take<Args<float>>(B);
         long long* off = A.take<long long>(B + 1);
         double* packed = A.take<double>(b->packed_len);
         int* queue = A.take<int>(4);
