@@ -559,11 +559,8 @@ static int launch_gemm(int impl, cudaStream_t st, int* err, int M, int N, int K,
                        const bf16* B, int ldb, const Epi& e)
 {
     if (impl == SCS_MLP_GEMM_TCGEN05) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            MCU(cudaFuncSetAttribute(gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-            attr_set = true;
-        }
+        // a per-device attribute: set before every launch (a host call of about a microsecond)
+        MCU(cudaFuncSetAttribute(gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
         dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
         gemm_nt_tc<<<grid, TC_NTH, TC_SMEM, st>>>(M, N, K, A, lda, B, ldb, e, err);
         const cudaError_t ce = cudaGetLastError();
