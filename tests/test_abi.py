@@ -64,3 +64,25 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(binding.SCSError):
         binding.lib()
+
+
+def test_mlp_gemm_entries_reject_bad_arguments_without_gpu():
+    """Argument checks run before any device call, so they hold on a host
+    without a GPU: an unknown kernel, a row stride that is not a multiple of
+    8, a stride below K, a missing output, misaligned operands."""
+    if not os.path.exists(binding.LIB_PATH):
+        pytest.skip("libsuperscs.so not built")
+    L = binding.lib()
+    p = ctypes.c_void_p(4096)  # never dereferenced: every call below fails its checks first
+    bad = [
+        (7, 4, 4, 8, p, 8, p, 8, p, 4),      # unknown kernel
+        (0, 4, 4, 8, p, 12, p, 8, p, 4),     # lda not a multiple of 8
+        (1, 4, 4, 16, p, 8, p, 16, p, 4),    # lda < K
+        (1, 4, 4, 8, p, 8, p, 8, None, 4),   # no output
+        (1, 4, 4, 8, ctypes.c_void_p(4100), 8, p, 8, p, 4),  # A not 16-byte aligned
+        (0, 4, 5, 8, p, 8, p, 8, p, 4),      # ldc < N
+        (0, -1, 4, 8, p, 8, p, 8, p, 4),     # negative M
+    ]
+    for args in bad:
+        assert L.scs_mlp_gemm_nt(*args, None) == binding.SCS_EINVAL, args
+    assert L.scs_mlp_set_gemm(None, 1) == binding.SCS_EINVAL
