@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const 
 
     const int KT = (K + TC_BK - 1) / TC_BK;
     bool ok = true;
+    int committed = -1;  // last K block whose MMAs thread 0 committed (the same in every thread)
     if (KT > 0) load(0, 0);
     cp_commit();
     for (int kt = 0; kt < KT; ++kt) {
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const 
             ok = false;
             break;
         }
+        committed = kt;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned a_s = sbase + (unsigned)st * 2u * TC_TILE, b_s = a_s + TC_TILE;
@@ -303,8 +305,9 @@ __global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const 
         }
     }
     cp_wait0();
-    const unsigned last_bar = bar0 + 8u * (unsigned)((KT - 1) & 1), last_par = (unsigned)((KT - 1) >> 1) & 1u;
-    if (ok && KT > 0 && !tc_wait(last_bar, last_par)) ok = false;
+    // completion of the last committed block implies completion of all earlier MMAs
+    const unsigned last_bar = bar0 + 8u * (unsigned)(committed & 1), last_par = (unsigned)(committed >> 1) & 1u;
+    if (ok && committed >= 0 && !tc_wait(last_bar, last_par)) ok = false;
     ok = !__syncthreads_or(!ok);
     if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const 
         }
     } else {
         // give MMAs still in flight a second bounded wait before the tensor memory is released
-        if (KT > 0) tc_wait(last_bar, last_par);
+        if (committed >= 0) tc_wait(last_bar, last_par);
         if (tid == 0) atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
