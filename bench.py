@@ -344,6 +344,8 @@ def run_c5(args):
         bt = batch_of(gs)
         xs, ys, ss, infos = bt.solve()
         bt.close()
+        # every batch of the family has the same shape: later ones reuse the first autotuned launch shape
+        kw.setdefault("threads", int(infos[0]["threads_per_block"]))
         for g, x, y, s_, inf in zip(gs, xs, ys, ss, infos):
             if inf["status"] == B.SOLVED:
                 G.append(g.astype(np.float32))
