@@ -193,6 +193,17 @@ def oracle_baseline(prob, kw, small_prob):
                        "t_scaled_solve_s": t_small, "est_time_to_eps_s": est}
 
 
+def job_throughput(total_ms, steps, world, dist=None, device="cuda"):
+    """Whole-job throughput of N replicas: the timed region of the slowest rank
+    (max over ranks) and the instances all ranks solved in it, world * steps."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -584,11 +595,7 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = job_throughput(total_ms, args.steps, world, dist, device="cuda")
     last = infos[-1]
     # plain FP64 solve of the same instance, for the chosen-form comparison
     fp64_ms = None
