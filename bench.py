@@ -32,8 +32,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# solver launch, from one ncu capture (one pass per launch; summary and command
-# in profiles/k_grid_c2_fp32_phase_dram.md).  Valid only for the kernel sources
+# solver launch, from one ncu capture (one pass per launch).  Valid only for the kernel sources
 # it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
 # solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {

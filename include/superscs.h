@@ -184,28 +184,32 @@ int scs_set_warm(scs_work *work, const double *u);
  * membership of s and y is not checked.  Synchronises the work's stream. */
 int scs_residuals(scs_work *work, const double *x, const double *y, const double *s, double *out);
 
-/* The same three numbers as scs_residuals, for callers that cannot allocate
- * device memory.  The paper has no counterpart; this is a service of the
- * library.  It needs no scs_work (whose setup allocates) and never calls
- * cudaMalloc or cudaFree: its only scratch -- the vector A^T y and per-block
- * partial sums -- is a static device array of 8 MiB + 48 KiB that every GPU
- * loading this library holds until the process exits.  Typical callers: code
- * that runs while a CUDA graph is being captured, where allocation calls are
- * not allowed; real-time or embedded loops that forbid allocation after
- * start-up, since cudaMalloc may block and synchronise the device; hosts
- * whose device memory belongs to another allocator or memory pool.
+/* The same three numbers as scs_residuals (up to rounding: the sums of A^T y
+ * are accumulated with atomic additions, whose order varies from call to
+ * call), for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a service of the library.  It needs no scs_work (whose
+ * setup allocates) and never calls cudaMalloc or cudaFree: its only scratch
+ * -- the vector A^T y and per-block partial sums -- is a static device array
+ * of 8 MiB + 56 KiB that every GPU loading this library holds until the
+ * process exits.  Typical callers: real-time or embedded loops that forbid
+ * allocation after start-up, since cudaMalloc may block and synchronise the
+ * device; hosts whose device memory belongs to another allocator or memory
+ * pool, which a second allocator would fragment or exhaust.
  *
  * Every pointer is a device pointer: A as CSR (Ap[m+1] int64, Ai[nnz] int32
  * column indices in [0,n), Ax[nnz]), b (m), c (n), x (n), y (m), s (m), and
  * out (3 doubles: pr, dr, gap).  n above 1048576 is rejected with SCS_EINVAL
- * (message in scs_last_error(NULL)); index validity is the caller's duty.
- * The work is queued on cuda_stream (NULL: legacy default stream) and the
- * call returns without synchronising.  The first call on each device looks up
- * the scratch array's device address with that device current; make that
- * first call before any stream capture.  All calls share the one scratch
- * array and it keeps the last call's contents (its A^T y part is cleared at
- * the start of each call), so calls whose work may overlap on the GPU --
- * from different streams or threads -- race and must be serialised. */
+ * (message in scs_last_error(NULL)).  A column index outside [0,n) is skipped
+ * by the kernel and makes all three outputs NaN; the row pointers must be
+ * nondecreasing and within Ai and Ax (not checked).  The work is queued on
+ * cuda_stream (NULL: legacy default stream) and the call returns without
+ * synchronising.  The scratch array's device address is looked up once per
+ * CUDA context: the first call on each device does it, with that device
+ * current (and again after cudaDeviceReset, which creates a new context);
+ * make that first call before any stream capture.  All calls share the one
+ * scratch array and it keeps the last call's contents (its A^T y part is
+ * cleared at the start of each call), so calls whose work may overlap on the
+ * GPU -- from different streams or threads -- race and must be serialised. */
 int scs_residuals_noalloc(int32_t m, int32_t n, const int64_t *Ap, const int32_t *Ai, const double *Ax,
                           const double *b, const double *c, const double *x, const double *y,
                           const double *s, double *out, void *cuda_stream);

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(NTH) gemm_nt(int M, int N, int K, const bf16* 
 // tensor memory and the four warps read their 32 lanes back with tcgen05.ld
 // for the epilogue.  While the tensor core works on one stage, all threads
 // fill the other by cp.async (zero fill gives the tails in M, N and K).
-// Every wait is bounded; on expiry *err is set and the tile is not written.
+// Every wait is bounded; on expiry *err is set (1; 2 if the MMAs in flight did
+// not drain either) and the tile is not written.
 // ---------------------------------------------------------------------------
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_NTH = 128;
 constexpr int TC_TILE = TC_BM * TC_BK * 2;  // bytes of one operand block (16 KB)
@@ -346,9 +348,12 @@ __global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const 
             }
         }
     } else {
-        // give MMAs still in flight a second bounded wait before the tensor memory is released
-        if (committed >= 0) tc_wait(last_bar, last_par);
-        if (tid == 0) atomicExch(err, 1);
+        // give MMAs still in flight a second bounded wait before the tensor memory is released;
+        // if that one expires too, MMAs may still write the columns about to be freed (and
+        // reallocated by a later CTA on this SM): report 2, which the host treats as fatal
+        const bool drained = committed < 0 || tc_wait(last_bar, last_par);
+        const bool undrained = __syncthreads_or(!drained);
+        if (tid == 0) atomicMax(err, undrained ? 2 : 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -558,9 +563,21 @@ static int mlp_err(const char* what, cudaError_t e)
         if (e_ != cudaSuccess) return mlp_err(#x, e_); \
     } while (0)
 
+// Set once a tensor-core GEMM reported that its MMAs did not drain before the
+// tensor memory was released: that memory may since have been written behind
+// another CTA's back, so no later GEMM of this process is trusted.
+static std::atomic<bool> g_tc_fatal{false};
+static const char* const TC_FATAL_MSG =
+    "mlp: a tensor-core GEMM released tensor memory while its MMAs may still have been running; "
+    "results of this CUDA context can no longer be trusted, every later GEMM call fails";
+
 static int launch_gemm(int impl, cudaStream_t st, int* err, int M, int N, int K, const bf16* A, int lda,
                        const bf16* B, int ldb, const Epi& e)
 {
+    if (g_tc_fatal) {
+        sscs::record_error(TC_FATAL_MSG);
+        return SCS_ECUDA;
+    }
     if (impl == SCS_MLP_GEMM_TCGEN05) {
         // a per-device attribute: set before every launch (a host call of about a microsecond)
         MCU(cudaFuncSetAttribute(gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
@@ -586,7 +603,8 @@ static int check_err_flag(scs_mlp* n)
     MCU(cudaStreamSynchronize(n->st));
     if (h) {
         MCU(cudaMemsetAsync(n->err, 0, sizeof(int), n->st));
-        sscs::record_error("mlp: a tensor-core GEMM wait timed out; its output tile was not written");
+        if (h >= 2) g_tc_fatal = true;
+        sscs::record_error(h >= 2 ? TC_FATAL_MSG : "mlp: a tensor-core GEMM wait timed out; its output tile was not written");
         return SCS_ECUDA;
     }
     return SCS_OK;
@@ -895,7 +913,8 @@ extern "C" int scs_mlp_gemm_nt(int32_t impl, int32_t M, int32_t N, int32_t K, co
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = mlp_err("gemm", cudaGetLastError());
     cudaFree(err);
     if (!rc && h) {
-        sscs::record_error("scs_mlp_gemm_nt: a tensor-core wait timed out");
+        if (h >= 2) g_tc_fatal = true;
+        sscs::record_error(h >= 2 ? TC_FATAL_MSG : "scs_mlp_gemm_nt: a tensor-core wait timed out");
         rc = SCS_ECUDA;
     }
     return rc;

@@ -17,14 +17,23 @@ namespace {
 
 constexpr int RS_MAX_N = 1 << 20;  // largest n accepted (the A^T y part of the scratch)
 constexpr int RS_BLOCKS = 1024;    // fixed grid of the two streaming kernels
-constexpr int RS_VALS = 6;         // sums per block: |Ax+s-b|^2, <b,y>, |b|^2, |A^T y+c|^2, <c,x>, |c|^2
+// sums per block: |Ax+s-b|^2, <b,y>, |b|^2, skipped column indices, |A^T y+c|^2, <c,x>, |c|^2
+constexpr int RS_VALS = 7;
 constexpr int RS_THREADS = 256;
 constexpr size_t RS_DOUBLES = (size_t)RS_MAX_N + (size_t)RS_VALS * RS_BLOCKS;
-constexpr int RS_MAX_DEVICES = 64;
+constexpr int RS_MAX_CONTEXTS = 64;
 
 thread_local char rs_err[256];
 std::mutex rs_mutex;
-double* rs_scratch_ptr[RS_MAX_DEVICES] = {nullptr};
+// device address of the scratch array per CUDA context, keyed by the
+// context's process-unique ID (a context created after cudaDeviceReset gets
+// a new ID, and its reloaded module a new address)
+struct RsEntry {
+    unsigned long long ctx_id;
+    double* ptr;
+};
+RsEntry rs_cache[RS_MAX_CONTEXTS];
+int rs_cache_len = 0;
 
 }  // namespace
 
@@ -38,7 +47,7 @@ static int rs_fail(int code)
     return code;
 }
 
-// 8 MiB + 48 KiB of scratch per device: A^T y (RS_MAX_N doubles), then block partials.
+// 8 MiB + 56 KiB of scratch per device: A^T y (RS_MAX_N doubles), then block partials.
 static __device__ __align__(256) double g_rs_scratch[RS_DOUBLES];
 
 __device__ __forceinline__ double rs_warp_sum(double v)
@@ -71,17 +80,24 @@ __global__ void __launch_bounds__(RS_THREADS) rs_zero(double* aty, int n)
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) aty[j] = 0.0;
 }
 
-// rows of A: primal residual terms, <b,y>, |b|^2, and A^T y scattered by atomics
-__global__ void __launch_bounds__(RS_THREADS) rs_rows(int m, const int64_t* Ap, const int32_t* Ai, const double* Ax,
-                                                      const double* b, const double* x, const double* y,
-                                                      const double* s, double* aty, double* part)
+// rows of A: primal residual terms, <b,y>, |b|^2, and A^T y scattered by
+// atomics.  A column index outside [0, n) is skipped (it would read x or
+// write the scratch out of bounds) and counted; a nonzero count makes every
+// output NaN.
+__global__ void __launch_bounds__(RS_THREADS) rs_rows(int m, int n, const int64_t* Ap, const int32_t* Ai,
+                                                      const double* Ax, const double* b, const double* x,
+                                                      const double* y, const double* s, double* aty, double* part)
 {
-    double v[3] = {0.0, 0.0, 0.0};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         double ax = 0.0;
         const double yi = y[i];
         for (int64_t k = Ap[i]; k < Ap[i + 1]; ++k) {
             const int j = Ai[k];
+            if ((unsigned)j >= (unsigned)n) {
+                v[3] += 1.0;
+                continue;
+            }
             ax += Ax[k] * x[j];
             atomicAdd(aty + j, Ax[k] * yi);
         }
@@ -91,7 +107,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_rows(int m, const int64_t* Ap, 
         v[1] += bi * yi;
         v[2] += bi * bi;
     }
-    rs_block_store<3>(v, part, 0);
+    rs_block_store<4>(v, part, 0);
 }
 
 // columns: dual residual terms, <c,x>, |c|^2
@@ -106,7 +122,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_cols(int n, const double* c, co
         v[1] += cj * x[j];
         v[2] += cj * cj;
     }
-    rs_block_store<3>(v, part, 3);
+    rs_block_store<3>(v, part, 4);
 }
 
 // one block: fixed-order sums of the partials, then the three ratios of Sec. 4.3
@@ -122,40 +138,84 @@ __global__ void __launch_bounds__(RS_THREADS) rs_final(const double* part, doubl
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double nb = sqrt(tot[2]), nc = sqrt(tot[5]);
-        const double cx = tot[4], by = tot[1];
-        out[0] = sqrt(tot[0]) / (1.0 + nb);
-        out[1] = sqrt(tot[3]) / (1.0 + nc);
-        out[2] = fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
+        const double nb = sqrt(tot[2]), nc = sqrt(tot[6]);
+        const double cx = tot[5], by = tot[1];
+        const bool bad = tot[3] != 0.0;  // column indices outside [0, n) were skipped
+        out[0] = bad ? NAN : sqrt(tot[0]) / (1.0 + nb);
+        out[1] = bad ? NAN : sqrt(tot[4]) / (1.0 + nc);
+        out[2] = bad ? NAN : fabs(cx + by) / (1.0 + fabs(cx) + fabs(by));
     }
 }
 
-// Device address of the static scratch on the current device, looked up once
-// per device with that device current (the host-side name of the array is
-// only a stand-in, not a device address).
-static int rs_scratch(double** out)
+// Device address of the static scratch in the current CUDA context (the
+// host-side name of the array is only a stand-in, not a device address).  It
+// is looked up with cudaGetSymbolAddress once per context -- normally once
+// per device, on the first call with that device current -- and cached under
+// the context's process-unique ID, so a call after cudaDeviceReset (a new
+// primary context, the module reloaded) looks it up again instead of using a
+// stale address.
+typedef int (*rs_ctx_get_current_fn)(void** ctx);
+typedef int (*rs_ctx_get_id_fn)(void* ctx, unsigned long long* id);
+
+static int rs_context_id(unsigned long long* id)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        snprintf(rs_err, sizeof rs_err, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+    static rs_ctx_get_current_fn get_current = nullptr;
+    static rs_ctx_get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e1 == cudaSuccess && e2 == cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = (rs_ctx_get_current_fn)f1;
+            get_id = (rs_ctx_get_id_fn)f2;
+        }
+    });
+    if (!get_current || !get_id) {
+        snprintf(rs_err, sizeof rs_err, "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
         return rs_fail(SCS_ECUDA);
     }
-    if (dev < 0 || dev >= RS_MAX_DEVICES) {
-        snprintf(rs_err, sizeof rs_err, "device ordinal %d beyond %d", dev, RS_MAX_DEVICES);
-        return rs_fail(SCS_ECUDA);
-    }
-    std::lock_guard<std::mutex> lock(rs_mutex);
-    if (!rs_scratch_ptr[dev]) {
-        double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_rs_scratch);
-        if (e != cudaSuccess || !p) {
-            snprintf(rs_err, sizeof rs_err, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) {
+        // no context is current yet: make the current device's primary context current
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess || get_current(&ctx) != 0 || !ctx) {
+            snprintf(rs_err, sizeof rs_err, "no current CUDA context");
             return rs_fail(SCS_ECUDA);
         }
-        rs_scratch_ptr[dev] = p;
     }
-    *out = rs_scratch_ptr[dev];
+    if (get_id(ctx, id) != 0) {
+        snprintf(rs_err, sizeof rs_err, "cuCtxGetId failed");
+        return rs_fail(SCS_ECUDA);
+    }
+    return SCS_OK;
+}
+
+static int rs_scratch(double** out)
+{
+    unsigned long long id = 0;
+    int rc = rs_context_id(&id);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(rs_mutex);
+    for (int k = 0; k < rs_cache_len; ++k)
+        if (rs_cache[k].ctx_id == id) {
+            *out = rs_cache[k].ptr;
+            return SCS_OK;
+        }
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_rs_scratch);
+    if (e != cudaSuccess || !p) {
+        snprintf(rs_err, sizeof rs_err, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        return rs_fail(SCS_ECUDA);
+    }
+    // a full table keeps its oldest entries; later contexts look the address up on every call
+    if (rs_cache_len < RS_MAX_CONTEXTS) rs_cache[rs_cache_len++] = RsEntry{id, p};
+    *out = p;
     return SCS_OK;
 }
 
@@ -182,7 +242,7 @@ extern "C" int scs_residuals_noalloc(int32_t m, int32_t n, const int64_t* Ap, co
     double* aty = scratch;
     double* part = scratch + RS_MAX_N;
     rs_zero<<<RS_BLOCKS, RS_THREADS, 0, st>>>(aty, n);
-    rs_rows<<<RS_BLOCKS, RS_THREADS, 0, st>>>(m, Ap, Ai, Ax, b, x, y, s, aty, part);
+    rs_rows<<<RS_BLOCKS, RS_THREADS, 0, st>>>(m, n, Ap, Ai, Ax, b, x, y, s, aty, part);
     rs_cols<<<RS_BLOCKS, RS_THREADS, 0, st>>>(n, c, x, aty, part);
     rs_final<<<1, RS_THREADS, 0, st>>>(part, out);
     const cudaError_t e = cudaGetLastError();
