@@ -63,6 +63,50 @@ int scs_mlp_set_params(scs_mlp *mlp, const float *params);
 
 void scs_mlp_destroy(scs_mlp *mlp);
 
+/* Internal buffers of a network, read back for checking each kernel on its
+ * own inputs (the paper has no counterpart).  Activations and their
+ * gradients are those of the last batch that ran forward (scs_mlp_forward,
+ * scs_mlp_gradients or scs_mlp_train_step), B rows; the weight copies are the
+ * BF16 operands the GEMMs read.  Buffers (element type, rows x cols):
+ *   PARAMS, GRAD, ADAM_M, ADAM_V   FP32, 1 x num_params (order of the gradients;
+ *                                  GRAD: the last gradients computed)
+ *   IN_MEAN, IN_STD                FP32, 1 x d_in;  OUT_MEAN, OUT_STD  FP32, 1 x d_out
+ *   XN   BF16, B x d_in    normalised input        H1, H2  BF16, B x d_hidden (after ReLU)
+ *   Y    FP32, B x d_out   output, normalised units
+ *   DY   FP32, B x d_out   d loss / d y;           DY16    BF16 copy of DY
+ *   DH2, DH1   FP32, B x d_hidden, gradient at the pre-activation of layer 2 / 1;
+ *   DH2_16, DH1_16   their BF16 copies
+ *   W1 (d_hidden x d_in), W2 (d_hidden x d_hidden), W3 (d_out x d_hidden)   BF16
+ *   W2T (d_hidden x d_hidden), W3T (d_hidden x d_out)   BF16 transposed copies
+ * *rows, *cols, *elem_bytes (host, each may be NULL) receive the shape and the
+ * element size (4 FP32, 2 BF16 bits).  With out non-NULL (host or device),
+ * rows x cols packed row-major elements are copied there; the stream is
+ * synchronised.  SCS_EINVAL for an unknown buffer. */
+#define SCS_MLP_READ_PARAMS 0
+#define SCS_MLP_READ_GRAD 1
+#define SCS_MLP_READ_ADAM_M 2
+#define SCS_MLP_READ_ADAM_V 3
+#define SCS_MLP_READ_IN_MEAN 4
+#define SCS_MLP_READ_IN_STD 5
+#define SCS_MLP_READ_OUT_MEAN 6
+#define SCS_MLP_READ_OUT_STD 7
+#define SCS_MLP_READ_XN 8
+#define SCS_MLP_READ_H1 9
+#define SCS_MLP_READ_H2 10
+#define SCS_MLP_READ_Y 11
+#define SCS_MLP_READ_DY 12
+#define SCS_MLP_READ_DY16 13
+#define SCS_MLP_READ_DH2 14
+#define SCS_MLP_READ_DH2_16 15
+#define SCS_MLP_READ_DH1 16
+#define SCS_MLP_READ_DH1_16 17
+#define SCS_MLP_READ_W1 18
+#define SCS_MLP_READ_W2 19
+#define SCS_MLP_READ_W3 20
+#define SCS_MLP_READ_W2T 21
+#define SCS_MLP_READ_W3T 22
+int scs_mlp_read(scs_mlp *mlp, int32_t what, void *out, int64_t *rows, int64_t *cols, int32_t *elem_bytes);
+
 /* GEMM kernels of the network.  SCS_MLP_GEMM_MMA: warp-level BF16 MMA
  * (m16n8k16) from shared memory.  SCS_MLP_GEMM_TCGEN05: fifth-generation
  * tensor cores (tcgen05.mma, accumulator in tensor memory), 128 x 128 tiles.

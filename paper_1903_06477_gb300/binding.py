@@ -116,6 +116,8 @@ _SIGS = [
     ("scs_mlp_set_gemm", C.c_int, [C.c_void_p, C.c_int32]),
     ("scs_mlp_gemm_nt", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                   C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    ("scs_mlp_read", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int32)]),
 ]
 
 
@@ -363,6 +365,9 @@ class Batch:
 
 
 GEMM_MMA, GEMM_TCGEN05 = 0, 1
+# buffers of scs_mlp_read (include/superscs_mlp.h)
+MLP_BUFFERS = ("params", "grad", "adam_m", "adam_v", "in_mean", "in_std", "out_mean", "out_std", "xn", "h1", "h2",
+               "y", "dy", "dy16", "dh2", "dh2_16", "dh1", "dh1_16", "w1", "w2", "w3", "w2t", "w3t")
 
 
 def gemm_nt(A, B, impl=GEMM_MMA, stream=None):
@@ -421,6 +426,21 @@ class MLP:
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(lib().scs_mlp_set_params(self.h, _ptr(p)))
+
+    def read(self, name):
+        """An internal buffer (scs_mlp_read) as a host float32 array of its
+        shape; BF16 buffers are widened exactly (their bits shifted into the
+        high half of an FP32 word)."""
+        what = MLP_BUFFERS.index(name)
+        r, c, eb = C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib().scs_mlp_read(self.h, what, None, C.byref(r), C.byref(c), C.byref(eb)))
+        if eb.value == 4:
+            out = np.empty((r.value, c.value), dtype=np.float32)
+            _check(lib().scs_mlp_read(self.h, what, _ptr(out), None, None, None))
+            return out
+        raw = np.empty((r.value, c.value), dtype=np.uint16)
+        _check(lib().scs_mlp_read(self.h, what, _ptr(raw), None, None, None))
+        return (raw.astype(np.uint32) << 16).view(np.float32)
 
     def close(self):
         if getattr(self, "h", None):

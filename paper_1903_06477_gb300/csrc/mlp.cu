@@ -547,6 +547,7 @@ struct scs_mlp {
     int* err;  // set by a tensor-core GEMM whose bounded wait expired
     int step;
     int gemm_impl;  // SCS_MLP_GEMM_MMA or SCS_MLP_GEMM_TCGEN05
+    int lastB;      // rows of the last batch that went through forward()
     char* arena;
 };
 
@@ -764,6 +765,7 @@ extern "C" int scs_mlp_fit_normalization(scs_mlp* n, const float* X, const float
 static int forward(scs_mlp* n, const float* X, int B)
 {
     int rc;
+    n->lastB = B;
     normalize_to_bf16<<<grid1d((long long)B * n->din), 256, 0, n->st>>>(X, B, n->din, n->in_mean, n->in_istd, n->Xn, n->ldin);
     if ((rc = gemm(n, B, n->dh, n->din, n->Xn, n->ldin, n->W1, n->ldin,
                    epi(n->p + n->ob1, nullptr, 0, 1, nullptr, 0, n->h1, n->dh))))
@@ -857,7 +859,8 @@ extern "C" int scs_mlp_train_step(scs_mlp* n, const float* X, const float* Y, in
     if (!rc) rc = backward(n, Y, B, loss);
     if (rc) return rc;
     n->step++;
-    const float b1c = 1.f - powf(0.9f, (float)n->step), b2c = 1.f - powf(0.999f, (float)n->step);
+    // bias corrections 1 - beta^t in FP64: in FP32, 1 - 0.999f^t loses five digits to cancellation
+    const float b1c = (float)(1.0 - pow(0.9, (double)n->step)), b2c = (float)(1.0 - pow(0.999, (double)n->step));
     Segs segs;
     segs.s[0] = {n->oW1, (long long)n->dh * n->din, n->W1, n->din, n->ldin};
     segs.s[1] = {n->ob1, n->dh, nullptr, 1, 1};
@@ -918,6 +921,55 @@ extern "C" int scs_mlp_gemm_nt(int32_t impl, int32_t M, int32_t N, int32_t K, co
         rc = SCS_ECUDA;
     }
     return rc;
+}
+
+extern "C" int scs_mlp_read(scs_mlp* n, int32_t what, void* out, int64_t* rows, int64_t* cols, int32_t* elem_bytes)
+{
+    if (!n) {
+        sscs::record_error("scs_mlp_read: NULL network");
+        return SCS_EINVAL;
+    }
+    const void* src = nullptr;
+    long long r = 1, c = 0, ld = 0;
+    int eb = 4;
+    const long long B = n->lastB;
+    switch (what) {
+        case SCS_MLP_READ_PARAMS: src = n->p; c = n->np; break;
+        case SCS_MLP_READ_GRAD: src = n->g; c = n->np; break;
+        case SCS_MLP_READ_ADAM_M: src = n->m; c = n->np; break;
+        case SCS_MLP_READ_ADAM_V: src = n->v; c = n->np; break;
+        case SCS_MLP_READ_IN_MEAN: src = n->in_mean; c = n->din; break;
+        case SCS_MLP_READ_IN_STD: src = n->in_std; c = n->din; break;
+        case SCS_MLP_READ_OUT_MEAN: src = n->out_mean; c = n->dout; break;
+        case SCS_MLP_READ_OUT_STD: src = n->out_std; c = n->dout; break;
+        case SCS_MLP_READ_XN: src = n->Xn; r = B; c = n->din; ld = n->ldin; eb = 2; break;
+        case SCS_MLP_READ_H1: src = n->h1; r = B; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_H2: src = n->h2; r = B; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_Y: src = n->y; r = B; c = n->dout; break;
+        case SCS_MLP_READ_DY: src = n->dy32; r = B; c = n->dout; break;
+        case SCS_MLP_READ_DY16: src = n->dy16; r = B; c = n->dout; ld = n->ldout; eb = 2; break;
+        case SCS_MLP_READ_DH2: src = n->dh2_32; r = B; c = n->dh; break;
+        case SCS_MLP_READ_DH2_16: src = n->dh2_16; r = B; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_DH1: src = n->dh1_32; r = B; c = n->dh; break;
+        case SCS_MLP_READ_DH1_16: src = n->dh1_16; r = B; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_W1: src = n->W1; r = n->dh; c = n->din; ld = n->ldin; eb = 2; break;
+        case SCS_MLP_READ_W2: src = n->W2; r = n->dh; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_W3: src = n->W3; r = n->dout; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_W2T: src = n->W2t; r = n->dh; c = n->dh; eb = 2; break;
+        case SCS_MLP_READ_W3T: src = n->W3t; r = n->dh; c = n->dout; ld = n->ldout; eb = 2; break;
+        default:
+            sscs::record_error("scs_mlp_read: unknown buffer");
+            return SCS_EINVAL;
+    }
+    if (ld == 0) ld = c;
+    if (rows) *rows = r;
+    if (cols) *cols = c;
+    if (elem_bytes) *elem_bytes = eb;
+    if (!out || r == 0 || c == 0) return SCS_OK;
+    MCU(cudaMemcpy2DAsync(out, (size_t)c * eb, src, (size_t)ld * eb, (size_t)c * eb, (size_t)r, cudaMemcpyDefault,
+                          n->st));
+    MCU(cudaStreamSynchronize(n->st));
+    return SCS_OK;
 }
 
 extern "C" void scs_mlp_destroy(scs_mlp* n)
