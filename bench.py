@@ -131,12 +131,16 @@ def _bytes_per_pass(prob, sT):
 
 def algorithmic_bytes(prob, info, phase):
     """Matrix streams of every SpMV pass (values + column indices + row
-    pointers of A or A^T) plus the CG vector traffic of the phase."""
+    pointers of A or A^T) plus the CG vector traffic of the phase.  The FP64
+    phase's refinement corrections stream the FP32 copy (mat_passes_ir) and
+    run their CG on FP32 vectors (cg_iters_ir)."""
     m, n = prob["A"].shape
-    sT = 8 if phase == 0 else 4
-    passes = info["mat_passes"][phase]
-    cg = info["cg_iters"] - info["cg_iters_fp32"] if phase == 0 else info["cg_iters_fp32"]
-    return passes * _bytes_per_pass(prob, sT) + cg * (11 * n + 2 * m) * sT
+    if phase == 1:
+        return info["mat_passes"][1] * _bytes_per_pass(prob, 4) + info["cg_iters_fp32"] * (11 * n + 2 * m) * 4
+    cg_ir = info.get("cg_iters_ir", 0)
+    cg64 = info["cg_iters"] - info["cg_iters_fp32"] - cg_ir
+    return (info["mat_passes"][0] * _bytes_per_pass(prob, 8) + info.get("mat_passes_ir", 0) * _bytes_per_pass(prob, 4)
+            + cg64 * (11 * n + 2 * m) * 8 + cg_ir * (11 * n + 2 * m) * 4)
 
 
 def build_workload(name, rank):
@@ -167,18 +171,20 @@ def build_workload(name, rank):
     return prob, kw, cfg
 
 
-def oracle_baseline(prob, kw, small_prob):
+def oracle_baseline(prob, kw, small_prob, iters_needed=None):
     """Times the FP64 oracle on a bounded sample: its setup (the g solve) and
     one outer iteration of Algorithm 1 on the full instance; the iteration
-    count to eps is the oracle's own count on a 0.02-scaled instance of the
-    same family.  Returns (solves/s estimate, detail dict)."""
+    count to eps is the oracle's own count on a scaled instance of the same
+    family (small_prob), or iters_needed.  Returns (solves/s estimate, detail dict)."""
     from oracle import oracle as O
-    okw = dict(kw)
+    okw = {k: v for k, v in kw.items() if k in O.DEFAULTS or k == "direction"}
     okw["direction"] = {0: O.DIR_AA, 1: O.DIR_RB}[kw.get("direction", 0)]
-    t0 = time.perf_counter()
-    small = O.Oracle(small_prob, **okw).solve()
-    t_small = time.perf_counter() - t0
-    iters_needed = max(1, small["info"].iters)
+    t_small = None
+    if small_prob is not None:
+        t0 = time.perf_counter()
+        small = O.Oracle(small_prob, **okw).solve()
+        t_small = time.perf_counter() - t0
+        iters_needed = max(1, small["info"].iters)
     okw1 = dict(okw, max_iters=1)
     t0 = time.perf_counter()
     orc = O.Oracle(prob, **okw1)
@@ -190,6 +196,36 @@ def oracle_baseline(prob, kw, small_prob):
     est = t_setup + t_iter * iters_needed
     return 1.0 / est, {"t_setup_s": t_setup, "t_first_iteration_s": t_iter, "iters_to_eps_scaled": iters_needed,
                        "t_scaled_solve_s": t_small, "est_time_to_eps_s": est}
+
+
+def _oracle_solve_worker(workload, repeat_s):
+    """The FP64 oracle on the workload's instance, one thread, in its own
+    (spawned) process: setup and one whole solve to eps, timed; solves are
+    repeated while the total stays under repeat_s (small instances)."""
+    from oracle import oracle as O
+    prob, kw, _ = build_workload(workload, 0)
+    okw = {k: v for k, v in kw.items() if k in O.DEFAULTS or k == "direction"}
+    okw["direction"] = {0: O.DIR_AA, 1: O.DIR_RB}[kw.get("direction", 0)]
+    times, out = [], None
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        orc = O.Oracle(prob, **okw)
+        out = orc.solve()
+        times.append(time.perf_counter() - t0)
+        orc.close()
+        if time.perf_counter() - t_all + times[-1] > repeat_s:
+            break
+    inf = out["info"]
+    return {"t_solve_s": float(np.median(times)), "solves": len(times), "status": int(inf.status),
+            "iters": int(inf.iters), "kkt": float(max(inf.pr, inf.dr, inf.gap)), "pobj": float(inf.pobj)}
+
+
+def start_oracle_solve(workload, repeat_s=10.0):
+    """Starts the oracle's full solve in a spawned process before any GPU work."""
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(1)
+    return pool, pool.apply_async(_oracle_solve_worker, (workload, repeat_s))
 
 
 def job_throughput(total_ms, steps, world, dist=None, device="cuda"):
@@ -268,56 +304,182 @@ def run_products(args):
     return 0 if err < (1e-4 if prec == B.MIXED else 1e-12) else 1
 
 
+def _oracle_batch_worker(seeds):
+    """One host process of the all-cores oracle baseline: solves the portfolio
+    instances of the given seeds with the FP64 oracle (one thread), returns
+    (seconds, solved)."""
+    from oracle import oracle as O
+    from paper_1903_06477_gb300 import workloads as W
+    t0 = time.perf_counter()
+    solved = 0
+    for sd in seeds:
+        out = O.Oracle(W.portfolio(seed=sd), direction=O.DIR_AA, mem=10, eps=1e-5, max_iters=20000,
+                       cg_rtol=1e-10, cg_adapt=1e-2).solve()
+        solved += int(out["info"].status == O.SOLVED)
+    return time.perf_counter() - t0, solved
+
+
+def host_info():
+    """CPU model and logical core count of this host (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def start_oracle_batch_baseline(count, seed0=1000, sample=1024):
+    """Starts (before any GPU work) the all-cores oracle baseline of the
+    portfolio batch: an evenly spaced sample of the instances, one process
+    per host core (spawned).  Returns (pool, async result, sample size)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    idx = list(range(0, count, max(1, count // sample)))[:sample]
+    chunks = [[seed0 + i for i in idx[c::cores]] for c in range(cores)]
+    pool = mp.get_context("spawn").Pool(cores)
+    t0 = time.perf_counter()
+    res = pool.map_async(_oracle_batch_worker, [c for c in chunks if c])
+    return pool, res, len(idx), cores, t0
+
+
 def run_batch(args):
     """The batched workload: 4096 independent portfolio SOCPs (k ~ U{20..400})
-    in one persistent launch per precision phase; step = one batch solve."""
+    in one persistent launch per precision phase; step = one batch solve.
+    Under torchrun the instances are split across ranks (shard.partition,
+    balanced by nnz + n + m) with no exchange on the data path; only the
+    per-instance results are gathered after the timed region."""
     import torch
     from paper_1903_06477_gb300 import binding as B
+    from paper_1903_06477_gb300 import shard
     from paper_1903_06477_gb300 import workloads as W
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    probs = W.c4_portfolios(args.instances)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    orc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        orc = start_oracle_batch_baseline(args.instances)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probs_all = W.c4_portfolios(args.instances)
+    costs = [shard.instance_cost(p) for p in probs_all]
+    mine = shard.partition(costs, world)[rank]
+    probs = [probs_all[i] for i in mine]
     kw = dict(direction=0, mem=10, eps=1e-5, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5)
+    if args.threads > 0:
+        kw["threads"] = args.threads
+    for key in ("mixed_switch", "mixed_resume", "mixed_refine", "mixed_stall"):
+        if getattr(args, key) is not None:
+            kw[key] = getattr(args, key)
     prec = B.MIXED if args.precision == "mixed" else B.FP64
     t0 = time.perf_counter()
     batch = B.Batch(probs, precision=prec, **kw)
     setup_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         batch.solve()
-    times, infos = [], None
-    with Clocks(0) as clk:
+    dev_s, infos, xs = [], None, None
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with Clocks(local) as clk:
         for _ in range(args.steps):
+            xs, _, _, infos = batch.solve()
+            dev_s.append(infos[0]["batch_device_s"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms, _ = job_throughput(1e3 * sum(dev_s), args.steps, world, dist, device="cuda")
+    value = len(probs_all) * args.steps / (total_ms / 1e3)
+    tuned = int(infos[0]["threads_per_block"])
+    # the same batch in plain FP64 (same launch shape), for the chosen-form comparison and err_vs_fp64
+    fp64_ms = None
+    errs = [None] * len(probs)
+    if prec == B.MIXED and not args.no_fp64:
+        b64 = B.Batch(probs, precision=B.FP64, **dict(kw, threads=tuned))
+        b64.solve()
+        ts64 = []
+        for _ in range(args.steps):
+            x64, _, _, i64 = b64.solve()
+            ts64.append(i64[0]["batch_device_s"])
+        b64.close()
+        fp64_ms, _ = job_throughput(1e3 * sum(ts64), args.steps, world, dist, device="cuda")
+        errs = [float(np.linalg.norm(a - c) / max(1e-300, np.linalg.norm(c))) for a, c in zip(xs, x64)]
+    # e2e through the public API with host buffers: setup (validation, H2D of every instance, graph
+    # capture at the first solve) + solve + D2H of x, y, s, at the autotuned launch shape
+    e2e = None
+    if args.e2e_steps > 0:
+        ts = []
+        for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, _, _, infos = batch.solve()
-            times.append(time.perf_counter() - t0)
-    ksum = infos[0]["kernel_s"][0] + infos[0]["kernel_s"][1]
-    solved = sum(1 for i in infos if i["status"] == B.SOLVED)
-    # looped plain FP64 single solves on a sample, for comparison
-    loop_s = None
-    if not args.no_fp64:
-        samp = probs[:: max(1, len(probs) // 32)][:32]
-        t0 = time.perf_counter()
-        for p in samp:
-            w = B.Work(p, precision=B.FP64, **kw)
-            w.solve()
-            w.close()
-        loop_s = (time.perf_counter() - t0) / len(samp)
-    line = {
-        "metric": METRIC, "value": len(probs) / float(np.mean(times)), "unit": "solves/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if prec == B.MIXED else "f64", "data": "synthetic",
-        "config": {"workload": f"{len(probs)} portfolio SOCPs, k ~ U{{20..400}}, rank k/10, eps 1e-5, AA mem 10",
-                   "precision": args.precision, "instances": len(probs),
-                   "nnz_total": int(sum(p["A"].nnz for p in probs))},
-        "solved": solved, "threads_per_block": infos[0]["threads_per_block"], "setup_s": setup_s,
-        "kernel_s_per_step": ksum,
-        "looped_fp64_single_solves_per_s": None if loop_s is None else 1.0 / loop_s,
-        "speedup_vs_looped_fp64": None if loop_s is None else (len(probs) / float(np.mean(times))) * loop_s,
-        "median_iters": float(np.median([i["iters"] for i in infos])),
-        "gpu_launches": args.steps * (4 if prec == B.MIXED else 2), "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
+            be = B.Batch(probs, precision=prec, **dict(kw, threads=tuned))
+            be.solve()
+            be.close()
+            ts.append(time.perf_counter() - t0)
+        t_e2e = float(np.mean(ts))
+        if dist:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = sum(p["A"].nnz * 12 + (p["A"].shape[0] + 1) * 8 + sum(p["A"].shape) * 8 for p in probs_all)
+        d2h = sum((p["A"].shape[1] + 2 * p["A"].shape[0]) * 8 for p in probs_all)
+        e2e = {"value": len(probs_all) / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "includes": "scs_batch_setup (no autotuning: the tuned shape) + scs_batch_solve + D2H, host buffers"}
+    res = [(int(i["status"]), int(i["iters"]), float(i["pobj"]), e) for i, e in zip(infos, errs)]
+    allres = shard.gather(mine, res, len(probs_all), dist)
+    clocks = clk.summary()
+    cpu = None
+    if orc is not None:
+        pool, ares, nsamp, cores, t_start = orc
+        parts = ares.get(timeout=1800)
+        wall = time.perf_counter() - t_start
+        pool.close()
+        pool.join()
+        busy = sum(t for t, _ in parts)
+        cpu = {"value": nsamp / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle on {nsamp} instances evenly spaced over the 4096 (every "
+                         f"{max(1, args.instances // nsamp)}th seed), one spawned process per host core, "
+                         f"run while the GPU part ran; solves/s = instances / wall time",
+               "single_core_solves_per_s": nsamp / busy, "solved": int(sum(sv for _, sv in parts)),
+               **host_info()}
+    if rank == 0:
+        errs_all = [r[3] for r in allres if r[3] is not None]
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak" if world == 1 else "strong",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == B.MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"{len(probs_all)} portfolio SOCPs, k ~ U{{20..400}}, rank k/10, eps 1e-5, "
+                                   f"AA mem 10", "precision": args.precision, "instances": len(probs_all),
+                       "nnz_total": int(sum(p["A"].nnz for p in probs_all)),
+                       "parallelism": f"instances sharded over {world} GPUs by nnz+n+m" if world > 1 else "single",
+                       "l2": "the batch's data (about 0.3 GB with both precisions) exceeds L2"},
+            "solved": int(sum(1 for r in allres if r[0] == B.SOLVED)),
+            "median_iters": float(np.median([r[1] for r in allres])),
+            "threads_per_block": tuned, "setup_s": setup_s,
+            "time_to_eps_s": total_ms / args.steps / 1e3,
+            "fp64_batch_solves_per_s": None if fp64_ms is None else len(probs_all) * args.steps / (fp64_ms / 1e3),
+            "speedup_vs_fp64_batch": None if fp64_ms is None else fp64_ms / total_ms,
+            "err_vs_fp64": None if not errs_all else {"median": float(np.median(errs_all)),
+                                                      "max": float(np.max(errs_all))},
+            "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                         "traffic": None, "kernel": "k_block (one CTA per instance, data L2-resident)",
+                         "note": "not HBM-bound: each instance's data stays on chip / in L2"},
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (4 if prec == B.MIXED else 2), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -509,12 +671,17 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-cap", type=float, default=900.0,
+                    help="seconds to wait for the oracle's CPU baseline after the GPU part")
     ap.add_argument("--max-iters", type=int, default=0, help="cap outer iterations (profiling only)")
     ap.add_argument("--threads", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
     ap.add_argument("--cg-adapt", type=float, default=None)
     ap.add_argument("--mixed-switch", type=float, default=None)
     ap.add_argument("--mixed-stall", type=int, default=None)
+    ap.add_argument("--mixed-resume", type=int, default=None, help="1: the FP64 phase continues the FP32 loop state")
+    ap.add_argument("--mixed-refine", type=int, default=None,
+                    help="1: the FP64 phase solves by iterative refinement with FP32 corrections")
     ap.add_argument("--instances", type=int, default=4096, help="batch size of the c4 workload")
     ap.add_argument("--c5-train", type=int, default=16384, help="training instances of the learned warm start")
     ap.add_argument("--c5-epochs", type=int, default=60)
@@ -545,6 +712,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the CPU baseline: one whole FP64 oracle solve, started before the first GPU call
+    orc_job = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2", "c2_small"):
+        orc_job = start_oracle_solve(args.workload)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -563,7 +734,11 @@ def main():
         kw["mixed_switch"] = args.mixed_switch
     if args.mixed_stall is not None:
         kw["mixed_stall"] = args.mixed_stall
-    for key in ("cg_adapt", "mixed_switch", "mixed_stall"):
+    if args.mixed_resume is not None:
+        kw["mixed_resume"] = args.mixed_resume
+    if args.mixed_refine is not None:
+        kw["mixed_refine"] = args.mixed_refine
+    for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine"):
         if key in kw:
             cfg[key] = kw[key]
     prec = B.MIXED if args.precision == "mixed" else B.FP64
@@ -596,20 +771,26 @@ def main():
     total_ms = float(sum(step_ms))
     total_ms, value = job_throughput(total_ms, args.steps, world, dist, device="cuda")
     last = infos[-1]
-    # plain FP64 solve of the same instance, for the chosen-form comparison
+    # plain FP64 solves of the same instance over the same number of steps, same device outputs
     fp64_ms = None
     fp64_info = None
     if prec == B.MIXED and not args.no_fp64:
         xm = xd.cpu().numpy().copy()
         work64 = B.Work(prob, stream=stream, precision=B.FP64, **kw)
-        work64.solve(xd, yd, sd)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        e0.record(stream)
-        x64, _, _, fp64_info = work64.solve()
-        e1.record(stream)
+        x6 = torch.empty_like(xd)
+        y6 = torch.empty_like(yd)
+        s6 = torch.empty_like(sd)
+        work64.solve(x6, y6, s6)
+        f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            f0[k].record(stream)
+            _, _, _, fp64_info = work64.solve(x6, y6, s6)
+            f1[k].record(stream)
         torch.cuda.synchronize()
-        fp64_ms = e0.elapsed_time(e1)
+        fp64_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(f0, f1)]))
+        x64 = x6.cpu().numpy()
         last["err_vs_fp64"] = float(np.linalg.norm(xm - x64) / max(1e-300, np.linalg.norm(x64)))
         work64.close()
     # roofline of the dominant solver kernel
@@ -624,10 +805,26 @@ def main():
     if (mt is not None and mt["digest"] == digest and phase == 1 and last["iters_fp32"] == mt["iters_fp32"]
             and last["cg_iters"] == mt["cg_iters"]):
         traffic = mt["bytes"]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "k_grid<float> (FP32 phase)" if phase == 1 else "k_grid<double> (FP64 phase)",
-                "kernel_ms": ks * 1e3, "algorithmic_bytes": abytes, "src_digest": digest[:16]}
+    team = "k_grid" if last["team"] == B.TEAM_GRID else "k_block"
+    kname = f"{team}<float> (FP32 phase)" if phase == 1 else f"{team}<double> (FP64 phase)"
+    # one-pass floor: one stream of A's values and column indices per sparse product
+    floor_bytes = last["mat_passes"][phase] * prob["A"].nnz * (8 if phase == 1 else 12)
+    if team == "k_block":
+        # one CTA holds the whole instance: bound by latency, not by HBM
+        roofline = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "kernel": kname, "kernel_ms": ks * 1e3,
+                    "note": "the instance lives in one SM's shared memory / L1 and L2; no HBM roofline applies"}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "peak_source": peak_kind, "kernel": kname,
+                    "kernel_ms": ks * 1e3, "algorithmic_bytes": abytes, "src_digest": digest[:16],
+                    "bytes_rule": "per pass nnz*(elem+4) + (m+n)/2*4 + 4; per CG iteration (11n+2m)*elem "
+                                  "(FP64 phase: refinement passes and CG at elem 4)",
+                    "mat_passes": last["mat_passes"][phase], "one_pass_floor_bytes": floor_bytes,
+                    "one_pass_floor_frac": floor_bytes / ks / 1e9 / peak,
+                    "dram_rate_gbs": None if traffic is None else traffic / ks / 1e9,
+                    "traffic_source": None if traffic is None else "ncu dram__bytes_read.sum+dram__bytes_write.sum "
+                                                                   "of this launch, digest-guarded constant"}
     # e2e through the public API with host buffers: setup (H2D of A,b,c) + solve + D2H of x,y,s
     e2e = None
     if args.e2e_steps > 0:
@@ -646,11 +843,21 @@ def main():
                "d2h_bytes_per_step": int(d2h), "includes": "scs_setup (validation, A^T build, H2D, g solve) + "
                                                             "scs_solve + D2H, host buffers"}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
-        val, det = oracle_baseline(prob, kw, W.c2_planted(seed=0, scale=0.02))
+    if orc_job is not None:
+        pool, res = orc_job
+        d = res.get(timeout=args.cpu_cap)
+        pool.close()
+        pool.join()
+        cpu = {"value": 1.0 / d["t_solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"whole FP64 oracle solves of the same instance to eps (setup + Algorithm 1), one "
+                         f"thread, run in a spawned process while the GPU part ran; median of {d['solves']}",
+               **d, **host_info()}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c3":
+        val, det = oracle_baseline(prob, kw, None, iters_needed=(fp64_info or last)["iters"])
         cpu = {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle, 1 thread: setup + 1 outer iteration on the full instance, scaled by the "
-                         "oracle's iteration count on the 0.02-scaled instance", **det}
+               "sample": "FP64 oracle, 1 thread: setup + 1 outer iteration on the full instance, times the GPU "
+                         "FP64 iteration count (a whole oracle solve of this SDP takes about an hour)",
+               **det, **host_info()}
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -664,6 +871,9 @@ def main():
             "time_to_eps_s": total_ms / args.steps / 1e3,
             "status": last["status"], "iters": last["iters"], "iters_fp32": last["iters_fp32"],
             "cg_iters": last["cg_iters"], "kkt": max(last["pr"], last["dr"], last["gap"]),
+            "cg_iters_fp32": last["cg_iters_fp32"], "mat_passes": list(last["mat_passes"]),
+            "cg_iters_ir": last["cg_iters_ir"], "mat_passes_ir": last["mat_passes_ir"], "ir_sweeps": last["ir_sweeps"],
+            "kernel_ms": [1e3 * last["kernel_s"][0], 1e3 * last["kernel_s"][1]],
             "pobj": last["pobj"], "err_vs_fp64": last.get("err_vs_fp64"),
             "fp64_time_to_eps_s": None if fp64_ms is None else fp64_ms / 1e3,
             "fp64_iters": None if fp64_info is None else fp64_info["iters"],

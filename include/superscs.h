@@ -117,6 +117,15 @@ typedef struct {
                                The block team always uses sliced ELL. */
     int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
                                after this many iterations is abandoned for the cold start */
+    int32_t mixed_resume;   /* SCS_MIXED, 1 (default): the FP64 phase continues Algorithm 1 from the
+                               FP32 phase's state -- its direction memory (AA pairs and Gram matrix,
+                               or the Broyden pairs), the pending secant pair, eta, eta0, r_safe and
+                               the outer index of q^nu; 0: it restarts Algorithm 1 from the FP32
+                               iterate */
+    int32_t mixed_refine;   /* SCS_MIXED, 1 (default): the FP64 phase solves each linear system of
+                               Sec. 4.1 by iterative refinement -- residuals with the FP64 matrix,
+                               corrections by CG with the FP32 copy -- so its FP64 work is a few
+                               sparse products per solve; 0: plain FP64 CG */
 } scs_settings;
 
 typedef struct {
@@ -140,6 +149,13 @@ typedef struct {
     int32_t warm_fallback_taken; /* 1 if the warm start was abandoned for the cold start */
     double kkt_fp32;        /* max(pr, dr, gap) of the FP32 phase's last termination test, evaluated
                                on FP32 data (SCS_MIXED; 0 otherwise) */
+    int64_t mat_passes_ir;  /* FP32 passes over A or A^T of the FP64 phase's refinement corrections */
+    int64_t cg_iters_ir;    /* FP32 CG iterations of those corrections (also counted in cg_iters) */
+    int64_t ir_sweeps;      /* correction solves of the FP64 phase's iterative refinement */
+    double batch_device_s;  /* scs_batch_solve: device time of the whole batch solve (both phases,
+                               hand-over, packing, copies to the host staging), CUDA events on the
+                               stream it runs on; the same in every instance's info */
+    int32_t team;           /* execution team that ran: SCS_TEAM_BLOCK (k_block) or SCS_TEAM_GRID (k_grid) */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
@@ -216,7 +232,9 @@ int scs_residuals_noalloc(int32_t m, int32_t n, const int64_t *Ap, const int32_t
 
 /* --- single operators of Eq. (drs), for checking one step at a time ------ */
 /* out = (I+Q)^{-1} r on N-vectors (Sec. 4.1, linear-system step of Eq. drs).
- * Uses and updates the work's CG warm start of slot 0 (u~) or 1 (d~). */
+ * Uses and updates the work's CG warm start of slot 0 (u~) or 1 (d~).  slot
+ * + 2 (works set up with SCS_MIXED): the FP64 solve by iterative refinement
+ * as the FP64 phase runs it (FP64 residuals, FP32 CG corrections). */
 int scs_linsys(scs_work *work, const double *r, double *out, int32_t slot);
 /* out = Pi_C(v), C = R^n x K* x R_+ (Sec. 3.1; projection step of Eq. drs). */
 int scs_project_cone(scs_work *work, const double *v, double *out);

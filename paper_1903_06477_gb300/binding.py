@@ -43,7 +43,7 @@ class Settings(C.Structure):
         ("aa_reg", C.c_double), ("team", C.c_int32), ("threads", C.c_int32),
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
-        ("warm_fallback", C.c_int32),
+        ("warm_fallback", C.c_int32), ("mixed_resume", C.c_int32), ("mixed_refine", C.c_int32),
     ]
 
 
@@ -56,7 +56,8 @@ class Info(C.Structure):
         ("err_vs_fp64", C.c_double), ("iters_fp32", C.c_int32), ("device_error", C.c_int32),
         ("kernel_s", C.c_double * 2), ("mat_passes", C.c_int64 * 2), ("cg_iters_fp32", C.c_int64),
         ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32), ("warm_fallback_taken", C.c_int32),
-        ("kkt_fp32", C.c_double),
+        ("kkt_fp32", C.c_double), ("mat_passes_ir", C.c_int64), ("cg_iters_ir", C.c_int64),
+        ("ir_sweeps", C.c_int64), ("batch_device_s", C.c_double), ("team", C.c_int32),
     ]
 
     def as_dict(self):

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(GRID_THREADS, 1) k_grid(const __grid_constant_
     // stream; for the column-blocked ring, "full" barriers (one arrival: the
     // producer's) at [0, CB_MAX_STAGES) and "empty" barriers (one arrival per
     // compute warp) at [CB_MAX_STAGES, 2 CB_MAX_STAGES)
-    const bool cb = a.P.A.cb.ncb > 0 || a.P.AT.cb.ncb > 0;
+    // (the FP32 copies the FP64 phase's refinement multiplies by count too)
+    const bool cb = a.P.A.cb.ncb > 0 || a.P.AT.cb.ncb > 0 || a.W.ir.A.cb.ncb > 0 || a.W.ir.AT.cb.ncb > 0;
     for (int i = threadIdx.x; i < 2 * MAX_WARPS; i += blockDim.x) {
         const bool empty = cb && i >= CB_MAX_STAGES && i < 2 * CB_MAX_STAGES;
         mbar_init(smem_addr(&sf.mbar[i]), empty ? (blockDim.x >> 5) - 1 : 1);

@@ -5,17 +5,37 @@ namespace sscs {
 
 // FP32 phase -> FP64 phase hand-over for a batch: one block per instance copies
 // the FP32 iterate (already FP64 in u_out) to the FP64 warm start and widens
-// the CG warm starts
-__global__ void k_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B)
+// the CG warm starts; with resume also the direction memory (mem columns of
+// Z and Xi), the pending secant pair and their tau entries
+__global__ void k_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B, int mem, int resume)
 {
     for (int i = blockIdx.x; i < B; i += gridDim.x) {
         const DevWork<float>& w32 = a32[i].W;
         const DevWork<double>& w64 = a64[i].W;
-        const int n = a64[i].P.n, N = n + a64[i].P.m + 1;
+        const int n = a64[i].P.n, nm = n + a64[i].P.m, N = nm + 1;
         for (int j = threadIdx.x; j < N; j += blockDim.x) w64.warm[j] = w32.u_out[j];
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             w64.ws[0][j] = (double)w32.ws[0][j];
             w64.ws[1][j] = (double)w32.ws[1][j];
+        }
+        if (resume) {
+            const long long cols = (long long)(mem > 0 ? mem : 1) * nm;
+            for (long long j = threadIdx.x; j < cols; j += blockDim.x) {
+                w64.Zv[j] = (double)w32.Zv[j];
+                w64.Xv[j] = (double)w32.Xv[j];
+            }
+            for (int j = threadIdx.x; j < nm; j += blockDim.x) {
+                w64.zp.v[j] = (double)w32.zp.v[j];
+                w64.xip.v[j] = (double)w32.xip.v[j];
+            }
+            for (int j = threadIdx.x; j < (mem > 0 ? mem : 1); j += blockDim.x) {
+                w64.Zt[j] = w32.Zt[j];
+                w64.Xt[j] = w32.Xt[j];
+            }
+            if (threadIdx.x == 0) {
+                *w64.zp.t = *w32.zp.t;
+                *w64.xip.t = *w32.xip.t;
+            }
         }
     }
 }
@@ -39,9 +59,10 @@ template const void* kblock_ptr<double>();
 template cudaError_t launch_block<double>(int, int, size_t, cudaStream_t, const Args<double>*, int, int*,
                                           const DevSettings&, int);
 
-cudaError_t launch_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B, cudaStream_t st)
+cudaError_t launch_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B, int mem, int resume,
+                                 cudaStream_t st)
 {
-    k_batch_handoff<<<std::min(B, 4096), 256, 0, st>>>(a32, a64, B);
+    k_batch_handoff<<<std::min(B, 4096), 256, 0, st>>>(a32, a64, B, mem, resume);
     return cudaGetLastError();
 }
 cudaError_t launch_batch_pack(const Args<double>* a64, int B, const long long* off, double* packed, cudaStream_t st)

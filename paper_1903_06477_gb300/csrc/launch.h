@@ -16,7 +16,8 @@ template <typename T>
 cudaError_t launch_block(int grid, int threads, size_t dyn, cudaStream_t st, const Args<T>* insts, int B, int* queue,
                          const DevSettings& S, int mode);
 cudaError_t launch_f2d(const float* in, double* out, long long n, cudaStream_t st);
-cudaError_t launch_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B, cudaStream_t st);
+cudaError_t launch_batch_handoff(const Args<float>* a32, const Args<double>* a64, int B, int mem, int resume,
+                                 cudaStream_t st);
 cudaError_t launch_batch_pack(const Args<double>* a64, int B, const long long* off, double* packed, cudaStream_t st);
 
 }  // namespace sscs

@@ -44,6 +44,20 @@ struct DevSettings {
     int keep_ws;           // 1: keep the CG warm starts found in ws (handed over by the FP32 phase)
     int warm_fallback;     // > 0 with a warm start: restart cold if ||Ru|| is not below the cold
                            // start's ||Ru0|| after this many iterations
+    int save_state;        // 1: write the loop state to W.res when the solve ends (FP32 phase of SCS_MIXED)
+    int resume;            // 1: continue from the loop state in W.res instead of starting Algorithm 1 afresh
+    int refine;            // 1 (FP64 data only): linear systems by iterative refinement, FP64 residuals
+                           // and FP32 CG corrections on the FP32 copy of A (W.ir)
+};
+
+// State of Algorithm 1 at the end of the FP32 phase of SCS_MIXED, so that the
+// FP64 phase continues the same iteration (direction memory, the K0/K1
+// references eta, eta0, r_safe and the outer index nu) instead of restarting.
+struct Resume {
+    int valid, count, have_pair, nu;
+    long long inserted;
+    double eta, eta0, r_safe, nz2;
+    double G[AAMAX * AAMAX];  // AA Gram matrix of the stored pairs
 };
 
 struct DevState {
@@ -55,6 +69,9 @@ struct DevState {
     double psd_resid;      // largest ||X V - V L||_F / ||X||_F of the FP32 eigensolves, in FP64
     int fallback;          // 1 if the warm start was abandoned for the cold start
     int pad2;
+    long long mat_passes_ir;  // FP32 passes of the refinement corrections (FP64 phase)
+    long long cg_iters_ir;    // FP32 CG iterations of the refinement corrections (FP64 phase)
+    long long ir_sweeps;      // refinement sweeps (FP32 correction solves)
 };
 
 // Column-blocked sliced ELL, the grid team's layout for large matrices.  CTA b
@@ -144,8 +161,18 @@ struct DevProb {
     const int* s_off;  // ns row offsets of the PSD blocks inside s
 };
 
+// Iterative refinement of the FP64 linear solves (SCS_MIXED, FP64 phase): the
+// FP32 copies of A and A^T and FP32 vectors for the correction solves.
+struct IrBufs {
+    Sell<float> A, AT;
+    float *r, *p, *q, *x;  // n
+    float* tm;             // m
+};
+
 template <typename T>
 struct DevWork {
+    IrBufs ir;
+    Resume* res;  // loop state handed from the FP32 to the FP64 phase (SCS_MIXED)
     HV<T> u, ut, ub, Ru, d, dt, wb, Rw, zp, xip, zt;
     T* g;       // n+m: g = M^{-1}(c, b)
     T* ws[2];   // CG warm starts (n) for the u~ and d~ systems
@@ -615,6 +642,89 @@ __device__ __forceinline__ void spmv2(const Team& tm, const Sell<T>& S, const T*
 }
 
 // ---------------------------------------------------------------------------
+// CG on (I + A^T A) x = rhs from the residual r = rhs - (I + A^T A) x of the
+// start x, rr = ||r||^2 (already reduced), stopping at ||r|| <= tol or after
+// cg_max iterations.  One reduction per iteration: <p,q>, <r,q>, <q,q> are
+// reduced together, ||r - alpha q||^2 = rr - 2 alpha <r,q> + alpha^2 <q,q>
+// gives beta, and x, r, p are updated in one pass; the exact ||r||^2 of the
+// updated r rides along with the next reduction and replaces the recurrence
+// value before it is used for alpha.  Returns the iterations.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CgBufs {
+    T *r, *p, *q;  // n
+    T* tm;         // m
+};
+
+template <typename T, class Team>
+__device__ int cg_loop(Team& tm, const Sell<T>& A, const Sell<T>& AT, int n, CgBufs<T> b, T* x, double rr,
+                       double tol, int cg_max)
+{
+    T* p = b.p;
+    T* q = b.q;
+    T* r = b.r;
+    T* tmv = b.tm;
+    for (int j = tm.rank(); j < n; j += tm.size()) p[j] = r[j];
+    tm.sync();
+    int it = 0;
+    T rr_part = 0;
+    bool have_part = false;
+    while (it < cg_max) {
+        if (tm.aborted()) break;
+        spmv(tm, A, p, [&](int i, T s) { tmv[i] = s; });
+        tm.sync();
+        T pq = 0, rq = 0, qq = 0;
+        spmv(tm, AT, tmv, [&](int j, T s) {
+            const T qj = p[j] + s;
+            q[j] = qj;
+            pq += p[j] * qj;
+            rq += r[j] * qj;
+            qq += qj * qj;
+        });
+        double red[4] = {(double)pq, (double)rq, (double)qq, (double)rr_part};
+        tm.reduce(red);
+        ++it;
+        // The scalar step (two FP64 divisions, a square root) is evaluated by
+        // one thread per CTA and handed to the others through shared memory:
+        // the FP64 pipe is a small fraction of the FP32 one, and every thread
+        // of every warp evaluating it costs more than the extra CTA barrier.
+        // The values are the same bits either way (rr lives in thread 0).
+        double* bc = tm.bcast();
+        if (threadIdx.x == 0) {
+            if (have_part) rr = red[3];
+            const double alpha = rr / red[0];
+            double rr_new = rr - 2.0 * alpha * red[1] + alpha * alpha * red[2];
+            if (rr_new < 0.0) rr_new = 0.0;
+            reinterpret_cast<T*>(bc)[0] = (T)alpha;
+            reinterpret_cast<T*>(bc)[1] = (T)(rr_new / rr);
+            reinterpret_cast<int*>(bc + 2)[0] = (!(sqrt(rr_new) > tol) || it >= cg_max) ? 1 : 0;
+            rr = rr_new;
+        }
+        __syncthreads();
+        const T ta = reinterpret_cast<const T*>(bc)[0];
+        const T tb = reinterpret_cast<const T*>(bc)[1];
+        const bool done = reinterpret_cast<const int*>(bc + 2)[0] != 0;
+        rr_part = 0;
+        if (done) {
+            for (int j = tm.rank(); j < n; j += tm.size()) x[j] += ta * p[j];
+        } else {
+            for (int j = tm.rank(); j < n; j += tm.size()) {
+                const T pj = p[j];
+                x[j] += ta * pj;
+                const T rj = r[j] - ta * q[j];
+                r[j] = rj;
+                p[j] = rj + tb * pj;
+                rr_part += rj * rj;
+            }
+        }
+        have_part = true;
+        tm.sync();
+        if (done) break;
+    }
+    return it;
+}
+
+// ---------------------------------------------------------------------------
 // M^{-1}(a, e) for M = [I A^T; -A I]: x = (I + A^T A)^{-1}(a - A^T e) by CG
 // warm-started from x (in place), y = e + A x written to W.py.  Returns the CG
 // iterations; htp = <c, x> + <b, y>.  CG stops when ||res|| <= rtol ||rhs||.
@@ -627,7 +737,6 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     const int n = P.n;
     T* tmv = W.tm;
     T* r = W.cr;
-    T* q = W.cq;
     spmv(tm, P.A, x, [&](int i, T s) { tmv[i] = s; });
     tm.sync();
     T acc_b = 0, acc_r = 0;
@@ -641,75 +750,14 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     double red2[2] = {(double)acc_b, (double)acc_r};
     tm.reduce(red2);
     const double rhs2 = red2[0];
-    double rr = red2[1];
+    const double rr = red2[1];
     const double tol = fmax(rtol * sqrt(rhs2), atol);
     int it = 0;
     if (rhs2 == 0.0) {
         for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
         tm.sync();
     } else if (sqrt(rr) > tol) {
-        // CG with one reduction per iteration: <p,q>, <r,q>, <q,q> are reduced
-        // together, ||r - alpha q||^2 = rr - 2 alpha <r,q> + alpha^2 <q,q> gives
-        // beta, and x, r, p are updated in one pass.  The exact ||r||^2 of the
-        // updated r rides along with the next reduction and replaces the
-        // recurrence value before it is used for alpha.
-        T* p = W.cp;
-        for (int j = tm.rank(); j < n; j += tm.size()) p[j] = r[j];
-        tm.sync();
-        T rr_part = 0;
-        bool have_part = false;
-        while (it < cg_max) {
-            if (tm.aborted()) break;
-            spmv(tm, P.A, p, [&](int i, T s) { tmv[i] = s; });
-            tm.sync();
-            T pq = 0, rq = 0, qq = 0;
-            spmv(tm, P.AT, tmv, [&](int j, T s) {
-                const T qj = p[j] + s;
-                q[j] = qj;
-                pq += p[j] * qj;
-                rq += r[j] * qj;
-                qq += qj * qj;
-            });
-            double red[4] = {(double)pq, (double)rq, (double)qq, (double)rr_part};
-            tm.reduce(red);
-            ++it;
-            // The scalar step (two FP64 divisions, a square root) is evaluated by
-            // one thread per CTA and handed to the others through shared memory:
-            // the FP64 pipe is a small fraction of the FP32 one, and every thread
-            // of every warp evaluating it costs more than the extra CTA barrier.
-            // The values are the same bits either way (rr lives in thread 0).
-            double* bc = tm.bcast();
-            if (threadIdx.x == 0) {
-                if (have_part) rr = red[3];
-                const double alpha = rr / red[0];
-                double rr_new = rr - 2.0 * alpha * red[1] + alpha * alpha * red[2];
-                if (rr_new < 0.0) rr_new = 0.0;
-                reinterpret_cast<T*>(bc)[0] = (T)alpha;
-                reinterpret_cast<T*>(bc)[1] = (T)(rr_new / rr);
-                reinterpret_cast<int*>(bc + 2)[0] = (!(sqrt(rr_new) > tol) || it >= cg_max) ? 1 : 0;
-                rr = rr_new;
-            }
-            __syncthreads();
-            const T ta = reinterpret_cast<const T*>(bc)[0];
-            const T tb = reinterpret_cast<const T*>(bc)[1];
-            const bool done = reinterpret_cast<const int*>(bc + 2)[0] != 0;
-            rr_part = 0;
-            if (done) {
-                for (int j = tm.rank(); j < n; j += tm.size()) x[j] += ta * p[j];
-            } else {
-                for (int j = tm.rank(); j < n; j += tm.size()) {
-                    const T pj = p[j];
-                    x[j] += ta * pj;
-                    const T rj = r[j] - ta * q[j];
-                    r[j] = rj;
-                    p[j] = rj + tb * pj;
-                    rr_part += rj * rj;
-                }
-            }
-            have_part = true;
-            tm.sync();
-            if (done) break;
-        }
+        it = cg_loop<T>(tm, P.A, P.AT, n, CgBufs<T>{r, W.cp, W.cq, tmv}, x, rr, tol, cg_max);
     }
     T hb = 0, hc = 0;
     T* py = W.py;
@@ -726,17 +774,130 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     return it;
 }
 
+// The same M^{-1}(a, e) in FP64 by iterative refinement (SCS_MIXED, FP64
+// phase): the residual r = rhs - (I + A^T A) x is formed in FP64 with the FP64
+// matrix, the correction solves (I + A^T A) dx = r / ||r|| in FP32 with the
+// FP32 copy of A by the same CG from dx = 0, and x += ||r|| dx in FP64; then
+// the FP64 residual is formed again, until ||r|| <= tol.  Where the requested
+// accuracy relative to ||r|| is looser than IR_VERIFY (the solves inside the
+// loop under cg_adapt) one correction is taken without the checking residual:
+// its FP32 rounding (about 1e-7 of ||r|| times the growth of the products) is
+// far below what was asked.  Each correction is asked for at most IR_FLOOR
+// relative accuracy, about what FP32 CG reaches reliably.  Returns the FP32
+// CG iterations.
+constexpr double IR_VERIFY = 1e-3;
+constexpr double IR_FLOOR = 1e-5;
+constexpr int IR_MAX_SWEEPS = 6;
+
+template <class Team>
+__device__ int minv_ir(Team& tm, const DevProb<double>& P, const DevWork<double>& W, const double* a,
+                       const double* e, double* x, double rtol, int cg_max, double& htp, double atol)
+{
+    const int n = P.n;
+    double* tmv = W.tm;
+    double* r = W.cr;
+    double* rhs = W.tn;
+    const IrBufs& ir = W.ir;
+    spmv(tm, P.A, x, [&](int i, double s) { tmv[i] = s; });
+    tm.sync();
+    double acc_b = 0, acc_r = 0;
+    spmv2(tm, P.AT, e, tmv, [&](int j, double s1, double s2) {
+        const double rh = a[j] - s1;
+        const double res = rh - x[j] - s2;
+        rhs[j] = rh;
+        r[j] = res;
+        acc_b += rh * rh;
+        acc_r += res * res;
+    });
+    double red2[2] = {acc_b, acc_r};
+    tm.reduce(red2);
+    const double rhs2 = red2[0];
+    double rr = red2[1];
+    const double tol = fmax(rtol * sqrt(rhs2), atol);
+    long long passes64 = 3, passes32 = 0, sweeps = 0;
+    int it = 0;
+    if (rhs2 == 0.0) {
+        for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
+        tm.sync();
+    } else {
+        for (int sw = 0; sw < IR_MAX_SWEEPS && sqrt(rr) > tol && it < cg_max && !tm.aborted(); ++sw) {
+            const double nr = sqrt(rr);
+            const double want = tol / nr;  // relative accuracy asked of this correction
+            // the scaled residual in FP32, the correction from zero
+            float acc32 = 0.f;
+            const double inv = 1.0 / nr;
+            for (int j = tm.rank(); j < n; j += tm.size()) {
+                const float rj = (float)(r[j] * inv);
+                ir.r[j] = rj;
+                ir.x[j] = 0.f;
+                acc32 += rj * rj;
+            }
+            double red3[1] = {(double)acc32};
+            tm.reduce(red3);
+            const int k = cg_loop<float>(tm, ir.A, ir.AT, n, CgBufs<float>{ir.r, ir.p, ir.q, ir.tm}, ir.x, red3[0],
+                                         fmax(want, IR_FLOOR) * sqrt(red3[0]), cg_max - it);
+            it += k;
+            passes32 += 2 * k;
+            ++sweeps;
+            if (want >= IR_VERIFY) {
+                for (int j = tm.rank(); j < n; j += tm.size()) x[j] += nr * (double)ir.x[j];
+                tm.sync();
+                break;
+            }
+            for (int j = tm.rank(); j < n; j += tm.size()) x[j] += nr * (double)ir.x[j];
+            tm.sync();
+            // FP64 residual of the corrected x
+            spmv(tm, P.A, x, [&](int i, double s) { tmv[i] = s; });
+            tm.sync();
+            double acc = 0;
+            spmv(tm, P.AT, tmv, [&](int j, double s) {
+                const double res = rhs[j] - x[j] - s;
+                r[j] = res;
+                acc += res * res;
+            });
+            double red4[1] = {acc};
+            tm.reduce(red4);
+            rr = red4[0];
+            passes64 += 2;
+        }
+    }
+    double hb = 0, hc = 0;
+    double* py = W.py;
+    spmv(tm, P.A, x, [&](int i, double s) {
+        const double yi = e[i] + s;
+        py[i] = yi;
+        hb += ro(P.b + i) * yi;
+    });
+    for (int j = tm.rank(); j < n; j += tm.size()) hc += ro(P.c + j) * x[j];
+    double red5[2] = {hb, hc};
+    tm.reduce(red5);
+    htp = red5[0] + red5[1];
+    if (tm.leader()) {
+        W.st->mat_passes += passes64 + 1;
+        W.st->mat_passes_ir += passes32;
+        W.st->cg_iters_ir += it;
+        W.st->ir_sweeps += sweeps;
+    }
+    return it;
+}
+
 // out = (I+Q)^{-1} r via tau = (r_tau + h^T M^{-1} r) / (1 + h^T g), (x,y) = M^{-1} r - tau g.
 // r and out must not share storage of the bulk part.
 template <typename T, class Team>
 __device__ int linsys(Team& tm, const DevProb<T>& P, const DevWork<T>& W, HV<T> r, HV<T> out, int slot,
-                      double rtol, int cg_max, double hg, double atol = 0.0)
+                      double rtol, int cg_max, double hg, double atol = 0.0, bool refine = false)
 {
     const int n = P.n, m = P.m;
     const double rtau = *r.t;
     T* x = W.ws[slot];
     double htp;
-    const int it = minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol);
+    int it;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        it = refine ? minv_ir(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol)
+                    : minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol);
+    } else {
+        it = minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol);
+    }
     const double tau = (rtau + htp) / (1.0 + hg);
     const T tt = (T)tau;
     for (int i = tm.rank(); i < n; i += tm.size()) out.v[i] = x[i] - tt * W.g[i];
@@ -1539,6 +1700,9 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         }
     if (tm.leader() && iter_base == 0) {
         W.st->mat_passes = 0;
+        W.st->mat_passes_ir = 0;
+        W.st->cg_iters_ir = 0;
+        W.st->ir_sweeps = 0;
         W.st->psd_resid = 0.0;
         W.st->fallback = 0;
     }
@@ -1549,7 +1713,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = T(0);
         if (tm.leader()) *W.u.t = 1.0;
         tm.sync();
-        cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+        cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, 0.0, S.refine != 0);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
         project_pass(tm, P, op, psd, &W.st->psd_resid);
         double red[1] = {(double)op.acc0};
@@ -1560,7 +1724,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
     for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = use_warm ? (T)W.warm[i] : T(0);
     if (tm.leader()) *W.u.t = use_warm ? W.warm[nm] : 1.0;
     tm.sync();
-    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg);
+    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, 0.0, S.refine != 0);
     double nRu;
     {
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
@@ -1569,10 +1733,28 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         tm.reduce(red);
         nRu = sqrt(red[0]);
     }
-    const double eta0 = nRu;
-    double r_safe = eta0, eta = eta0, nz2 = 0.0;
+    double eta0 = nRu, r_safe = nRu, eta = nRu, nz2 = 0.0;
     bool have_pair = false;
     DirState ds{0, 0};
+    int nu_q = 0;  // outer iterations before this launch (the exponent of q^nu continues)
+    if (S.resume && W.res->valid) {
+        // continue the FP32 phase's iteration: its direction memory (Z, Xi and
+        // the pending secant pair were widened by the hand-over), the Gram
+        // matrix, and the K0/K1 references; u~, u_ and Ru were just evaluated
+        // in this precision at the handed-over u
+        const Resume* R = W.res;
+        eta0 = R->eta0;
+        eta = R->eta;
+        r_safe = R->r_safe;
+        nz2 = R->nz2;
+        have_pair = R->have_pair != 0;
+        ds.count = R->count;
+        ds.inserted = R->inserted;
+        nu_q = R->nu;
+        if (S.direction == 0)
+            for (int i = threadIdx.x; i < AAMAX * AAMAX; i += blockDim.x) G[i] = R->G[i];
+        __syncthreads();
+    }
     int status = ST_MAX_ITERS;
     TermOut to;
     to.pr = to.dr = to.gap = to.ic = to.uc = INFINITY;
@@ -1640,7 +1822,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             tm.sync();
         }
         const double atol = S.cg_adapt > 0.0 ? S.cg_adapt * nRu : 0.0;
-        cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg, atol);
+        cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg, atol, S.refine != 0);
         if (nRu <= S.c0 * eta) {
             // K0
             eta = nRu;
@@ -1663,7 +1845,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
                 const double rho = red[1];
                 if ((nRu <= r_safe && nRw <= S.c1 * nRu) || nRw == 0.0) {
                     // K1: u <- w, reuse w~, w_, Rw
-                    r_safe = nRw + pow(S.q, (double)nu) * eta0;
+                    r_safe = nRw + pow(S.q, (double)(nu + nu_q)) * eta0;
                     const T ta = (T)alpha;
                     T zz = 0;
                     for (int i = tm.rank(); i < nm; i += tm.size()) {
@@ -1714,7 +1896,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
                     }
                     tm.reduce(red2);
                     nz2 = red2[0];
-                    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol);
+                    cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol, S.refine != 0);
                     OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
                     project_pass(tm, P, opr, psd, &W.st->psd_resid);
                     double red3[1] = {(double)opr.acc0};
@@ -1732,6 +1914,23 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
     if (need_final_check && !tm.aborted()) {
         const int st = termination(tm, P, W, S.eps, 0.0, to);
         if (st != 0 && status != ST_NUMERICAL) status = st;
+    }
+    if (S.save_state) {
+        // the loop state for a continuation in FP64 (the vectors stay in W)
+        Resume* R = W.res;
+        if (tm.leader()) {
+            R->valid = 1;
+            R->count = ds.count;
+            R->inserted = ds.inserted;
+            R->have_pair = have_pair ? 1 : 0;
+            R->nu = nu + nu_q;
+            R->eta = eta;
+            R->eta0 = eta0;
+            R->r_safe = r_safe;
+            R->nz2 = nz2;
+        }
+        if (tm.block() == 0 && S.direction == 0)
+            for (int i = threadIdx.x; i < AAMAX * AAMAX; i += blockDim.x) R->G[i] = G[i];
     }
     write_outputs(tm, P, W, status, to);
     iters_out = iter_base + nu;
@@ -1933,7 +2132,8 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
     if (tm.leader()) *W.u.t = W.io_in[nm];
     tm.sync();
     if (mode == MODE_LINSYS) {
-        linsys(tm, P, W, W.u, W.ut, slot, S.cg_rtol, S.cg_max, W.st->hg);
+        // slot 0 / 1: the CG warm start of u~ / d~; + 2: by iterative refinement (FP64 data only)
+        linsys(tm, P, W, W.u, W.ut, slot & 1, S.cg_rtol, S.cg_max, W.st->hg, 0.0, (slot & 2) != 0);
         for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ut.v[i];
         if (tm.leader()) W.io_out[nm] = *W.ut.t;
     } else if (mode == MODE_PROJECT) {

@@ -495,6 +495,34 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     W.bar = A.take<unsigned>(4);
     W.abort_flag = A.take<int>(4);
     W.st = st_ext ? st_ext : A.take<DevState>(1);
+    W.res = A.take<Resume>(1);
+    W.ir = IrBufs{};
+}
+
+// The FP64 phase of SCS_MIXED reads the FP32 phase's loop state (one shared
+// record) and refines its linear solves with the FP32 copy of A and the FP32
+// phase's CG vectors, which are idle by then.
+static void link_phases(const DevProb<float>& P32, DevWork<float>& W32, DevWork<double>& W64)
+{
+    W32.res = W64.res;
+    W64.ir = IrBufs{P32.A, P32.AT, W32.cr, W32.cp, W32.cq, W32.tn, W32.tm};
+}
+
+// Widens the FP32 phase's direction memory (mem columns of Z and Xi), the
+// pending secant pair and their FP64 tau entries into the FP64 work.
+static cudaError_t widen_memory(const DevWork<float>& W32, const DevWork<double>& W64, int mem, int nm, cudaStream_t st)
+{
+    const long long cols = (long long)std::max(mem, 1) * nm;
+    cudaError_t e;
+    if ((e = launch_f2d(W32.Zv, W64.Zv, cols, st)) != cudaSuccess) return e;
+    if ((e = launch_f2d(W32.Xv, W64.Xv, cols, st)) != cudaSuccess) return e;
+    if ((e = launch_f2d(W32.zp.v, W64.zp.v, nm, st)) != cudaSuccess) return e;
+    if ((e = launch_f2d(W32.xip.v, W64.xip.v, nm, st)) != cudaSuccess) return e;
+    const size_t tb = sizeof(double) * std::max(mem, 1);
+    if ((e = cudaMemcpyAsync(W64.Zt, W32.Zt, tb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(W64.Xt, W32.Xt, tb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(W64.zp.t, W32.zp.t, sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(W64.xip.t, W32.xip.t, sizeof(double), cudaMemcpyDeviceToDevice, st);
 }
 
 template <typename T>
@@ -577,6 +605,9 @@ static DevSettings dev_settings(const scs_settings* S)
     D.cg_adapt = S->cg_adapt;
     D.keep_ws = 0;
     D.warm_fallback = S->warm_fallback;
+    D.save_state = 0;
+    D.resume = 0;
+    D.refine = 0;
     return D;
 }
 
@@ -691,6 +722,8 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->cg_adapt = 0.0;
     o->spmv_path = 0;
     o->warm_fallback = 0;
+    o->mixed_resume = 1;
+    o->mixed_refine = 1;
     return SCS_OK;
 }
 
@@ -788,6 +821,8 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     }
     w->D.dyn64 = std::max({dyn_smem<double>(H, w->D.threads, tma), H.cA64.dyn(), H.cAT64.dyn()});
     w->D.dyn32 = w->has32 ? std::max({dyn_smem<float>(H, w->D.threads, tma), H.cA32.dyn(), H.cAT32.dyn()}) : 0;
+    // the FP64 phase of SCS_MIXED also runs FP32 products (refinement corrections)
+    if (w->has32) w->D.dyn64 = std::max(w->D.dyn64, w->D.dyn32);
     int rc2 = config_kernels<double>(w->D.dyn64, w->err);
     if (!rc2 && w->has32) rc2 = config_kernels<float>(w->D.dyn32, w->err);
     if (rc2) { memcpy(g_err, w->err, 512); delete w; return rc2; }
@@ -839,6 +874,7 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
         w->P32.q_off = w->P64.q_off;
         w->P32.s_dim = w->P64.s_dim;
         w->P32.s_off = w->P64.s_off;
+        link_phases(w->P32, w->W32, w->W64);
     }
     w->dargs64 = A.take<Args<double>>(1);
     w->dargs32 = A.take<Args<float>>(1);
@@ -892,6 +928,9 @@ static void fill_info(scs_info* info, const DevState& s)
     info->uc = s.uc;
     info->pobj = s.pobj;
     info->dobj = s.dobj;
+    info->mat_passes_ir = s.mat_passes_ir;
+    info->cg_iters_ir = s.cg_iters_ir;
+    info->ir_sweeps = s.ir_sweeps;
 }
 
 extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info* info)
@@ -916,6 +955,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         S32.stall_iters = w->S.mixed_stall;
         S32.switch_kkt = w->S.mixed_switch;
         S32.max_iters = w->S.mixed_max_iters > 0 ? std::min(w->S.mixed_max_iters, w->S.max_iters) : w->S.max_iters;
+        S32.save_state = w->S.mixed_resume ? 1 : 0;
         if (S.use_warm) CU(cudaMemcpyAsync(w->W32.warm, w->W64.warm, sizeof(double) * N, cudaMemcpyDeviceToDevice, w->stream), w->err);
         Args<float> a32 = make_args(w->P32, w->W32, S32, MODE_SOLVE);
         CU(cudaEventRecord(w->ev[2], w->stream), w->err);
@@ -926,9 +966,12 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         for (int k = 0; k < 2; ++k) {
             CU(launch_f2d(w->W32.ws[k], w->W64.ws[k], H.n, w->stream), w->err);
         }
+        if (w->S.mixed_resume) CU(widen_memory(w->W32, w->W64, w->S.mem, H.n + H.m, w->stream), w->err);
         S.use_warm = 1;
         S.keep_ws = 1;
         S.warm_fallback = 0;
+        S.resume = w->S.mixed_resume ? 1 : 0;
+        S.refine = w->S.mixed_refine ? 1 : 0;
         CU(cudaMemcpyAsync(&st32, w->W32.st, sizeof(DevState), cudaMemcpyDeviceToHost, w->stream), w->err);
     }
     Args<double> a = make_args(w->P64, w->W64, S, MODE_SOLVE);
@@ -963,6 +1006,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
         info->solve_s = now_s() - t0;
         info->device_error = abort_flag | abort32;
         info->threads_per_block = w->D.threads;
+        info->team = w->D.team;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w->ev[0], w->ev[1]) == cudaSuccess) info->kernel_s[0] = ms * 1e-3;
         cudaGetLastError();
@@ -1127,7 +1171,9 @@ extern "C" int scs_residuals(scs_work* w, const double* x, const double* y, cons
 
 extern "C" int scs_linsys(scs_work* w, const double* r, double* out, int32_t slot)
 {
-    return single_op(w, MODE_LINSYS, slot ? 1 : 0, r, out, nullptr);
+    if (!w || slot < 0 || slot > 3) { set_err(w ? w->err : g_err, "bad arguments"); return SCS_EINVAL; }
+    if ((slot & 2) && !w->has32) { set_err(w->err, "refinement needs a work set up with SCS_MIXED"); return SCS_EINVAL; }
+    return single_op(w, MODE_LINSYS, slot, r, out, nullptr);
 }
 extern "C" int scs_project_cone(scs_work* w, const double* v, double* out)
 {
@@ -1176,6 +1222,7 @@ struct scs_batch {
     DevState* hst = nullptr;    // pinned host staging (2B states)
     int* queue = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_all[2] = {nullptr, nullptr};  // around the whole solve, on the stream it runs on
     char err[512];
     double setup_s = 0;
     double tune_ms[4] = {0, 0, 0, 0};
@@ -1197,6 +1244,7 @@ static DevSettings batch_settings(const scs_batch* b, bool first_phase_of_mixed)
         S.stall_iters = b->S.mixed_stall;
         S.switch_kkt = b->S.mixed_switch;
         S.max_iters = b->S.mixed_max_iters > 0 ? std::min(b->S.mixed_max_iters, b->S.max_iters) : b->S.max_iters;
+        S.save_state = b->S.mixed_resume ? 1 : 0;
     }
     return S;
 }
@@ -1287,6 +1335,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
     for (auto& h : b->H) any_psd |= !h.s.empty();
     b->dyn64 = any_psd ? psd_smem_bytes<double>() : 0;
     b->dyn32 = any_psd && b->has32 ? psd_smem_bytes<float>() : 0;
+    if (b->has32) b->dyn64 = std::max(b->dyn64, b->dyn32);
     if ((rc = config_kernels<double>(b->dyn64, b->err)) || (b->has32 && (rc = config_kernels<float>(b->dyn32, b->err)))) {
         memcpy(g_err, b->err, 512);
         delete b;
@@ -1332,6 +1381,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
                         p.A.val = b->a32[0].P.A.val;
                         p.AT.val = b->a32[0].P.AT.val;
                     }
+                    link_phases(p, b->a32[qi].W, b->a64[qi].W);
                 }
             }
         }
@@ -1370,6 +1420,8 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
         return fail(SCS_ENOMEM);
     }
     for (auto& e : b->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { set_err(b->err, "cudaEventCreate failed"); return fail(SCS_ECUDA); }
+    for (auto& e : b->ev_all)
         if (cudaEventCreate(&e) != cudaSuccess) { set_err(b->err, "cudaEventCreate failed"); return fail(SCS_ECUDA); }
     A.off = 0;
     A.base = b->arena;
@@ -1481,6 +1533,8 @@ extern "C" void scs_batch_finish(scs_batch* b)
     if (b->gev) cudaEventDestroy(b->gev);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : b->ev_all)
+        if (e) cudaEventDestroy(e);
     if (b->hpacked) cudaFreeHost(b->hpacked);
     if (b->hst) cudaFreeHost(b->hst);
     if (b->arena) cudaFree(b->arena);
@@ -1506,13 +1560,15 @@ static int batch_enqueue(scs_batch* b, cudaStream_t st, int g32, int g64, bool c
         CU(rec(b->ev[2]), b->err);
         CU(launch_block<float>(g32, b->threads, b->dyn32, st, b->d32, B, b->queue, S32, MODE_SOLVE), b->err);
         CU(rec(b->ev[3]), b->err);
-        CU(launch_batch_handoff(b->d32, b->d64, B, st), b->err);
+        CU(launch_batch_handoff(b->d32, b->d64, B, b->S.mem, b->S.mixed_resume ? 1 : 0, st), b->err);
     }
     DevSettings S = batch_settings<double>(b, false);
     if (b->has32) {
         S.use_warm = 1;
         S.keep_ws = 1;
         S.warm_fallback = 0;
+        S.resume = b->S.mixed_resume ? 1 : 0;
+        S.refine = b->S.mixed_refine ? 1 : 0;
     } else {
         S.use_warm = b->use_warm ? 1 : 0;
     }
@@ -1581,13 +1637,19 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
     if (batch_graph(b, g32, g64) == SCS_OK) {
         CU(cudaEventRecord(b->gev, b->stream), b->err);
         CU(cudaStreamWaitEvent(b->gstream, b->gev, 0), b->err);
+        CU(cudaEventRecord(b->ev_all[0], b->gstream), b->err);
         CU(cudaGraphLaunch(b->gexec, b->gstream), b->err);
+        CU(cudaEventRecord(b->ev_all[1], b->gstream), b->err);
         CU(cudaStreamSynchronize(b->gstream), b->err);
     } else {
+        CU(cudaEventRecord(b->ev_all[0], b->stream), b->err);
         int rc = batch_enqueue(b, b->stream, g32, g64, false);
         if (rc) return rc;
+        CU(cudaEventRecord(b->ev_all[1], b->stream), b->err);
     }
     CU(cudaStreamSynchronize(b->stream), b->err);
+    float ms_all = 0.f;
+    if (cudaEventElapsedTime(&ms_all, b->ev_all[0], b->ev_all[1]) != cudaSuccess) ms_all = 0.f;
     if (cudaEventElapsedTime(&ms64, b->ev[0], b->ev[1]) != cudaSuccess) ms64 = 0.f;
     if (b->has32 && cudaEventElapsedTime(&ms32, b->ev[2], b->ev[3]) != cudaSuccess) ms32 = 0.f;
     cudaGetLastError();  // a failed timing query must not surface in a later error check
@@ -1626,7 +1688,9 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
             }
             info->setup_s = b->setup_s;
             info->solve_s = el;
+            info->batch_device_s = ms_all * 1e-3;
             info->threads_per_block = b->threads;
+            info->team = SCS_TEAM_BLOCK;
         }
     }
     return SCS_OK;

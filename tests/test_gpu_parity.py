@@ -165,6 +165,44 @@ def test_infeasible_and_unbounded(team):
 
 
 @pytest.mark.parametrize("team", TEAMS)
+@pytest.mark.parametrize("name", list(PROBS))
+def test_refined_linsys_matches_oracle(name, team):
+    """(I+Q)^{-1} by iterative refinement (FP64 residuals, FP32 CG corrections
+    with the FP32 copy of A) reaches the same FP64 solution as plain CG."""
+    prob = PROBS[name]
+    work = B.Work(prob, team=team, precision=B.MIXED, cg_rtol=1e-14, cg_max=5000)
+    orc = O.Oracle(prob, cg_rtol=1e-14, cg_max=5000)
+    rng = np.random.default_rng(11)
+    for slot in (0, 1, 0):
+        r = rng.standard_normal(work.N) * 3
+        out = work.linsys(r, slot=slot + 2)
+        ref = orc.linsys(r, slot=slot)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-9 * (1 + np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("team", TEAMS)
+@pytest.mark.parametrize("resume,refine", [(1, 1), (0, 0), (1, 0), (0, 1)])
+def test_mixed_handover_modes(team, resume, refine):
+    """Every combination of the FP32 -> FP64 hand-over (resume the loop state
+    or restart) and of the FP64 phase's linear solves (refinement or plain
+    FP64 CG) ends at the FP64 tolerance with the planted objective."""
+    prob = W.c2_planted(seed=2, scale=0.02)
+    eps = 1e-6
+    work = B.Work(prob, team=team, precision=B.MIXED, eps=eps, max_iters=20000, cg_adapt=1e-2,
+                  mixed_switch=1e-5, mixed_resume=resume, mixed_refine=refine)
+    x, y, s, info = work.solve()
+    assert info["status"] == B.SOLVED, info
+    pr, dr, gap = _kkt(prob, x, y, s)
+    assert max(pr, dr, gap) <= eps * 1.01
+    pstar = prob["c"] @ prob["xstar"]
+    assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+    if refine and info["iters"] > info["iters_fp32"]:
+        assert info["ir_sweeps"] > 0 and info["mat_passes_ir"] > 0, info
+    if not refine:
+        assert info["ir_sweeps"] == 0 and info["mat_passes_ir"] == 0, info
+
+
+@pytest.mark.parametrize("team", TEAMS)
 def test_mixed_precision_reaches_fp64_tolerance(team):
     prob = W.c2_planted(seed=2, scale=0.02)
     eps = 1e-6
