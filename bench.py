@@ -873,6 +873,7 @@ def main():
             "cg_iters": last["cg_iters"], "kkt": max(last["pr"], last["dr"], last["gap"]),
             "cg_iters_fp32": last["cg_iters_fp32"], "mat_passes": list(last["mat_passes"]),
             "cg_iters_ir": last["cg_iters_ir"], "mat_passes_ir": last["mat_passes_ir"], "ir_sweeps": last["ir_sweeps"],
+            "kkt_fp32": last["kkt_fp32"], "steps_k0_k1_k2_bt": [last["k0"], last["k1"], last["k2"], last["backtracks"]],
             "kernel_ms": [1e3 * last["kernel_s"][0], 1e3 * last["kernel_s"][1]],
             "pobj": last["pobj"], "err_vs_fp64": last.get("err_vs_fp64"),
             "fp64_time_to_eps_s": None if fp64_ms is None else fp64_ms / 1e3,

@@ -12,7 +12,8 @@
  * (Sec. 4.4).  Every step runs in hand-written CUDA kernels for sm_103a.
  *
  * Conventions
- *  - Cone rows of s are ordered [ f zero | l orthant | q SOCs | s PSDs ].
+ *  - Cone rows of s are ordered [ f zero | l orthant | q SOCs | s PSDs |
+ *    ep primal exponential cones | ed dual exponential cones ].
  *    An SOC block (x, t) stores t LAST (Sec. 2, cone (iii)).  A PSD block of
  *    order d occupies d(d+1)/2 rows holding svec(X): lower triangle, column
  *    by column, off-diagonal entries multiplied by sqrt(2) (Sec. 2, map mat).
@@ -70,6 +71,10 @@ typedef struct {
     const int32_t *q;    /* SOC dimensions, each >= 1 (Sec. 2 cone (iii)) */
     int32_t ns;          /* number of PSD blocks */
     const int32_t *s;    /* PSD orders d, each 1..64 (Sec. 2 cone (ii)) */
+    int32_t ep;          /* primal exponential cones (Sec. 2 cone (v)), 3 rows each:
+                            (x1, x2, x3) with x1 >= x2 exp(x3 / x2), x2 > 0, closure */
+    int32_t ed;          /* dual exponential cones, 3 rows each: (y1, y2, y3) with
+                            -y3 exp(y2 / y3) <= e y1, y3 < 0, closure */
 } scs_cone;
 
 typedef struct {

@@ -47,6 +47,7 @@ class _Problem(C.Structure):
         ("f", C.c_int32), ("l", C.c_int32),
         ("nq", C.c_int32), ("q", C.POINTER(C.c_int32)),
         ("ns", C.c_int32), ("s", C.POINTER(C.c_int32)),
+        ("ep", C.c_int32), ("ed", C.c_int32),
     ]
 
 
@@ -92,6 +93,10 @@ def lib():
         L.orc_proj_soc.argtypes = [dp, C.c_int32]
         L.orc_jacobi_eig.argtypes = [C.c_int32, dp, dp, dp]
         L.orc_proj_psd.argtypes = [dp, C.c_int32]
+        L.orc_proj_exp.argtypes = [dp]
+        L.orc_proj_exp_dual.argtypes = [dp]
+        L.orc_in_exp.argtypes = [dp, C.c_double]
+        L.orc_in_exp_dual.argtypes = [dp, C.c_double]
         L.orc_svec_to_mat.argtypes = [C.c_int32, dp, dp]
         L.orc_mat_to_svec.argtypes = [C.c_int32, dp, dp]
         for name in ("orc_proj_dual_cone", "orc_proj_primal_cone"):
@@ -174,6 +179,7 @@ class Oracle:
             _dp(k["b"]), _dp(k["c"]),
             int(prob.get("f", 0)), int(prob.get("l", 0)),
             len(prob.get("q", [])), _ip(k["q"]), len(prob.get("s", [])), _ip(k["s"]),
+            int(prob.get("ep", 0)), int(prob.get("ed", 0)),
         )
         st = dict(DEFAULTS)
         warm = settings.pop("warm_u", None)
@@ -259,6 +265,27 @@ def proj_soc(z):
     z = np.array(z, dtype=np.float64, copy=True)
     lib().orc_proj_soc(_dp(z), len(z))
     return z
+
+
+def proj_exp(v):
+    """Pi on the exponential cone of Sec. 2, cone (v), order (x1, x2, x3)."""
+    v = np.array(v, dtype=np.float64, copy=True)
+    lib().orc_proj_exp(_dp(v))
+    return v
+
+
+def proj_exp_dual(v):
+    v = np.array(v, dtype=np.float64, copy=True)
+    lib().orc_proj_exp_dual(_dp(v))
+    return v
+
+
+def in_exp(v, tol=0.0):
+    return bool(lib().orc_in_exp(_dp(np.ascontiguousarray(v, dtype=np.float64)), tol))
+
+
+def in_exp_dual(v, tol=0.0):
+    return bool(lib().orc_in_exp_dual(_dp(np.ascontiguousarray(v, dtype=np.float64)), tol))
 
 
 def proj_psd(v, d):

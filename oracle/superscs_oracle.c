@@ -10,6 +10,7 @@
  * blocking or fusion.  Where the paper is silent, the reading taken is given
  * in the comment above the routine.
  */
+#define _GNU_SOURCE
 #include "superscs_oracle.h"
 
 #include <math.h>
@@ -66,6 +67,146 @@ void orc_proj_soc(double *z, int32_t dim)
     double a = (nx + t) / (2.0 * nx);
     for (int32_t i = 0; i < dim - 1; ++i) z[i] *= a;
     z[dim - 1] = a * nx;
+}
+
+/* Exponential cone K^e = cl{(x1,x2,x3) : x1 >= x2 exp(x3/x2), x2 > 0} (Sec. 2,
+ * cone (v)).  Below a point is named by (r, s, t) = (x3, x2, x1), so K^e =
+ * cl{s exp(r/s) <= t, s > 0} and its dual (K^e)* = cl{(u, v, w) : u < 0,
+ * -u exp(v/u) <= e w} in the same roles (u = y3, v = y2, w = y1).
+ *
+ * Projection of a point outside K^e and outside its polar -(K^e)*: the
+ * nearest point of K^e lies on its boundary, which is the face {s = 0, r <= 0,
+ * t >= 0} together with the rays {c (rho, 1, e^rho) : c >= 0}.  The nearest
+ * point of the face is (min(r,0), 0, max(t,0)).  On the ray of slope rho the
+ * nearest point is c a with a = (rho, 1, e^rho) and c = <v,a>/|a|^2; the
+ * distance is stationary in rho exactly where
+ *   F(rho) = r (1 + (1-rho) e^{2 rho}) - s (rho + e^{2 rho}) + t e^rho (rho^2 - rho + 1)
+ * vanishes (the derivative of <v,a>^2/|a|^2, cleared of positive factors).
+ * The oracle collects every candidate -- the face point, the origin, and the
+ * point of every root of F with c > 0, found by scanning rho on a fine grid
+ * and bisecting each sign change -- all of which lie in K^e, and returns the
+ * nearest.  F is evaluated as F e^{-2 rho} for rho > 0 (same sign, no
+ * overflow); roots beyond the grid are bracketed by doubling. */
+static double exp_F(double rho, double r, double s, double t)
+{
+    if (rho <= 0.0) {
+        const double e = exp(rho), e2 = e * e;
+        return r * (1.0 + (1.0 - rho) * e2) - s * (rho + e2) + t * e * (rho * rho - rho + 1.0);
+    }
+    const double em = exp(-rho), em2 = em * em;
+    return r * ((1.0 - rho) + em2) - s * (rho * em2 + 1.0) + t * em * (rho * rho - rho + 1.0);
+}
+
+/* the point c a of the ray of slope rho nearest to (r,s,t), as (r,s,t); 0 if c <= 0 */
+static int exp_ray_point(double rho, double r, double s, double t, double *pr, double *ps, double *pt)
+{
+    double a0, a1, a2;  /* a scaled by max(1, e^rho)^-1 */
+    if (rho <= 0.0) { a0 = rho; a1 = 1.0; a2 = exp(rho); }
+    else { const double em = exp(-rho); a0 = rho * em; a1 = em; a2 = 1.0; }
+    const double c = (r * a0 + s * a1 + t * a2) / (a0 * a0 + a1 * a1 + a2 * a2);
+    if (!(c > 0.0)) return 0;
+    *pr = c * a0; *ps = c * a1; *pt = c * a2;
+    return 1;
+}
+
+static double exp_bisect(double lo, double hi, double r, double s, double t)
+{
+    double flo = exp_F(lo, r, s, t);
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = exp_F(mid, r, s, t);
+        if (fm == 0.0) return mid;
+        if ((fm > 0.0) == (flo > 0.0)) { lo = mid; flo = fm; } else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int exp_member(double r, double s, double t, double tol)
+{
+    if (s > 0.0) return s * exp(r / s) <= t + tol;   /* exp overflow gives +inf: outside */
+    return s >= -tol && r <= tol && t >= -tol;
+}
+static int exp_dual_member(double u, double v, double w, double tol)
+{
+    if (u < 0.0) return -u * exp(v / u) <= M_E * w + tol;
+    return u <= tol && v >= -tol && w >= -tol;
+}
+int orc_in_exp(const double *x, double tol) { return exp_member(x[2], x[1], x[0], tol); }
+int orc_in_exp_dual(const double *y, double tol) { return exp_dual_member(y[2], y[1], y[0], tol); }
+
+void orc_proj_exp(double *x)
+{
+    const double r = x[2], s = x[1], t = x[0];
+    if (exp_member(r, s, t, 0.0)) return;
+    if (exp_dual_member(-r, -s, -t, 0.0)) { x[0] = x[1] = x[2] = 0.0; return; }  /* v in the polar cone */
+    if (r <= 0.0 && s <= 0.0) { x[0] = t > 0.0 ? t : 0.0; x[1] = 0.0; return; }
+    /* candidates: the origin, the face point, the ray points at the roots of F */
+    double best_r = 0.0, best_s = 0.0, best_t = 0.0;
+    double best_d = r * r + s * s + t * t;
+    {
+        const double fr = r < 0.0 ? r : 0.0, ft = t > 0.0 ? t : 0.0;
+        const double d = (r - fr) * (r - fr) + s * s + (t - ft) * (t - ft);
+        if (d < best_d) { best_d = d; best_r = fr; best_s = 0.0; best_t = ft; }
+    }
+    const double L = 60.0, h = 0.05;
+    const int npts = (int)(2.0 * L / h + 0.5) + 1;
+    double roots[64];
+    int nr = 0;
+    double prev_x = -L, prev_f = exp_F(-L, r, s, t);
+    /* below the grid: F ~ r - s rho, one sign change at most */
+    {
+        double lo = -L;
+        for (int k = 0; k < 1100 && nr < 64; ++k) {
+            const double lo2 = 2.0 * lo;
+            if ((exp_F(lo2, r, s, t) > 0.0) != (exp_F(lo, r, s, t) > 0.0)) {
+                roots[nr++] = exp_bisect(lo2, lo, r, s, t);
+                break;
+            }
+            lo = lo2;
+            if (!isfinite(lo)) break;
+        }
+    }
+    for (int k = 1; k < npts && nr < 64; ++k) {
+        const double xk = -L + h * k;
+        const double fk = exp_F(xk, r, s, t);
+        if (fk == 0.0) roots[nr++] = xk;
+        else if ((fk > 0.0) != (prev_f > 0.0) && prev_f != 0.0) roots[nr++] = exp_bisect(prev_x, xk, r, s, t);
+        prev_x = xk;
+        prev_f = fk;
+    }
+    /* above the grid: F e^{-2 rho} ~ r (1 - rho) - s, one sign change at most */
+    {
+        double hi = L;
+        for (int k = 0; k < 1100 && nr < 64; ++k) {
+            const double hi2 = 2.0 * hi;
+            if ((exp_F(hi2, r, s, t) > 0.0) != (exp_F(hi, r, s, t) > 0.0)) {
+                roots[nr++] = exp_bisect(hi, hi2, r, s, t);
+                break;
+            }
+            hi = hi2;
+            if (!isfinite(hi)) break;
+        }
+    }
+    for (int k = 0; k < nr; ++k) {
+        double pr, ps, pt;
+        if (!exp_ray_point(roots[k], r, s, t, &pr, &ps, &pt)) continue;
+        const double d = (r - pr) * (r - pr) + (s - ps) * (s - ps) + (t - pt) * (t - pt);
+        if (d < best_d) { best_d = d; best_r = pr; best_s = ps; best_t = pt; }
+    }
+    x[0] = best_t;
+    x[1] = best_s;
+    x[2] = best_r;
+}
+
+/* Moreau: Pi_{K*}(v) = v + Pi_K(-v), since the polar of K* is -K */
+void orc_proj_exp_dual(double *v)
+{
+    double w[3] = {-v[0], -v[1], -v[2]};
+    orc_proj_exp(w);
+    v[0] += w[0];
+    v[1] += w[1];
+    v[2] += w[2];
 }
 
 /* svec index of entry (i, j), i >= j: lower triangle stored column by column
@@ -183,10 +324,11 @@ static int64_t cone_rows(const orc_problem *P)
     int64_t r = (int64_t)P->f + P->l;
     for (int32_t i = 0; i < P->nq; ++i) r += P->q[i];
     for (int32_t i = 0; i < P->ns; ++i) r += (int64_t)P->s[i] * (P->s[i] + 1) / 2;
+    r += 3 * (int64_t)P->ep + 3 * (int64_t)P->ed;
     return r;
 }
 
-/* Projection on K (primal = 0) or K* (dual = 1) over rows [f | l | q | s].
+/* Projection on K (primal = 0) or K* (dual = 1) over rows [f | l | q | s | ep | ed].
  * The zero cone's dual is the free cone, so its rows are set to 0 for K and
  * left untouched for K*; orthant, SOC and PSD cones are self-dual. */
 static int proj_cone(const orc_problem *P, double *v, int dual)
@@ -203,6 +345,14 @@ static int proj_cone(const orc_problem *P, double *v, int dual)
     for (int32_t k = 0; k < P->ns; ++k) {
         if (orc_proj_psd(v + o, P->s[k]) != 0) return -1;
         o += (int64_t)P->s[k] * (P->s[k] + 1) / 2;
+    }
+    /* the exponential cone is not self-dual: a primal block of K projects on
+     * K^e and, in K*, on (K^e)*; a dual block the other way round */
+    for (int32_t k = 0; k < P->ep; ++k, o += 3) {
+        if (dual) orc_proj_exp_dual(v + o); else orc_proj_exp(v + o);
+    }
+    for (int32_t k = 0; k < P->ed; ++k, o += 3) {
+        if (dual) orc_proj_exp(v + o); else orc_proj_exp_dual(v + o);
     }
     return 0;
 }

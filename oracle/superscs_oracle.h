@@ -18,7 +18,8 @@
  *   Anderson's acceleration                                              (Sec. 4.4.2)
  *   termination and certificates                                         (Sec. 4.3)
  *
- * Cone rows of s are ordered [ f zero | l orthant | q SOCs... | s PSDs... ].
+ * Cone rows of s are ordered [ f zero | l orthant | q SOCs... | s PSDs... |
+ * ep primal exponential cones | ed dual exponential cones ] (3 rows each).
  * A is CSR with m rows: Ap[m+1] (int64), Ai[nnz] (int32), Ax[nnz].
  *
  * Parity status of each function is stated in the tests that pin it.  The
@@ -48,6 +49,7 @@ typedef struct {
     const int32_t *q;
     int32_t ns;
     const int32_t *s;
+    int32_t ep, ed;  /* primal / dual exponential cones, 3 rows each, after the PSD rows */
 } orc_problem;
 
 enum { ORC_DIR_AA = 0, ORC_DIR_RB = 1, ORC_DIR_NONE = 2 };
@@ -91,6 +93,15 @@ typedef struct {
 typedef struct orc_work orc_work;
 
 /* --- cones (Sec. 2) ------------------------------------------------------ */
+/* Exponential cone, cone (v) of Sec. 2, in the paper's element order:
+ * K^e = cl{(x1, x2, x3) : x1 >= x2 exp(x3 / x2), x2 > 0}.  orc_proj_exp
+ * projects v (3 values, in place) on K^e, orc_proj_exp_dual on its dual cone
+ * (K^e)* = cl{(y1, y2, y3) : y3 < 0, -y3 exp(y2 / y3) <= e y1}; the
+ * membership tests return 1 inside (closure), 0 outside. */
+void orc_proj_exp(double *v);
+void orc_proj_exp_dual(double *v);
+int  orc_in_exp(const double *v, double tol);
+int  orc_in_exp_dual(const double *v, double tol);
 void orc_proj_soc(double *z, int32_t dim);
 int  orc_jacobi_eig(int32_t d, const double *Xin, double *lam, double *V);
 int  orc_proj_psd(double *v, int32_t d);

@@ -24,7 +24,7 @@ TEAM_AUTO, TEAM_BLOCK, TEAM_GRID = 0, 1, 2
 
 class Cone(C.Structure):
     _fields_ = [("f", C.c_int32), ("l", C.c_int32), ("nq", C.c_int32), ("q", C.POINTER(C.c_int32)),
-                ("ns", C.c_int32), ("s", C.POINTER(C.c_int32))]
+                ("ns", C.c_int32), ("s", C.POINTER(C.c_int32)), ("ep", C.c_int32), ("ed", C.c_int32)]
 
 
 class Data(C.Structure):
@@ -186,7 +186,7 @@ class _Keep:
         self.data = Data(self.m, self.n, self.Ap.ctypes.data_as(C.POINTER(C.c_int64)), ip(self.Ai), dp(self.Ax),
                          dp(self.b), dp(self.c))
         self.cone = Cone(int(prob.get("f", 0)), int(prob.get("l", 0)), len(prob.get("q", [])), ip(self.q),
-                         len(prob.get("s", [])), ip(self.s))
+                         len(prob.get("s", [])), ip(self.s), int(prob.get("ep", 0)), int(prob.get("ed", 0)))
 
 
 class Work:

@@ -159,6 +159,8 @@ struct DevProb {
     const int* q_off;  // nq+1 row offsets of the SOCs inside s
     const int* s_dim;  // ns PSD orders
     const int* s_off;  // ns row offsets of the PSD blocks inside s
+    int ep, ed;        // primal / dual exponential cones (3 rows each)
+    int e_off;         // row offset of the first exponential cone inside s
 };
 
 // Iterative refinement of the FP64 linear solves (SCS_MIXED, FP64 phase): the
@@ -1019,6 +1021,134 @@ __device__ void jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exponential cone K = cl{(x1, x2, x3) : x1 >= x2 exp(x3 / x2), x2 > 0}
+// (Sec. 2, cone (v)), one cone per thread, in FP64 whatever T is.  With
+// (r, s, t) = (x3, x2, x1): a point inside K is kept, a point of the polar
+// cone -K* goes to 0, a point with r <= 0 and s <= 0 goes to the face
+// (r, 0, max(t, 0)).  Any other point projects on the boundary: either on the
+// face {s = 0, r <= 0, t >= 0}, whose nearest point is (min(r,0), 0,
+// max(t,0)), or on a ray c (rho, 1, e^rho), c > 0, where the distance is
+// stationary in rho, i.e. where
+//   F(rho) = r (1 + (1-rho) e^{2rho}) - s (rho + e^{2rho}) + t e^rho (rho^2 - rho + 1)
+// vanishes.  The sign changes of F (evaluated as F e^{-2rho} for rho > 0)
+// are found on a grid of step 1/4 over [-60, 60] (its roots lie at least
+// about 3 apart) and by doubling brackets outside it, each root is bisected
+// to full precision, and the nearest of the candidates (origin, face point,
+// ray points) is returned.  The dual cone K* = cl{y3 < 0, -y3 exp(y2/y3) <= e y1}
+// is projected through Moreau's decomposition, Pi_{K*}(v) = v + Pi_K(-v).
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ double expc_F(double rho, double r, double s, double t)
+{
+    if (rho <= 0.0) {
+        const double e = exp(rho), e2 = e * e;
+        return r * (1.0 + (1.0 - rho) * e2) - s * (rho + e2) + t * e * (rho * rho - rho + 1.0);
+    }
+    const double em = exp(-rho), em2 = em * em;
+    return r * ((1.0 - rho) + em2) - s * (rho * em2 + 1.0) + t * em * (rho * rho - rho + 1.0);
+}
+
+// root of F in [lo, hi] (sign change), by bisection to adjacent doubles
+static __device__ double expc_root(double lo, double hi, double flo, double r, double s, double t)
+{
+    for (int it = 0; it < 2200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const double fm = expc_F(mid, r, s, t);
+        if (fm == 0.0) return mid;
+        if ((fm > 0.0) == (flo > 0.0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// candidate on the ray of slope rho: the ray's nearest point to (r, s, t) if it lies on the open ray
+static __device__ void expc_try_ray(double rho, double r, double s, double t, double& br, double& bs, double& bt, double& bd)
+{
+    double a0, a1, a2;  // the ray direction scaled by 1 / max(1, e^rho)
+    if (rho <= 0.0) {
+        a0 = rho;
+        a1 = 1.0;
+        a2 = exp(rho);
+    } else {
+        const double em = exp(-rho);
+        a0 = rho * em;
+        a1 = em;
+        a2 = 1.0;
+    }
+    const double c = (r * a0 + s * a1 + t * a2) / (a0 * a0 + a1 * a1 + a2 * a2);
+    if (!(c > 0.0)) return;
+    const double pr = c * a0, ps = c * a1, pt = c * a2;
+    const double d = (r - pr) * (r - pr) + (s - ps) * (s - ps) + (t - pt) * (t - pt);
+    if (d < bd) {
+        bd = d;
+        br = pr;
+        bs = ps;
+        bt = pt;
+    }
+}
+
+// x = (x1, x2, x3) <- Pi_K(x)
+static __device__ void expc_project(double& x1, double& x2, double& x3)
+{
+    const double r = x3, s = x2, t = x1;
+    if (s > 0.0 ? s * exp(r / s) <= t : (s == 0.0 && r <= 0.0 && t >= 0.0)) return;  // in K
+    if (r > 0.0 ? r * exp(s / r) <= -2.718281828459045 * t : (r == 0.0 && s <= 0.0 && t <= 0.0)) {
+        x1 = x2 = x3 = 0.0;  // in the polar cone
+        return;
+    }
+    if (r <= 0.0 && s <= 0.0) {
+        x1 = t > 0.0 ? t : 0.0;
+        x2 = 0.0;
+        return;
+    }
+    double br = 0.0, bs = 0.0, bt = 0.0, bd = r * r + s * s + t * t;  // the origin
+    {
+        const double fr = fmin(r, 0.0), ft = fmax(t, 0.0);
+        const double d = (r - fr) * (r - fr) + s * s + (t - ft) * (t - ft);
+        if (d < bd) {
+            bd = d;
+            br = fr;
+            bs = 0.0;
+            bt = ft;
+        }
+    }
+    // outside the grid F is dominated by its linear part: at most one sign change on each side
+    for (int side = 0; side < 2; ++side) {
+        double a = side == 0 ? -60.0 : 60.0;
+        double fa = expc_F(a, r, s, t);
+        for (int k = 0; k < 1100; ++k) {
+            const double b = 2.0 * a;
+            if (!isfinite(b)) break;
+            const double fb = expc_F(b, r, s, t);
+            if (fb != 0.0 && (fb > 0.0) != (fa > 0.0)) {
+                const double rho = side == 0 ? expc_root(b, a, fb, r, s, t) : expc_root(a, b, fa, r, s, t);
+                expc_try_ray(rho, r, s, t, br, bs, bt, bd);
+                break;
+            }
+            a = b;
+            fa = fb;
+        }
+    }
+    double xa = -60.0, fa = expc_F(xa, r, s, t);
+    for (int k = 1; k <= 480; ++k) {
+        const double xb = -60.0 + 0.25 * k;
+        const double fb = expc_F(xb, r, s, t);
+        if (fb == 0.0) expc_try_ray(xb, r, s, t, br, bs, bt, bd);
+        else if (fa != 0.0 && (fb > 0.0) != (fa > 0.0))
+            expc_try_ray(expc_root(xa, xb, fa, r, s, t), r, s, t, br, bs, bt, bd);
+        xa = xb;
+        fa = fb;
+    }
+    x1 = bt;
+    x2 = bs;
+    x3 = br;
+}
+
 template <typename T>
 struct PsdSmem {
     T* X;
@@ -1166,6 +1296,29 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
             }
             __syncthreads();
         }
+    }
+    // exponential cones, one per thread: the psi part lies in K*, so a primal
+    // block projects on the dual cone (Moreau: v + Pi_K(-v)) and a dual block on K
+    for (int k = tm.rank(); k < P.ep + P.ed; k += tm.size()) {
+        const int o = n + P.e_off + 3 * k;
+        T w[3], wt[3];
+        double v[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            op.load(o + j, w[j], wt[j]);
+            v[j] = 2.0 * (double)wt[j] - (double)w[j];
+        }
+        if (k < P.ep) {
+            double m1 = -v[0], m2 = -v[1], m3 = -v[2];
+            expc_project(m1, m2, m3);
+            v[0] += m1;
+            v[1] += m2;
+            v[2] += m3;
+        } else {
+            expc_project(v[0], v[1], v[2]);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) op.store(o + j, w[j], wt[j], (T)v[j]);
     }
     if (tm.leader()) {
         double w, wt;

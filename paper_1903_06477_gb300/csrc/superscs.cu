@@ -67,6 +67,7 @@ struct HostProb {
     std::vector<double> Ax, Tx, b, c;
     int f = 0, l = 0;
     std::vector<int> q, s, q_off, s_off;
+    int ep = 0, ed = 0, e_off = 0;  // exponential cones and the row offset of the first
     double nb = 0, nc = 0;
     int vecA = 32, vecT = 32;
     struct Sell {
@@ -274,7 +275,7 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err,
         if (d->Ap[i + 1] < d->Ap[i]) { set_err(err, "Ap is not nondecreasing at row %d", i); return SCS_EINVAL; }
     const long long nnz = d->Ap[m];
     if (nnz >= (1ll << 31)) { set_err(err, "nnz = %lld is not below 2^31", nnz); return SCS_EINVAL; }
-    if (k->f < 0 || k->l < 0 || k->nq < 0 || k->ns < 0) { set_err(err, "negative cone counts"); return SCS_EINVAL; }
+    if (k->f < 0 || k->l < 0 || k->nq < 0 || k->ns < 0 || k->ep < 0 || k->ed < 0) { set_err(err, "negative cone counts"); return SCS_EINVAL; }
     if ((k->nq > 0 && !k->q) || (k->ns > 0 && !k->s)) { set_err(err, "cone arrays must not be NULL"); return SCS_EINVAL; }
     long long rows = (long long)k->f + k->l;
     H.q_off.assign(1, 0);
@@ -292,6 +293,8 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err,
     long long o = (long long)k->f + k->l;
     for (int i = 0; i < k->nq; ++i) { o += k->q[i]; }
     for (int i = 0; i < k->ns; ++i) { o += (long long)k->s[i] * (k->s[i] + 1) / 2; }
+    const long long e_off = o;
+    o += 3LL * k->ep + 3LL * k->ed;
     rows = o;
     if (rows != m) { set_err(err, "cone rows (%lld) do not sum to m (%d)", rows, m); return SCS_EINVAL; }
     H.n = n;
@@ -299,6 +302,9 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err,
     H.nnz = nnz;
     H.f = k->f;
     H.l = k->l;
+    H.ep = k->ep;
+    H.ed = k->ed;
+    H.e_off = (int)e_off;
     long long qo = (long long)k->f + k->l;
     for (int i = 0; i < k->nq; ++i) { H.q_off.push_back(0); }
     H.q_off[0] = (int)qo;
@@ -463,6 +469,9 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     P.l = H.l;
     P.nq = (int)H.q.size();
     P.ns = (int)H.s.size();
+    P.ep = H.ep;
+    P.ed = H.ed;
+    P.e_off = H.e_off;
     double* taus = A.take<double>(16);
     HV<T>* hvs[] = {&W.u, &W.ut, &W.ub, &W.Ru, &W.d, &W.dt, &W.wb, &W.Rw, &W.zp, &W.xip, &W.zt};
     for (int i = 0; i < 11; ++i) {
@@ -1492,6 +1501,7 @@ extern "C" int scs_batch_setup_shared(int32_t B, const scs_data* data, const scs
         if (i > 0) {  // light copy: sizes and cones; the matrix stays with instance 0
             const HostProb& h0 = b->H[0];
             h.n = h0.n; h.m = h0.m; h.nnz = h0.nnz; h.f = h0.f; h.l = h0.l;
+            h.ep = h0.ep; h.ed = h0.ed; h.e_off = h0.e_off;
             h.q = h0.q; h.s = h0.s; h.q_off = h0.q_off; h.s_off = h0.s_off; h.vecA = h0.vecA; h.vecT = h0.vecT;
             h.SA.rows = h0.SA.rows; h.SA.V = h0.SA.V; h.SA.nslices = h0.SA.nslices;
             h.ST.rows = h0.ST.rows; h.ST.V = h0.ST.V; h.ST.nslices = h0.ST.nslices;

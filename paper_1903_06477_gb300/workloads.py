@@ -112,7 +112,26 @@ def _svec(X):
     return out
 
 
-def planted(seed=0, n=200, l=200, soc=(), psd=(), f=0, nnz=None, density=None, psd_rank=None):
+def _exp_pair(rng, case):
+    """A complementary pair (x in K^e, z in (K^e)*) of the exponential cone
+    K^e = cl{x1 >= x2 exp(x3/x2), x2 > 0} (Sec. 2, cone (v)): case 0 x
+    interior, z = 0; case 1 x = 0, z interior; case 2 both on the boundary,
+    x = c (e^rho, 1, rho) and z = lam (1, -e^rho (1 - rho), -e^rho), <x, z> = 0."""
+    x, z = np.zeros(3), np.zeros(3)
+    if case == 0:
+        x2, x3 = rng.uniform(0.5, 1.5), rng.standard_normal()
+        x[:] = (x2 * np.exp(x3 / x2) + rng.uniform(0.5, 1.5), x2, x3)
+    elif case == 1:
+        z3, z2 = -rng.uniform(0.5, 1.5), rng.standard_normal()
+        z[:] = (-z3 * np.exp(z2 / z3) / np.e + rng.uniform(0.5, 1.5), z2, z3)
+    else:
+        rho, cc, lam = rng.uniform(-2, 2), rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5)
+        x[:] = cc * np.array([np.exp(rho), 1.0, rho])
+        z[:] = lam * np.array([1.0, -np.exp(rho) * (1 - rho), -np.exp(rho)])
+    return x, z
+
+
+def planted(seed=0, n=200, l=200, soc=(), psd=(), f=0, nnz=None, density=None, psd_rank=None, ep=0, ed=0):
     """Random sparse cone program with a planted strictly complementary
     primal-dual optimum (x*, y*, s*); b = A x* + s*, c = -A^T y*.
 
@@ -122,11 +141,14 @@ def planted(seed=0, n=200, l=200, soc=(), psd=(), f=0, nnz=None, density=None, p
     s = 0;  s = a(u,1), y = beta(-u,1).  PSD of order d: V from the QR of a
     Gaussian, S = V diag(lam_1..lam_k, 0..) V^T, Y = V diag(0.., lam_{k+1}..) V^T
     with lam ~ U(0.5, 2) and k ~ U{d/4..3d/4}.  Zero-cone rows: s = 0, y ~ N(0,1).
+    Exponential cones (ep primal blocks of K^e, then ed blocks of its dual),
+    cycling over the three complementary cases of _exp_pair (for a dual
+    block the roles of s and y swap).
     A has N(0,1) values at uniform random positions.
     """
     rng = np.random.default_rng(seed)
     soc, psd = list(soc), list(psd)
-    m = f + l + sum(soc) + sum(d * (d + 1) // 2 for d in psd)
+    m = f + l + sum(soc) + sum(d * (d + 1) // 2 for d in psd) + 3 * (ep + ed)
     if nnz is None:
         nnz = int(round((density if density is not None else 0.05) * m * n))
     A = random_pattern(rng, m, n, nnz)
@@ -173,10 +195,17 @@ def planted(seed=0, n=200, l=200, soc=(), psd=(), f=0, nnz=None, density=None, p
         s[o:o + k] = _svec(S)
         y[o:o + k] = _svec(Y)
         o += k
+    for i in range(ep + ed):
+        xk, zk = _exp_pair(rng, i % 3)
+        if i < ep:
+            s[o:o + 3], y[o:o + 3] = xk, zk
+        else:
+            s[o:o + 3], y[o:o + 3] = zk, xk
+        o += 3
     assert o == m
     b = A @ xs + s
     c = -(A.T @ y)
-    return dict(A=A, b=b, c=c, f=f, l=l, q=soc, s=psd, xstar=xs, ystar=y, sstar=s)
+    return dict(A=A, b=b, c=c, f=f, l=l, q=soc, s=psd, ep=ep, ed=ed, xstar=xs, ystar=y, sstar=s)
 
 
 def c2_planted(seed=0, scale=1.0):
@@ -313,3 +342,64 @@ def lasso_family_rhs_smooth(F, seed, base_seed=0, frac_nz=0.05, rel=0.1, noise=0
     rng = np.random.default_rng(seed)
     x = xb * (1.0 + rel * rng.standard_normal(nvar))
     return F @ x + noise * rng.standard_normal(F.shape[0])
+
+
+def logreg(seed=0, p=100, q=120, lam=10.0, density=1.0, frac_nz=0.1):
+    """Sparse l1-regularised logistic regression (Sec. 5.4) as a conic program
+    with exponential cones.  Reading of the printed objective (its sign and
+    indices are garbled): minimise lam ||w||_1 + sum_i log(1 + exp(a_i^T w)),
+    with a_i = -y_i x_i (labels folded into the samples).  Data: features x_i
+    with N(0,1) entries at `density`, a planted w0 with frac_nz N(0,1)
+    nonzeros, labels y_i = sign(x_i^T w0 + 0.1 N(0,1)).
+
+    Variables (w, t, u, v1, v2) of sizes (p, p, q, q, q); objective
+    lam sum t + sum u.  Orthant rows: t - w >= 0, t + w >= 0, 1 - v1 - v2 >= 0;
+    per sample two exponential cones (x1 >= x2 exp(x3/x2)):
+    (v1_i, 1, a_i^T w - u_i) and (v2_i, 1, -u_i), which together say
+    exp(a_i^T w - u_i) + exp(-u_i) <= 1, i.e. u_i >= log(1 + exp(a_i^T w))."""
+    rng = np.random.default_rng(seed)
+    if density >= 1.0:
+        X = rng.standard_normal((q, p))
+    else:
+        X = (rng.random((q, p)) < density) * rng.standard_normal((q, p))
+    w0 = np.zeros(p)
+    nz = rng.choice(p, max(1, int(round(frac_nz * p))), replace=False)
+    w0[nz] = rng.standard_normal(len(nz))
+    lab = np.sign(X @ w0 + 0.1 * rng.standard_normal(q))
+    lab[lab == 0] = 1.0
+    Asmp = -lab[:, None] * X
+    n = 2 * p + 3 * q
+    iw, it_, iu, iv1, iv2 = 0, p, 2 * p, 2 * p + q, 2 * p + 2 * q
+    l = 2 * p + q
+    m = l + 6 * q
+    rows, cols, vals = [], [], []
+    b = np.zeros(m)
+
+    def put(r, c, v):
+        rows.append(r)
+        cols.append(c)
+        vals.append(v)
+
+    for j in range(p):
+        put(j, iw + j, 1.0)
+        put(j, it_ + j, -1.0)
+        put(p + j, iw + j, -1.0)
+        put(p + j, it_ + j, -1.0)
+    for i in range(q):
+        put(2 * p + i, iv1 + i, 1.0)
+        put(2 * p + i, iv2 + i, 1.0)
+        b[2 * p + i] = 1.0
+    for i in range(q):
+        e0 = l + 6 * i
+        put(e0, iv1 + i, -1.0)
+        b[e0 + 1] = 1.0
+        for j in np.nonzero(Asmp[i])[0]:
+            put(e0 + 2, iw + j, -Asmp[i, j])
+        put(e0 + 2, iu + i, 1.0)
+        put(e0 + 3, iv2 + i, -1.0)
+        b[e0 + 4] = 1.0
+        put(e0 + 5, iu + i, 1.0)
+    A = _csr(np.array(rows, np.int64), np.array(cols, np.int64), np.array(vals), m, n)
+    c = np.concatenate([np.zeros(p), lam * np.ones(p), np.ones(q), np.zeros(2 * q)])
+    return dict(A=A, b=b, c=c, f=0, l=l, q=[], s=[], ep=2 * q, ed=0,
+                meta=dict(p=p, q=q, lam=lam, samples=Asmp, w0=w0))

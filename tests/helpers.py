@@ -56,6 +56,34 @@ def cone_blocks(prob):
         k = d * (d + 1) // 2
         yield "s", o, k, d
         o += k
+    for _ in range(prob.get("ep", 0)):
+        yield "ep", o, 3, 0
+        o += 3
+    for _ in range(prob.get("ed", 0)):
+        yield "ed", o, 3, 0
+        o += 3
+
+
+def _exp_gens():
+    """Normalised extreme rays of the exponential cone K^e = cl{x1 >= x2 e^{x3/x2}, x2 > 0}
+    (Sec. 2, cone (v)) and of its dual cl{-y3 e^{y2/y3} <= e y1, y3 < 0}."""
+    rho = np.concatenate([-np.logspace(3, -3, 300), [0.0], np.linspace(-60, 60, 12001), np.logspace(-3, 2.5, 300)])
+    GK = np.vstack([np.stack([np.exp(rho), np.ones_like(rho), rho], 1), [[1.0, 0, 0], [0, 0, -1.0]]])
+    GD = np.vstack([np.stack([np.exp(rho - 1), -rho, -np.ones_like(rho)], 1), [[1.0, 0, 0], [0, 1.0, 0]]])
+    return (GK / np.linalg.norm(GK, axis=1, keepdims=True), GD / np.linalg.norm(GD, axis=1, keepdims=True))
+
+
+EXP_GK, EXP_GD = _exp_gens()
+
+
+def in_exp(x, tol):
+    """x in K^e, tested through duality: <x, g> >= -tol for every generator g of the dual cone."""
+    return (EXP_GD @ np.asarray(x, float)).min() >= -tol
+
+
+def in_exp_dual(y, tol):
+    """y in (K^e)*: <y, g> >= -tol for every generator g of K^e (the definition of a dual cone)."""
+    return (EXP_GK @ np.asarray(y, float)).min() >= -tol
 
 
 def svec_mat(v, d):
@@ -81,8 +109,12 @@ def check_in_cone(prob, s, dual, tol):
             assert blk.min() >= -tol
         elif kind == "q":
             assert np.linalg.norm(blk[:-1]) <= blk[-1] + tol
-        else:
+        elif kind == "s":
             assert np.linalg.eigvalsh(svec_mat(blk, d)).min() >= -tol
+        elif (kind == "ep") != dual:  # K^e: a primal block of K, or a dual block of K*
+            assert in_exp(blk, tol), blk
+        else:
+            assert in_exp_dual(blk, tol), blk
 
 
 def fista_lasso(F, g, mu, iters=20000):
@@ -100,3 +132,23 @@ def fista_lasso(F, g, mu, iters=20000):
         yv = xn + ((t - 1) / tn) * (xn - x)
         x, t = xn, tn
     return x
+
+
+def fista_logreg(Asmp, lam, iters=20000):
+    """Independent FISTA for lam ||w||_1 + sum_i log(1 + exp(a_i^T w)) (FP64);
+    returns (w, objective)."""
+    Asmp = np.asarray(Asmp, float)
+    L = 0.25 * np.linalg.norm(Asmp, 2) ** 2
+    w = np.zeros(Asmp.shape[1])
+    yv = w.copy()
+    t = 1.0
+    for _ in range(iters):
+        z = Asmp @ yv
+        grad = Asmp.T @ (0.5 * (1.0 + np.tanh(0.5 * z)))
+        u = yv - grad / L
+        wn = np.sign(u) * np.maximum(np.abs(u) - lam / L, 0.0)
+        tn = 0.5 * (1 + np.sqrt(1 + 4 * t * t))
+        yv = wn + ((t - 1) / tn) * (wn - w)
+        w, t = wn, tn
+    obj = lam * np.abs(w).sum() + np.logaddexp(0.0, Asmp @ w).sum()
+    return w, obj

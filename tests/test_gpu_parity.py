@@ -26,6 +26,8 @@ def _problems():
         "planted_mixed_cones": W.planted(seed=2, n=70, l=50, soc=[1, 2, 3, 7, 40], psd=[1, 2, 3, 5], f=3, nnz=1500),
         "portfolio": W.portfolio(seed=3, k=60),
         "planted_c2_small": W.c2_planted(seed=1, scale=0.01),
+        "planted_exp_cones": W.planted(seed=21, n=60, l=30, soc=[5, 4], ep=9, ed=6, nnz=900),
+        "logreg": W.logreg(seed=3, p=20, q=30, lam=2.0),
     }
 
 
@@ -214,6 +216,32 @@ def test_mixed_precision_reaches_fp64_tolerance(team):
     assert max(pr, dr, gap) <= eps * 1.01
     pstar = prob["c"] @ prob["xstar"]
     assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_exp_cone_projection_extreme_points(team):
+    """Pi_C on exponential-cone rows at points that exercise every branch of the
+    projection: inside K, in the polar cone, the face case, roots far beyond
+    the scan range (|rho| in the hundreds), and magnitudes from 1e-6 to 1e6."""
+    prob = W.planted(seed=4, n=20, l=4, ep=40, ed=40, nnz=300)
+    work = B.Work(prob, team=team)
+    orc = O.Oracle(prob)
+    rng = np.random.default_rng(7)
+    n, m = work.n, work.m
+    for trial in range(6):
+        v = rng.standard_normal(work.N)
+        e = v[n + 4:n + m].reshape(-1, 3)
+        if trial == 1:
+            e[:, 2] = np.abs(e[:, 2]) * 1e-4   # x3 tiny positive, x2 negative: roots near 1 - x2/x3
+            e[:, 1] = -np.abs(e[:, 1])
+        if trial == 2:
+            e *= np.exp(rng.uniform(-14, 14, (len(e), 1)))
+        if trial == 3:
+            e[:, 1] = np.abs(e[:, 1]) * 1e-5  # x2 tiny positive
+        v[n + 4:n + m] = e.ravel()
+        out = work.project_cone(v)
+        ref = orc.proj_C(v)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * (1 + np.abs(ref).max()))
 
 
 def test_edge_cases():

@@ -132,3 +132,109 @@ def test_proj_C_structure():
     np.testing.assert_array_equal(out[:n], v[:n])
     assert out[-1] == 0.0
     np.testing.assert_allclose(out[n:n + m], orc.proj_dual_cone(v[n:n + m]))
+
+
+# --- exponential cone (Sec. 2, cone (v)): K^e = cl{x1 >= x2 exp(x3/x2), x2 > 0} ---------------------------
+_RHO = np.concatenate([-np.logspace(3, -3, 400), [0.0], np.linspace(-60, 60, 24001), np.logspace(-3, 3, 400)])
+
+
+def _gens_K():
+    # extreme rays of K^e, normalised: x2 = 1, x3 = rho, x1 = e^rho, and the face rays (1,0,0), (0,0,-1)
+    rho = _RHO[np.abs(_RHO) < 350]
+    G = np.stack([np.exp(rho), np.ones_like(rho), rho], 1)
+    G = np.vstack([G, [[1.0, 0, 0], [0, 0, -1.0]]])
+    return G / np.linalg.norm(G, axis=1, keepdims=True)
+
+
+def _gens_Kdual():
+    # extreme rays of (K^e)*: y3 = -1, y2 = -sig, y1 = e^(sig - 1), and the face rays (1,0,0), (0,1,0)
+    sig = _RHO[np.abs(_RHO) < 350]
+    G = np.stack([np.exp(sig - 1), -sig, -np.ones_like(sig)], 1)
+    G = np.vstack([G, [[1.0, 0, 0], [0, 1.0, 0]]])
+    return G / np.linalg.norm(G, axis=1, keepdims=True)
+
+
+_GK, _GKD = _gens_K(), _gens_Kdual()
+
+
+def _exp_in(x, tol):
+    # x in K^e = (K^e)** iff <x, g> >= 0 for every generator g of the dual cone (a distance-like test)
+    return (_GKD @ np.asarray(x, float)).min() >= -tol
+
+
+def _exp_dual_in(y, tol):
+    # y in (K^e)* iff <y, g> >= 0 for every generator g of K^e (the definition of a dual cone)
+    return (_GK @ np.asarray(y, float)).min() >= -tol
+
+
+def test_exp_membership_and_closed_forms():
+    assert O.in_exp([np.e, 1.0, 1.0]) and O.in_exp([0.0, 0.0, -5.0]) and not O.in_exp([1.0, 1.0, 1.0])
+    assert O.in_exp_dual([1.0, 0.0, -np.e]) and O.in_exp_dual([1.0, 2.0, 0.0]) and not O.in_exp_dual([1.0, 0.0, 1.0])
+    # a point of the cone is its own projection, a point of the polar cone -(K^e)* goes to 0
+    np.testing.assert_array_equal(O.proj_exp([5.0, 1.0, 0.5]), [5.0, 1.0, 0.5])
+    np.testing.assert_array_equal(O.proj_exp([-1.0, 0.0, np.e]), [0.0, 0.0, 0.0])
+    # x2 <= 0 and x3 <= 0: the face {x2 = 0, x3 <= 0, x1 >= 0}, nearest point (max(x1, 0), 0, x3)
+    np.testing.assert_array_equal(O.proj_exp([2.0, -1.0, -3.0]), [2.0, 0.0, -3.0])
+    np.testing.assert_array_equal(O.proj_exp([-2.0, -1.0, -3.0]), [0.0, 0.0, -3.0])
+
+
+def test_exp_projection_of_planted_kkt_points():
+    # p on the surface x1 = x2 e^{x3/x2} (x2 = c, x3 = c rho) plus lam times the outward normal
+    # n = (-1, e^rho (1 - rho), e^rho) of {x2 e^{x3/x2} - x1 <= 0}: Pi(p + lam n) = p
+    rng = np.random.default_rng(3)
+    for _ in range(400):
+        rho = rng.uniform(-8, 8)
+        c = np.exp(rng.uniform(-4, 3))
+        lam = np.exp(rng.uniform(-4, 3))
+        p = c * np.array([np.exp(rho), 1.0, rho])
+        n = np.array([-1.0, np.exp(rho) * (1 - rho), np.exp(rho)])
+        got = O.proj_exp(p + lam * n)
+        np.testing.assert_allclose(got, p, rtol=0, atol=1e-11 * (1 + np.abs(p).max() + lam * np.abs(n).max()))
+
+
+def test_exp_projection_kkt_and_moreau_on_random_points():
+    rng = np.random.default_rng(4)
+    for _ in range(3000):
+        v = rng.standard_normal(3) * np.exp(rng.uniform(-3, 3))
+        p = O.proj_exp(v)
+        q = v - p
+        sc = 1e-10 * (1 + np.abs(v).max())
+        assert _exp_in(p, sc), (v, p)
+        assert _exp_dual_in(-q, sc), (v, p, q)  # v - p in the polar cone -(K^e)*
+        assert abs(p @ q) <= sc * (1 + np.abs(v).max()), (v, p)
+        np.testing.assert_allclose(O.proj_exp(p), p, rtol=0, atol=sc)  # idempotent
+        # the dual projection: Pi_{K*}(v) in K*, v - Pi_{K*}(v) in -K, orthogonal
+        pd = O.proj_exp_dual(v)
+        qd = v - pd
+        assert _exp_dual_in(pd, sc) and _exp_in(-qd, sc) and abs(pd @ qd) <= sc * (1 + np.abs(v).max())
+
+
+def test_exp_projection_is_nearest_boundary_point_brute_force():
+    # brute force on a dense sampling of the boundary: rays c (e^rho, 1, rho) and the face
+    rng = np.random.default_rng(5)
+    rho = np.linspace(-12, 12, 24001)
+    A = np.stack([np.exp(rho), np.ones_like(rho), rho], 1)
+    An = A / np.linalg.norm(A, axis=1, keepdims=True)
+    for _ in range(300):
+        v = rng.standard_normal(3) * np.exp(rng.uniform(-2, 2))
+        p = O.proj_exp(v)
+        d = np.linalg.norm(v - p)
+        cs = np.maximum(An @ v, 0)
+        dray = np.sqrt(np.maximum(v @ v - cs ** 2, 0)).min()
+        face = np.array([max(v[0], 0), 0.0, min(v[2], 0)])
+        dbest = min(dray, np.linalg.norm(v - face), np.linalg.norm(v), 0.0 if _exp_in(v, 0) else np.inf)
+        assert d <= dbest + 1e-7 * (1 + np.abs(v).max()), (v, p, d, dbest)
+        assert d >= dbest - 1e-3 * (1 + np.abs(v).max())  # the sampling is fine enough to come close
+
+
+def test_exp_planted_mistake_is_caught():
+    # planted mistake, on the CPU: using the wrong element order (x3 read as x1) breaks the KKT pin
+    rng = np.random.default_rng(6)
+    bad = 0
+    for _ in range(50):
+        v = rng.standard_normal(3)
+        p = O.proj_exp(v[::-1])[::-1]
+        q = v - p
+        if not (_exp_in(p, 1e-9) and _exp_dual_in(-q, 1e-9) and abs(p @ q) <= 1e-9):
+            bad += 1
+    assert bad > 10

@@ -234,3 +234,33 @@ def test_warm_start_from_solution_terminates_immediately():
     o1 = O.Oracle(prob, eps=1e-8, max_iters=20000).solve()
     out = O.Oracle(prob, eps=1e-7, max_iters=20000, warm_u=o1["u"]).solve()
     assert out["info"].status == O.SOLVED and out["info"].iters <= 2
+
+
+def test_planted_optimum_with_exponential_cones():
+    # planted complementary pairs on primal and dual exponential cone blocks (all three cases),
+    # mixed with orthant and SOC rows: the oracle must reach the planted objective
+    prob = W.planted(seed=21, n=60, l=30, soc=[5, 4], ep=9, ed=6, nnz=900)
+    eps = 1e-7
+    out = O.Oracle(prob, eps=eps, max_iters=20000).solve()
+    assert out["info"].status == O.SOLVED, out["info"]
+    pstar = prob["c"] @ prob["xstar"]
+    assert abs(out["info"].pobj - pstar) <= 10 * eps * (1 + abs(pstar))
+    check_in_cone(prob, out["s"], dual=False, tol=1e-6)
+    check_in_cone(prob, out["y"], dual=True, tol=1e-6)
+
+
+@pytest.mark.parametrize("lam", [2.0, 8.0])
+def test_logreg_vs_fista(lam):
+    # the l1-regularised logistic regression of Sec. 5.4 in conic form (two exponential cones per
+    # sample) against an independent proximal-gradient solve of the same objective
+    from tests.helpers import fista_logreg
+    prob = W.logreg(seed=3, p=20, q=30, lam=lam)
+    out = O.Oracle(prob, eps=1e-9, max_iters=50000).solve()
+    assert out["info"].status == O.SOLVED, out["info"]
+    p = prob["meta"]["p"]
+    w = out["x"][:p]
+    wf, objf = fista_logreg(prob["meta"]["samples"], lam, iters=40000)
+    obj = lam * np.abs(w).sum() + np.logaddexp(0.0, prob["meta"]["samples"] @ w).sum()
+    assert abs(out["info"].pobj - objf) <= 1e-6 * (1 + abs(objf))
+    assert abs(obj - objf) <= 1e-6 * (1 + abs(objf))
+    np.testing.assert_allclose(w, wf, atol=1e-4)
