@@ -54,6 +54,9 @@ extern "C" {
 #define SCS_DIR_AA 0   /* Anderson's acceleration */
 #define SCS_DIR_RB 1   /* restarted Broyden, Algorithm 2 */
 #define SCS_DIR_NONE 2 /* d = 0: with c0 = 0 every step is the KM step of Eq. (km) */
+#define SCS_DIR_AA_QR 3 /* Anderson's acceleration with its least squares solved through a QR
+                           factorisation of the window, updated as pairs enter (Gram-Schmidt)
+                           and leave (Givens rotations), Sec. 4.4 */
 
 /* precision */
 #define SCS_FP64 0  /* every vector and the matrix in FP64 */
@@ -87,8 +90,8 @@ typedef struct {
 } scs_data;
 
 typedef struct {
-    int32_t direction;   /* SCS_DIR_AA | SCS_DIR_RB | SCS_DIR_NONE */
-    int32_t mem;         /* memory of the direction (AA: 1..32, RB: 0..64) */
+    int32_t direction;   /* SCS_DIR_AA | SCS_DIR_RB | SCS_DIR_NONE | SCS_DIR_AA_QR */
+    int32_t mem;         /* memory of the direction (AA, AA_QR: 1..32, RB: 0..64) */
     double eps;          /* tolerance of Sec. 4.3 on pr, dr, gap, ic, uc */
     double c0, c1, q, sigma, lambda; /* Algorithm 1 parameters */
     double thetabar;     /* Powell safeguard of Algorithm 2 */

@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "superscs_oracle.c")
 _LIB = os.path.join(_HERE, "libsuperscs_oracle.so")
 
 SOLVED, INFEASIBLE, UNBOUNDED, MAX_ITERS, NUMERICAL = 1, -1, -2, -3, -5
-DIR_AA, DIR_RB, DIR_NONE = 0, 1, 2
+DIR_AA, DIR_RB, DIR_NONE, DIR_AA_QR = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:

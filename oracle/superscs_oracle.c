@@ -607,6 +607,8 @@ struct orc_dir {
     double thetabar, aa_reg;
     double *Z, *Zt; /* mem x N each: z^i and z~^i (RB) or z^i and xi^i (AA) */
     double *v;      /* N scratch */
+    double *Q, *R;  /* AA_QR: Q (mem x N, orthonormal columns), R (mem x mem, row-major,
+                       upper triangular), Xi_window = Q R with the pairs oldest first */
 };
 
 orc_dir *orc_dir_new(int32_t kind, int64_t N, int32_t mem, double thetabar, double aa_reg)
@@ -614,18 +616,110 @@ orc_dir *orc_dir_new(int32_t kind, int64_t N, int32_t mem, double thetabar, doub
     orc_dir *D = (orc_dir *)calloc(1, sizeof(orc_dir));
     if (!D) return NULL;
     D->kind = kind; D->mem = mem < 0 ? 0 : mem; D->N = N;
+    if (kind == ORC_DIR_AA_QR && D->mem > 64) D->mem = 64; /* the QR variant keeps at most 64 pairs */
     D->thetabar = thetabar; D->aa_reg = aa_reg;
     size_t cnt = (size_t)(D->mem > 0 ? D->mem : 1) * (size_t)N;
     D->Z = (double *)calloc(cnt, sizeof(double));
     D->Zt = (double *)calloc(cnt, sizeof(double));
     D->v = (double *)calloc((size_t)N, sizeof(double));
-    if (!D->Z || !D->Zt || !D->v) { orc_dir_free(D); return NULL; }
+    D->Q = (double *)calloc(cnt, sizeof(double));
+    D->R = (double *)calloc((size_t)(D->mem > 0 ? D->mem : 1) * (D->mem > 0 ? D->mem : 1), sizeof(double));
+    if (!D->Z || !D->Zt || !D->v || !D->Q || !D->R) { orc_dir_free(D); return NULL; }
     return D;
 }
 void orc_dir_free(orc_dir *D)
 {
     if (!D) return;
-    free(D->Z); free(D->Zt); free(D->v); free(D);
+    free(D->Z); free(D->Zt); free(D->v); free(D->Q); free(D->R); free(D);
+}
+
+/* Anderson's acceleration with the least-squares problem min ||Xi t - Ru|| of
+ * Sec. 4.4 solved through Xi = Q R, kept up to date as the window moves:
+ *  - the oldest pair leaves: R loses its first column, which leaves it upper
+ *    Hessenberg; Givens rotations on rows (j, j+1), j = 0..k-2, restore the
+ *    triangle and the same rotations combine the columns of Q;
+ *  - a new pair xi enters: two rounds of classical Gram-Schmidt against Q
+ *    give the new column of R and, normalised, the new column of Q (a pair
+ *    whose remainder is below 1e-14 ||xi|| is rank deficient and not stored);
+ *  - t solves R t = Q^T Ru by back substitution, d = -Ru - (Z - Xi) t.
+ * The columns (Z, Xi, Q) are kept oldest first. */
+static void aa_qr_drop_oldest(orc_dir *D)
+{
+    int64_t N = D->N;
+    int32_t k = D->count, m = D->mem;
+    double *R = D->R;
+    /* R[:, 1:] is k x (k-1) upper Hessenberg */
+    for (int32_t j = 0; j + 1 < k; ++j) {
+        double a = R[j * m + j + 1], b = R[(j + 1) * m + j + 1];
+        double h = hypot(a, b);
+        double c = h > 0.0 ? a / h : 1.0, s = h > 0.0 ? b / h : 0.0;
+        for (int32_t col = j + 1; col < k; ++col) {
+            double x = R[j * m + col], y = R[(j + 1) * m + col];
+            R[j * m + col] = c * x + s * y;
+            R[(j + 1) * m + col] = -s * x + c * y;
+        }
+        double *qa = D->Q + (size_t)j * N, *qb = D->Q + (size_t)(j + 1) * N;
+        for (int64_t i = 0; i < N; ++i) {
+            double x = qa[i], y = qb[i];
+            qa[i] = c * x + s * y;
+            qb[i] = -s * x + c * y;
+        }
+    }
+    /* shift R's columns left by one (rows 0..k-2) and the windows of Z, Xi */
+    for (int32_t r = 0; r + 1 < k; ++r)
+        for (int32_t col = 0; col + 1 < k; ++col) R[r * m + col] = col >= r ? R[r * m + col + 1] : 0.0;
+    for (int32_t col = 0; col < k; ++col) R[(k - 1) * m + col] = 0.0;
+    memmove(D->Z, D->Z + N, sizeof(double) * (size_t)(k - 1) * N);
+    memmove(D->Zt, D->Zt + N, sizeof(double) * (size_t)(k - 1) * N);
+    D->count = k - 1;
+}
+
+static void aa_qr_append(orc_dir *D, const double *z, const double *xi)
+{
+    int64_t N = D->N;
+    int32_t k = D->count, m = D->mem;
+    double *w = D->v;
+    memcpy(w, xi, sizeof(double) * (size_t)N);
+    double nxi = vnorm(xi, N);
+    double rcol[64];
+    for (int32_t j = 0; j < k; ++j) rcol[j] = 0.0;
+    for (int round = 0; round < 2; ++round) {
+        double h[64];
+        for (int32_t j = 0; j < k; ++j) h[j] = vdot(D->Q + (size_t)j * N, w, N);
+        for (int32_t j = 0; j < k; ++j) {
+            const double *qj = D->Q + (size_t)j * N;
+            for (int64_t i = 0; i < N; ++i) w[i] -= h[j] * qj[i];
+            rcol[j] += h[j];
+        }
+    }
+    double rkk = vnorm(w, N);
+    if (!(rkk > 1e-14 * nxi)) return; /* rank deficient: the pair is not stored */
+    for (int32_t j = 0; j < k; ++j) D->R[j * m + k] = rcol[j];
+    D->R[k * m + k] = rkk;
+    double *qk = D->Q + (size_t)k * N;
+    for (int64_t i = 0; i < N; ++i) qk[i] = w[i] / rkk;
+    memcpy(D->Z + (size_t)k * N, z, sizeof(double) * (size_t)N);
+    memcpy(D->Zt + (size_t)k * N, xi, sizeof(double) * (size_t)N);
+    D->count = k + 1;
+}
+
+static void aa_qr_direction(orc_dir *D, const double *r, double *d)
+{
+    int64_t N = D->N;
+    int32_t k = D->count, m = D->mem;
+    for (int64_t i = 0; i < N; ++i) d[i] = -r[i];
+    if (k == 0) return;
+    double t[64];
+    for (int32_t j = 0; j < k; ++j) t[j] = vdot(D->Q + (size_t)j * N, r, N);
+    for (int32_t j = k - 1; j >= 0; --j) {
+        double e = t[j];
+        for (int32_t p = j + 1; p < k; ++p) e -= D->R[j * m + p] * t[p];
+        t[j] = e / D->R[j * m + j];
+    }
+    for (int32_t j = 0; j < k; ++j) {
+        const double *zj = D->Z + (size_t)j * N, *xj = D->Zt + (size_t)j * N;
+        for (int64_t i = 0; i < N; ++i) d[i] -= t[j] * (zj[i] - xj[i]);
+    }
 }
 int32_t orc_dir_count(const orc_dir *D) { return D ? D->count : 0; }
 
@@ -747,6 +841,14 @@ int orc_dir_compute(orc_dir *D, const double *Ru, const double *z, const double 
         return 0;
     }
     if (have_pair && vdot(z, z, N) == 0.0) have_pair = 0; /* degenerate pair: not used */
+    if (D->kind == ORC_DIR_AA_QR) {
+        if (have_pair && D->mem > 0) {
+            if (D->count == D->mem) aa_qr_drop_oldest(D);
+            aa_qr_append(D, z, xi);
+        }
+        aa_qr_direction(D, Ru, d);
+        return 0;
+    }
     if (D->kind == ORC_DIR_RB) {
         if (!have_pair) {
             for (int64_t i = 0; i < N; ++i) d[i] = -Ru[i];

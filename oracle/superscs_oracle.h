@@ -52,7 +52,10 @@ typedef struct {
     int32_t ep, ed;  /* primal / dual exponential cones, 3 rows each, after the PSD rows */
 } orc_problem;
 
-enum { ORC_DIR_AA = 0, ORC_DIR_RB = 1, ORC_DIR_NONE = 2 };
+/* ORC_DIR_AA_QR: Anderson's acceleration with its least-squares problem solved
+ * through a QR factorisation of the window of residual differences, updated
+ * as pairs enter (Gram-Schmidt) and leave (Givens rotations) -- Sec. 4.4. */
+enum { ORC_DIR_AA = 0, ORC_DIR_RB = 1, ORC_DIR_NONE = 2, ORC_DIR_AA_QR = 3 };
 
 typedef struct {
     int32_t direction;   /* ORC_DIR_AA | ORC_DIR_RB | ORC_DIR_NONE (d = 0: pure KM) */

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsuperscs.so")
 
 SCS_OK, SCS_EINVAL, SCS_ENOMEM, SCS_ECUDA, SCS_ETIMEOUT = 0, -1, -2, -3, -4
 SOLVED, INFEASIBLE, UNBOUNDED, MAX_ITERS, TIME_LIMIT, NUMERICAL = 1, -1, -2, -3, -4, -5
-DIR_AA, DIR_RB, DIR_NONE = 0, 1, 2
+DIR_AA, DIR_RB, DIR_NONE, DIR_AA_QR = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 TEAM_AUTO, TEAM_BLOCK, TEAM_GRID = 0, 1, 2
 

@@ -23,6 +23,7 @@ __global__ void k_batch_handoff(const Args<float>* a32, const Args<double>* a64,
             for (long long j = threadIdx.x; j < cols; j += blockDim.x) {
                 w64.Zv[j] = (double)w32.Zv[j];
                 w64.Xv[j] = (double)w32.Xv[j];
+                if (w32.Qv && w64.Qv) w64.Qv[j] = (double)w32.Qv[j];
             }
             for (int j = threadIdx.x; j < nm; j += blockDim.x) {
                 w64.zp.v[j] = (double)w32.zp.v[j];
@@ -31,6 +32,7 @@ __global__ void k_batch_handoff(const Args<float>* a32, const Args<double>* a64,
             for (int j = threadIdx.x; j < (mem > 0 ? mem : 1); j += blockDim.x) {
                 w64.Zt[j] = w32.Zt[j];
                 w64.Xt[j] = w32.Xt[j];
+                if (w32.Qt && w64.Qt) w64.Qt[j] = w32.Qt[j];
             }
             if (threadIdx.x == 0) {
                 *w64.zp.t = *w32.zp.t;

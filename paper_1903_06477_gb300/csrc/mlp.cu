@@ -6,12 +6,15 @@
 // and runs on one of two BF16 kernels with FP32 accumulation: gemm_nt, the
 // warp-level MMA (m16n8k16) on 128x128x32 tiles staged by cp.async, or
 // gemm_nt_tc, tcgen05.mma with the accumulator in tensor memory.
+#include <cuda.h>  // CUtensorMap and its enums (types only: the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -163,23 +166,28 @@ __global__ void __launch_bounds__(NTH) gemm_nt(int M, int N, int K, const bf16* 
 // ---------------------------------------------------------------------------
 // The same product C = A B^T on the fifth-generation tensor cores.
 //
-// Both operands are staged in shared memory in the K-major layout without
-// swizzle that tcgen05.mma reads through a matrix descriptor: core matrices
-// of 8 rows x 16 bytes (8 BF16 along K) stored contiguously, LBO = 128 bytes
-// between the core matrices of one 8-row group along K, SBO = 1024 bytes
-// between 8-row groups (a 64-wide K block per stage).  One thread issues the
-// four 128 x 128 x 16 MMAs of a K block and commits them to that stage's
-// mbarrier; the accumulator tile (FP32, 128 lanes x 128 columns) lives in
-// tensor memory and the four warps read their 32 lanes back with tcgen05.ld
-// for the epilogue.  While the tensor core works on one stage, all threads
-// fill the other by cp.async (zero fill gives the tails in M, N and K).
-// Every wait is bounded; on expiry *err is set (1; 2 if the MMAs in flight did
-// not drain either) and the tile is not written.
+// Operands arrive by TMA: a 2D tensor map per operand (K innermost, rows
+// outer) copies 128-row x 64-column BF16 boxes into shared memory with the
+// 128-byte swizzle, zero-filling whatever lies past M, N or K, so the kernel
+// needs no tail logic.  A ring of TC_STAGES stages (one A and one B box each,
+// 32 KB) is filled by one producer lane (warp 0) and drained by one MMA lane
+// (warp 1), which issues the four 128 x 128 x 16 tcgen05.mma of a stage from
+// shared-memory descriptors (K-major, 128-byte swizzle, 1024 bytes between
+// 8-row groups; the 16-element K steps advance the start address by 32 bytes
+// inside the swizzle atom) and commits them to the stage's "empty" barrier,
+// which frees it for the producer.  The FP32 accumulator (128 lanes x 128
+// columns) lives in tensor memory, allocated by warp 1; after the last stage
+// a commit to the "done" barrier hands it to the four epilogue warps (2..5),
+// which read their lane quarter (warp % 4) with tcgen05.ld, apply bias, ReLU
+// mask and output conversion, and store.  With split-K (grid z > 1) each CTA
+// takes a contiguous range of K blocks and writes its FP32 partial tile to a
+// workspace that a second kernel sums in a fixed order (deterministic) before
+// the same epilogue.  Every wait is bounded; on expiry *err is set (1; 2 if
+// copies or MMAs in flight did not drain either) and the tile is not written.
 // ---------------------------------------------------------------------------
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_NTH = 128;
-constexpr int TC_TILE = TC_BM * TC_BK * 2;  // bytes of one operand block (16 KB)
-constexpr int TC_SMEM = 2 * 2 * TC_TILE;    // two stages of A and B
-constexpr unsigned TC_LBO = 128, TC_SBO = 1024;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4, TC_NTH = 192;
+constexpr int TC_TILE = TC_BM * TC_BK * 2;                 // bytes of one operand box (16 KB)
+constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE + 1024;    // + slack to align the ring to 1024 bytes
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 // kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
@@ -211,16 +219,14 @@ __device__ bool tc_wait(unsigned bar, unsigned parity)
         if (tc_now() - t0 > TC_WAIT_NS) return false;
     return true;
 }
-// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
-// SBO >> 4 (32-45), descriptor version 1 (bits 46-47), no swizzle (61-63 = 0)
-__device__ __forceinline__ unsigned long long tc_desc(unsigned addr)
+// shared-memory matrix descriptor, K-major with the 128-byte swizzle: start
+// >> 4 (bits 0-13), leading offset 16 bytes (unused by swizzled K-major
+// layouts, bits 16-29), stride offset 1024 bytes between 8-row groups (bits
+// 32-45), descriptor version 1 (bits 46-47), swizzle mode 2 = 128 bytes (bits 61-63)
+__device__ __forceinline__ unsigned long long tc_desc_sw128(unsigned addr)
 {
-    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)(TC_LBO >> 4) << 16) |
-           ((unsigned long long)(TC_SBO >> 4) << 32) | (1ull << 46);
-}
-__device__ __forceinline__ void tc_cp16(unsigned dst, const void* src, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 __device__ __forceinline__ void tc_mma(unsigned tmem, unsigned long long ad, unsigned long long bd, unsigned acc)
 {
@@ -230,135 +236,177 @@ __device__ __forceinline__ void tc_mma(unsigned tmem, unsigned long long ad, uns
         "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
         : "memory");
 }
-
-__global__ void __launch_bounds__(TC_NTH) gemm_nt_tc(int M, int N, int K, const bf16* __restrict__ A, int lda,
-                                                      const bf16* __restrict__ Bm, int ldb, Epi e, int* err)
+__device__ __forceinline__ void tc_tma_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar)
 {
-    extern __shared__ __align__(1024) unsigned char tc_sm[];
-    __shared__ __align__(8) unsigned long long bar[2];
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// one output element through the epilogue (bias, ReLU mask, ReLU, FP32 and/or BF16 store)
+__device__ __forceinline__ void epi_store(const Epi& e, int m, int n, float x)
+{
+    if (e.bias) x += e.bias[n];
+    if (e.mask && !((float)e.mask[(size_t)m * e.ldm + n] > 0.f)) x = 0.f;
+    if (e.relu) x = fmaxf(x, 0.f);
+    if (e.C32) e.C32[(size_t)m * e.ldc + n] = x;
+    if (e.C16) e.C16[(size_t)m * e.ldc16 + n] = __float2bfloat16(x);
+}
+
+__global__ void __launch_bounds__(TC_NTH, 1) gemm_nt_tc(const __grid_constant__ CUtensorMap ta,
+                                                         const __grid_constant__ CUtensorMap tb, int M, int N, int K,
+                                                         int kb_per_split, Epi e, float* ws, int* err)
+{
+    extern __shared__ unsigned char tc_dyn[];
+    __shared__ __align__(8) unsigned long long bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
     __shared__ unsigned tmem_slot;
+    __shared__ int fail_s, issued_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
-    const unsigned sbase = sa(tc_sm);
-    const unsigned bar0 = sa(&bar[0]);
-    if (warp == 0) {
+    const int KB = (K + TC_BK - 1) / TC_BK;
+    const int kb0 = blockIdx.z * kb_per_split, kb1 = min(KB, kb0 + kb_per_split);
+    const int nk = max(kb1 - kb0, 0);
+    // the ring starts at the first 1024-byte boundary (the swizzle pattern follows address bits)
+    const unsigned ring = (sa(tc_dyn) + 1023u) & ~1023u;
+    auto full = [&](int s) { return sa(&bar_full[s]); };
+    auto empty = [&](int s) { return sa(&bar_empty[s]); };
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full(s)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty(s)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar_done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail_s = 0;
+        issued_s = 0;
+    }
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_slot)),
                      "r"(TC_BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_slot;
-
-    auto load = [&](int st, int k0) {
-        const unsigned a_s = sbase + (unsigned)st * 2u * TC_TILE, b_s = a_s + TC_TILE;
-        for (int c = tid; c < TC_BM * (TC_BK / 8); c += TC_NTH) {
-            const int r = c >> 3, kc = c & 7;
-            const unsigned off = (unsigned)(r >> 3) * TC_SBO + (unsigned)kc * TC_LBO + (unsigned)(r & 7) * 16u;
-            const int gk = k0 + kc * 8;
-            const int gm = m0 + r;
-            int bytes = (gm < M && gk < K) ? min(16, (K - gk) * 2) : 0;
-            tc_cp16(a_s + off, bytes ? A + (size_t)gm * lda + gk : A, bytes);
-            const int gn = n0 + r;
-            bytes = (gn < N && gk < K) ? min(16, (K - gk) * 2) : 0;
-            tc_cp16(b_s + off, bytes ? Bm + (size_t)gn * ldb + gk : Bm, bytes);
+    if (warp == 0 && lane == 0) {
+        // producer: one stage = one A box and one B box (rows m0.. / n0.., K block kb0 + i)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&ta) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tb) : "memory");
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            if (i >= TC_STAGES && !tc_wait(empty(s), (unsigned)((i / TC_STAGES) - 1) & 1u)) {
+                atomicExch(&fail_s, 1);
+                break;
+            }
+            if (*(volatile int*)&fail_s) break;
+            const unsigned a_s = ring + (unsigned)s * 2u * TC_TILE, b_s = a_s + TC_TILE;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(2 * TC_TILE)
+                         : "memory");
+            const int kx = (kb0 + i) * TC_BK;  // a multiple of 64 elements: 128-byte aligned inner coordinate
+            tc_tma_2d(a_s, &ta, kx, m0, full(s));
+            tc_tma_2d(b_s, &tb, kx, n0, full(s));
+            issued_s = i + 1;
         }
-    };
-
-    const int KT = (K + TC_BK - 1) / TC_BK;
-    bool ok = true;
-    int committed = -1;  // last K block whose MMAs thread 0 committed (the same in every thread)
-    if (KT > 0) load(0, 0);
-    cp_commit();
-    for (int kt = 0; kt < KT; ++kt) {
-        const int st = kt & 1;
-        if (kt + 1 < KT) {
-            // stage st^1 is free once the MMAs of block kt-1 (its last reader) completed
-            if (kt >= 1 && !tc_wait(bar0 + 8u * (unsigned)(st ^ 1), (unsigned)((kt - 1) >> 1) & 1u)) ok = false;
-            if (ok) load(st ^ 1, (kt + 1) * TC_BK);
-            cp_commit();
-            cp_wait1();
-        } else {
-            cp_wait0();
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor-core reads
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            break;
-        }
-        committed = kt;
-        if (tid == 0) {
+    } else if (warp == 1 && lane == 0) {
+        // MMA lane
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            if (!tc_wait(full(s), (unsigned)(i / TC_STAGES) & 1u) || *(volatile int*)&fail_s) {
+                atomicExch(&fail_s, 1);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned a_s = sbase + (unsigned)st * 2u * TC_TILE, b_s = a_s + TC_TILE;
+            const unsigned a_s = ring + (unsigned)s * 2u * TC_TILE, b_s = a_s + TC_TILE;
 #pragma unroll
             for (int j = 0; j < TC_BK / 16; ++j)
-                tc_mma(tmem, tc_desc(a_s + (unsigned)j * 2u * TC_LBO), tc_desc(b_s + (unsigned)j * 2u * TC_LBO),
-                       (kt | j) != 0);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             bar0 + 8u * (unsigned)st)
+                tc_mma(tmem, tc_desc_sw128(a_s + (unsigned)j * 32u), tc_desc_sw128(b_s + (unsigned)j * 32u),
+                       (i | j) != 0);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(s))
                          : "memory");
         }
-    }
-    cp_wait0();
-    // completion of the last committed block implies completion of all earlier MMAs
-    const unsigned last_bar = bar0 + 8u * (unsigned)(committed & 1), last_par = (unsigned)(committed >> 1) & 1u;
-    if (ok && committed >= 0 && !tc_wait(last_bar, last_par)) ok = false;
-    ok = !__syncthreads_or(!ok);
-    if (ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int m = m0 + warp * 32 + lane;
+        // completion of the last commit implies completion of every earlier MMA
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sa(&bar_done))
+                     : "memory");
+    } else if (warp >= 2) {
+        // epilogue: wait for the accumulator, then lane quarter warp % 4 = rows m0 + 32 (warp % 4) + lane
+        // the tcgen05.ld below is warp-collective: decide once per warp
+        const bool ok = __all_sync(0xffffffffu, nk == 0 || tc_wait(sa(&bar_done), 0u));
+        if (!ok && lane == 0) atomicExch(&fail_s, 1);
+        const int failed = __shfl_sync(0xffffffffu, *(volatile int*)&fail_s, 0);
+        if (ok && !failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int q = warp & 3;
+            const int m = m0 + q * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-            unsigned v[32];
-            if (KT > 0) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            } else {
+            for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+                unsigned v[32];
+                if (nk > 0) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+                        "%30, %31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                } else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = 0u;
-            }
-            if (m < M) {
+                    for (int t = 0; t < 32; ++t) v[t] = 0u;
+                }
+                if (m < M) {
+                    if (ws) {
+                        // split-K partial tile (FP32, row stride N) of split blockIdx.z
+                        float* row = ws + ((size_t)blockIdx.z * M + m) * N;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int n = n0 + c0 + q;
-                    if (n >= N) break;
-                    float x = __uint_as_float(v[q]);
-                    if (e.bias) x += e.bias[n];
-                    if (e.mask && !((float)e.mask[(size_t)m * e.ldm + n] > 0.f)) x = 0.f;
-                    if (e.relu) x = fmaxf(x, 0.f);
-                    if (e.C32) e.C32[(size_t)m * e.ldc + n] = x;
-                    if (e.C16) e.C16[(size_t)m * e.ldc16 + n] = __float2bfloat16(x);
+                        for (int t = 0; t < 32; ++t)
+                            if (n0 + c0 + t < N) row[n0 + c0 + t] = __uint_as_float(v[t]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 32; ++t)
+                            if (n0 + c0 + t < N) epi_store(e, m, n0 + c0 + t, __uint_as_float(v[t]));
+                    }
                 }
             }
         }
-    } else {
-        // give MMAs still in flight a second bounded wait before the tensor memory is released;
-        // if that one expires too, MMAs may still write the columns about to be freed (and
-        // reallocated by a later CTA on this SM): report 2, which the host treats as fatal
-        const bool drained = committed < 0 || tc_wait(last_bar, last_par);
-        const bool undrained = __syncthreads_or(!drained);
-        if (tid == 0) atomicMax(err, undrained ? 2 : 1);
+    }
+    __syncwarp();
+    __syncthreads();
+    if (*(volatile int*)&fail_s && tid == 0) {
+        // before the stages and the tensor memory are released, copies still in flight and
+        // MMAs still in flight must finish: the producer reuses a stage only after its MMAs
+        // consumed it, so only the last TC_STAGES issued copies can be pending (each completes
+        // the phase (i / TC_STAGES) of its stage's "full" barrier), and the "done" commit,
+        // made after the MMA lane's last issue, completes once every MMA has
+        bool drained = true;
+        const int issued = issued_s;
+        for (int i = max(0, issued - TC_STAGES); i < issued; ++i)
+            if (!tc_wait(full(i % TC_STAGES), (unsigned)(i / TC_STAGES) & 1u)) drained = false;
+        if (!tc_wait(sa(&bar_done), 0u)) drained = false;
+        atomicMax(err, drained ? 1 : 2);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+}
+
+// split-K: C = epilogue(sum over z of ws[z]) in a fixed order
+__global__ void splitk_epilogue(const float* ws, int splits, int M, int N, Epi e)
+{
+    const long long total = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int z = 0; z < splits; ++z) acc += ws[(size_t)z * total + i];
+        epi_store(e, (int)(i / N), (int)(i % N), acc);
+    }
 }
 
 // out (C x R, ld_out) = in (R x C, ld_in)^T, BF16, 32 x 32 tiles
@@ -548,6 +596,8 @@ struct scs_mlp {
     int step;
     int gemm_impl;  // SCS_MLP_GEMM_MMA or SCS_MLP_GEMM_TCGEN05
     int lastB;      // rows of the last batch that went through forward()
+    float* ws;      // split-K partial tiles of the tensor-core GEMMs
+    size_t ws_floats;
     char* arena;
 };
 
@@ -572,20 +622,100 @@ static const char* const TC_FATAL_MSG =
     "mlp: a tensor-core GEMM released tensor memory while its MMAs may still have been running; "
     "results of this CUDA context can no longer be trusted, every later GEMM call fails";
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// tensor map of a row-major BF16 operand (rows x K, row stride ld elements): boxes of
+// TC_BM rows x TC_BK columns, 128-byte swizzle, zero fill past the extents
+static int operand_map(CUtensorMap* map, const bf16* base, int rows, int K, int ld)
+{
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) {
+        sscs::record_error("mlp: cuTensorMapEncodeTiled is unavailable");
+        return SCS_ECUDA;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "mlp: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        sscs::record_error(buf);
+        return SCS_ECUDA;
+    }
+    return SCS_OK;
+}
+
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return sms > 0 ? sms : 1;
+}
+
+// K splits for a tcgen05 product: when its 128 x 128 tiles would leave most SMs idle and
+// K is deep, split K (at least 4 K blocks a split) as far as the workspace allows
+static int tc_splits(int M, int N, int K, size_t ws_floats)
+{
+    const int tiles = ((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
+    const int KB = (K + TC_BK - 1) / TC_BK;
+    const int sms = device_sms();
+    if (ws_floats == 0 || 2 * tiles > sms || KB < 8) return 1;
+    int sp = std::min((sms + tiles - 1) / tiles, KB / 4);
+    while (sp > 1 && (size_t)sp * M * N > ws_floats) --sp;
+    if (sp < 2) return 1;
+    const int per = (KB + sp - 1) / sp;
+    return (KB + per - 1) / per;
+}
+
 static int launch_gemm(int impl, cudaStream_t st, int* err, int M, int N, int K, const bf16* A, int lda,
-                       const bf16* B, int ldb, const Epi& e)
+                       const bf16* B, int ldb, const Epi& e, float* ws = nullptr, size_t ws_floats = 0)
 {
     if (g_tc_fatal) {
         sscs::record_error(TC_FATAL_MSG);
         return SCS_ECUDA;
     }
     if (impl == SCS_MLP_GEMM_TCGEN05) {
+        CUtensorMap ta, tb;
+        int rc;
+        if ((rc = operand_map(&ta, A, M, K, lda)) || (rc = operand_map(&tb, B, N, K, ldb))) return rc;
+        const int KB = (K + TC_BK - 1) / TC_BK;
+        const int splits = tc_splits(M, N, K, ws_floats);
+        const int per = (KB + splits - 1) / splits;
         // a per-device attribute: set before every launch (a host call of about a microsecond)
         MCU(cudaFuncSetAttribute(gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-        dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
-        gemm_nt_tc<<<grid, TC_NTH, TC_SMEM, st>>>(M, N, K, A, lda, B, ldb, e, err);
-        const cudaError_t ce = cudaGetLastError();
-        return ce == cudaSuccess ? SCS_OK : mlp_err("gemm_nt_tc launch", ce);
+        dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, splits);
+        gemm_nt_tc<<<grid, TC_NTH, TC_SMEM, st>>>(ta, tb, M, N, K, per, e, splits > 1 ? ws : nullptr, err);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return mlp_err("gemm_nt_tc launch", ce);
+        if (splits > 1) {
+            const long long total = (long long)M * N;
+            splitk_epilogue<<<(int)std::min<long long>(8192, (total + 255) / 256), 256, 0, st>>>(ws, splits, M, N, e);
+            ce = cudaGetLastError();
+            if (ce != cudaSuccess) return mlp_err("splitk_epilogue launch", ce);
+        }
+        return SCS_OK;
     }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     gemm_nt<<<grid, NTH, 0, st>>>(M, N, K, A, lda, B, ldb, e);
@@ -594,7 +724,7 @@ static int launch_gemm(int impl, cudaStream_t st, int* err, int M, int N, int K,
 }
 static int gemm(scs_mlp* n, int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const Epi& e)
 {
-    return launch_gemm(n->gemm_impl, n->st, n->err, M, N, K, A, lda, B, ldb, e);
+    return launch_gemm(n->gemm_impl, n->st, n->err, M, N, K, A, lda, B, ldb, e, n->ws, n->ws_floats);
 }
 // reads (and clears) the tensor-core GEMM's timeout flag; the stream must be synchronised
 static int check_err_flag(scs_mlp* n)
@@ -694,6 +824,9 @@ extern "C" int scs_mlp_create(int32_t din, int32_t dh, int32_t dout, int32_t max
     take((void**)&n->part, sizeof(double) * 8192);
     take((void**)&n->loss, sizeof(double) * 2);
     take((void**)&n->err, sizeof(int) * 4);
+    // split-K workspace: up to 16 partial tiles of the widest batch-row product
+    n->ws_floats = (size_t)16 * maxB * (size_t)std::max(std::max(dh, din), 128);
+    take((void**)&n->ws, sizeof(float) * n->ws_floats);
     for (auto& pl : plan) off += (pl.second + 255) & ~size_t(255);
     cudaError_t e = cudaMalloc((void**)&n->arena, off);
     if (e != cudaSuccess) {
@@ -905,16 +1038,30 @@ extern "C" int scs_mlp_gemm_nt(int32_t impl, int32_t M, int32_t N, int32_t K, co
     }
     int* err = nullptr;
     MCU(cudaMalloc((void**)&err, sizeof(int)));
+    // the split-K workspace this product would use (tensor-core kernel only)
+    float* ws = nullptr;
+    size_t ws_floats = 0;
+    if (impl == SCS_MLP_GEMM_TCGEN05) {
+        const int sp = tc_splits(M, N, K, (size_t)1 << 40);
+        if (sp > 1) {
+            ws_floats = (size_t)sp * M * N;
+            if (cudaMalloc((void**)&ws, sizeof(float) * ws_floats) != cudaSuccess) {
+                cudaFree(err);
+                return mlp_err("cudaMalloc", cudaGetLastError());
+            }
+        }
+    }
     int rc = SCS_OK;
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) rc = mlp_err("memset", cudaGetLastError());
     if (!rc)
         rc = launch_gemm(impl, st, err, M, N, K, static_cast<const bf16*>(A), lda, static_cast<const bf16*>(B), ldb,
-                         epi(nullptr, nullptr, 0, 0, C, ldc, nullptr, 0));
+                         epi(nullptr, nullptr, 0, 0, C, ldc, nullptr, 0), ws, ws_floats);
     int h = 0;
     if (!rc && cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = mlp_err("copy", cudaGetLastError());
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = mlp_err("gemm", cudaGetLastError());
     cudaFree(err);
+    if (ws) cudaFree(ws);
     if (!rc && h) {
         if (h >= 2) g_tc_fatal = true;
         sscs::record_error(h >= 2 ? TC_FATAL_MSG : "scs_mlp_gemm_nt: a tensor-core wait timed out");

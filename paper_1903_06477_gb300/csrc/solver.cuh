@@ -184,6 +184,8 @@ struct DevWork {
     double* Zt;  // mem columns (AA: z^i; RB: z^i)
     T* Xv;
     double* Xt;  // mem columns (AA: xi^i; RB: z~^i)
+    T* Qv;
+    double* Qt;  // AA with QR: mem orthonormal columns, Xi (oldest first) = Q R
     double *io_in, *io_out, *io_out2;      // N-vectors of the single-operator entries
     double* warm;                          // N: warm start (FP64)
     double *x_out, *y_out, *s_out, *u_out; // results (FP64)
@@ -1686,6 +1688,203 @@ __device__ void aa_direction(Team& tm, const DevProb<T>& P, const DevWork<T>& W,
     tm.sync();
 }
 
+// Anderson's acceleration with the least squares min ||Xi t - Ru|| solved
+// through Xi = Q R (Sec. 4.4: an updated QR factorisation in place of the
+// normal equations).  Q's columns are kept oldest first in W.Qv/W.Qt, R
+// (upper triangular, row stride AAMAX) in the CTA's shared array G; Z and Xi
+// stay in their ring slots (the oldest pair at (inserted - count) mod mem).
+//  - a full window drops its oldest pair: R without its first column is upper
+//    Hessenberg; Givens rotations (j, j+1), j = 0..k-2, restore the triangle
+//    (computed by thread 0 of every CTA from identical data) and one pass
+//    applies them to Q's columns, carrying column j+1 in a register;
+//  - a new pair enters by two rounds of classical Gram-Schmidt (dots in
+//    chunks of 8 per reduction); a remainder below 1e-14 ||xi|| is rank
+//    deficient and the pair is not stored;
+//  - t solves R t = Q^T Ru, d = -Ru - sum_j t_j (Z_j - Xi_j).
+template <typename T, class Team>
+__device__ void aa_qr_direction(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S,
+                                bool have_pair, double nz2, DirState& ds, double* R, double* sm_h, double* sm_cs,
+                                double* sm_t)
+{
+    const int nm = P.n + P.m;
+    const int mem = S.mem;
+    auto qcol = [&](int j) { return W.Qv + (size_t)j * nm; };
+    auto slot_of = [&](int j) { return (int)((ds.inserted - ds.count + j) % mem); };  // ring slot of pair j
+    if (have_pair && mem > 0 && nz2 > 0.0) {
+        if (ds.count == mem) {
+            const int k = ds.count;
+            if (threadIdx.x == 0) {
+                for (int j = 0; j + 1 < k; ++j) {
+                    const double a = R[j * AAMAX + j + 1], b = R[(j + 1) * AAMAX + j + 1];
+                    const double h = hypot(a, b);
+                    const double c = h > 0.0 ? a / h : 1.0, sn = h > 0.0 ? b / h : 0.0;
+                    for (int col = j + 1; col < k; ++col) {
+                        const double x = R[j * AAMAX + col], y = R[(j + 1) * AAMAX + col];
+                        R[j * AAMAX + col] = c * x + sn * y;
+                        R[(j + 1) * AAMAX + col] = -sn * x + c * y;
+                    }
+                    sm_cs[2 * j] = c;
+                    sm_cs[2 * j + 1] = sn;
+                }
+                for (int r = 0; r + 1 < k; ++r)
+                    for (int col = 0; col + 1 < k; ++col) R[r * AAMAX + col] = col >= r ? R[r * AAMAX + col + 1] : 0.0;
+                for (int col = 0; col < k; ++col) R[(k - 1) * AAMAX + col] = 0.0;
+            }
+            __syncthreads();
+            for (int i = tm.rank(); i < nm; i += tm.size()) {
+                T x = qcol(0)[i];
+                for (int j = 0; j + 1 < k; ++j) {
+                    const T y = qcol(j + 1)[i];
+                    const T c = (T)sm_cs[2 * j], sn = (T)sm_cs[2 * j + 1];
+                    qcol(j)[i] = c * x + sn * y;
+                    x = -sn * x + c * y;
+                }
+            }
+            if (tm.leader()) {
+                double x = W.Qt[0];
+                for (int j = 0; j + 1 < k; ++j) {
+                    const double y = W.Qt[j + 1];
+                    W.Qt[j] = sm_cs[2 * j] * x + sm_cs[2 * j + 1] * y;
+                    x = -sm_cs[2 * j + 1] * x + sm_cs[2 * j] * y;
+                }
+            }
+            ds.count = k - 1;
+            tm.sync();
+        }
+        // append xi: the new column k of Q is built in place
+        const int k = ds.count;
+        const T* xi = W.xip.v;
+        const double xit = *W.xip.t;
+        T* w = qcol(k);
+        double nxi2 = 0.0;
+        for (int round = 0; round < 2; ++round) {
+            const T* src = round == 0 ? xi : w;
+            const double srct = round == 0 ? xit : W.Qt[k];
+            // h_j = <q_j, src>, chunks of 8 (the first chunk of round 0 also reduces ||xi||^2)
+            for (int j0 = 0; j0 < (k > 0 ? k : 1); j0 += 8) {
+                T a[8];
+                T x2 = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] = 0;
+                for (int i = tm.rank(); i < nm; i += tm.size()) {
+                    const T v = src[i];
+                    if (round == 0 && j0 == 0) x2 += v * v;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (j0 + q < k) a[q] += qcol(j0 + q)[i] * v;
+                }
+                double red[9];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) red[q] = (double)a[q];
+                red[8] = (double)x2;
+                if (tm.leader()) {
+                    if (round == 0 && j0 == 0) red[8] += srct * srct;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (j0 + q < k) red[q] += W.Qt[j0 + q] * srct;
+                }
+                tm.reduce(red);
+                if (round == 0 && j0 == 0) nxi2 = red[8];
+                if (threadIdx.x == 0)
+                    for (int q = 0; q < 8 && j0 + q < k; ++q) sm_h[j0 + q] = red[q];
+            }
+            __syncthreads();
+            // w = src - Q h (and ||w||^2 after the second round); R's new column accumulates h
+            T ww = 0;
+            for (int i = tm.rank(); i < nm; i += tm.size()) {
+                T v = src[i];
+                for (int j = 0; j < k; ++j) v -= (T)sm_h[j] * qcol(j)[i];
+                w[i] = v;
+                ww += v * v;
+            }
+            double red2[1] = {(double)ww};
+            if (tm.leader()) {
+                double v = srct;
+                for (int j = 0; j < k; ++j) v -= sm_h[j] * W.Qt[j];
+                W.Qt[k] = v;
+                red2[0] += v * v;
+            }
+            tm.reduce(red2);
+            if (threadIdx.x == 0)
+                for (int j = 0; j < k; ++j) R[j * AAMAX + k] = (round == 0 ? 0.0 : R[j * AAMAX + k]) + sm_h[j];
+            if (round == 1 && threadIdx.x == 0) sm_t[0] = red2[0];  // ||w||^2 after the second round
+            __syncthreads();
+        }
+        const double rkk = sqrt(sm_t[0]);
+        if (rkk > 1e-14 * sqrt(nxi2)) {
+            const T inv = (T)(1.0 / rkk);
+            const int slot = (int)(ds.inserted % mem);
+            HV<T> Zs = col(W.Zv, W.Zt, slot, nm), Xs = col(W.Xv, W.Xt, slot, nm);
+            for (int i = tm.rank(); i < nm; i += tm.size()) {
+                w[i] *= inv;
+                Zs.v[i] = W.zp.v[i];
+                Xs.v[i] = xi[i];
+            }
+            if (tm.leader()) {
+                W.Qt[k] /= rkk;
+                *Zs.t = *W.zp.t;
+                *Xs.t = xit;
+            }
+            if (threadIdx.x == 0) R[k * AAMAX + k] = rkk;
+            ds.inserted++;
+            ds.count++;
+        }
+        tm.sync();
+    }
+    const int k = ds.count;
+    if (k == 0) {
+        for (int i = tm.rank(); i < nm; i += tm.size()) W.d.v[i] = -W.Ru.v[i];
+        if (tm.leader()) *W.d.t = -*W.Ru.t;
+        tm.sync();
+        return;
+    }
+    // Q^T Ru, then R t = Q^T Ru by back substitution (thread 0 of every CTA)
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        T a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = 0;
+        for (int i = tm.rank(); i < nm; i += tm.size()) {
+            const T r = W.Ru.v[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < k) a[q] += qcol(j0 + q)[i] * r;
+        }
+        double red[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[q] = (double)a[q];
+        if (tm.leader()) {
+            const double rt = *W.Ru.t;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < k) red[q] += W.Qt[j0 + q] * rt;
+        }
+        tm.reduce(red);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 8 && j0 + q < k; ++q) sm_t[j0 + q] = red[q];
+    }
+    if (threadIdx.x == 0)
+        for (int j = k - 1; j >= 0; --j) {
+            double e = sm_t[j];
+            for (int p = j + 1; p < k; ++p) e -= R[j * AAMAX + p] * sm_t[p];
+            sm_t[j] = e / R[j * AAMAX + j];
+        }
+    __syncthreads();
+    for (int i = tm.rank(); i < nm; i += tm.size()) {
+        T di = -W.Ru.v[i];
+        for (int j = 0; j < k; ++j) {
+            const size_t o = (size_t)slot_of(j) * nm + i;
+            di -= (T)sm_t[j] * (W.Zv[o] - W.Xv[o]);
+        }
+        W.d.v[i] = di;
+    }
+    if (tm.leader()) {
+        double di = -*W.Ru.t;
+        for (int j = 0; j < k; ++j) di -= sm_t[j] * (W.Zt[slot_of(j)] - W.Xt[slot_of(j)]);
+        *W.d.t = di;
+    }
+    tm.sync();
+}
+
 // Restarted Broyden, Algorithm 2 (readings: m' = stored pairs; restart when
 // m' = mem empties the buffers without storing the current pair; the
 // denominator of z~ is <z, H xi~>; sgn(0) = 1).
@@ -1904,7 +2103,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         ds.count = R->count;
         ds.inserted = R->inserted;
         nu_q = R->nu;
-        if (S.direction == 0)
+        if (S.direction == 0 || S.direction == 3)  // the Gram matrix, or R of the QR variant
             for (int i = threadIdx.x; i < AAMAX * AAMAX; i += blockDim.x) G[i] = R->G[i];
         __syncthreads();
     }
@@ -1967,6 +2166,8 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         // direction d (Sec. 4.4)
         if (S.direction == 0)
             aa_direction(tm, P, W, S, have_pair, nz2, ds, G, sm_rhs, sm_L, sm_t);
+        else if (S.direction == 3)
+            aa_qr_direction(tm, P, W, S, have_pair, nz2, ds, G, sm_rhs, sm_L, sm_t);
         else if (S.direction == 1)
             rb_direction(tm, P, W, S, have_pair, nz2, ds);
         else {
@@ -2082,7 +2283,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             R->r_safe = r_safe;
             R->nz2 = nz2;
         }
-        if (tm.block() == 0 && S.direction == 0)
+        if (tm.block() == 0 && (S.direction == 0 || S.direction == 3))
             for (int i = threadIdx.x; i < AAMAX * AAMAX; i += blockDim.x) R->G[i] = G[i];
     }
     write_outputs(tm, P, W, status, to);

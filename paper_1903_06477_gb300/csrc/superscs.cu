@@ -382,8 +382,8 @@ static void finish_layouts(HostProb& H, bool sell_A, bool sell_T)
 static int check_settings(const scs_settings* S, char* err)
 {
     if (!S) { set_err(err, "settings must not be NULL"); return SCS_EINVAL; }
-    if (S->direction < 0 || S->direction > 2) { set_err(err, "bad direction %d", S->direction); return SCS_EINVAL; }
-    if (S->direction == SCS_DIR_AA && (S->mem < 0 || S->mem > AAMAX)) { set_err(err, "AA mem must be in 0..%d", AAMAX); return SCS_EINVAL; }
+    if (S->direction < 0 || S->direction > 3) { set_err(err, "bad direction %d", S->direction); return SCS_EINVAL; }
+    if ((S->direction == SCS_DIR_AA || S->direction == SCS_DIR_AA_QR) && (S->mem < 0 || S->mem > AAMAX)) { set_err(err, "AA mem must be in 0..%d", AAMAX); return SCS_EINVAL; }
     if (S->direction == SCS_DIR_RB && (S->mem < 0 || S->mem > MAXMEM)) { set_err(err, "RB mem must be in 0..%d", MAXMEM); return SCS_EINVAL; }
     if (!(S->eps > 0) || S->max_iters < 0 || S->ls_max < 0 || S->cg_max < 0) { set_err(err, "bad tolerances or caps"); return SCS_EINVAL; }
     if (!(S->lambda > 0 && S->lambda < 2)) { set_err(err, "lambda must lie in (0,2)"); return SCS_EINVAL; }
@@ -411,7 +411,7 @@ struct Arena {
 
 // layout of one instance's data and work in precision T; base == nullptr only measures
 template <typename T>
-static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevProb<T>& P, DevWork<T>& W,
+static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, int max_blocks, DevProb<T>& P, DevWork<T>& W,
                     const int* shared_idx /* index arrays shared with another precision or null */,
                     DevState* st_ext = nullptr)
 {
@@ -492,6 +492,8 @@ static void lay_out(Arena& A, const HostProb& H, int mem, int max_blocks, DevPro
     W.Xv = A.take<T>((size_t)mm * nm);
     W.Zt = A.take<double>(mm);
     W.Xt = A.take<double>(mm);
+    W.Qv = qr ? A.take<T>((size_t)mm * nm) : nullptr;
+    W.Qt = qr ? A.take<double>(mm) : nullptr;
     W.io_in = A.take<double>(nm + 1);
     W.io_out = A.take<double>(nm + 1);
     W.io_out2 = A.take<double>(nm + 1);
@@ -525,6 +527,11 @@ static cudaError_t widen_memory(const DevWork<float>& W32, const DevWork<double>
     cudaError_t e;
     if ((e = launch_f2d(W32.Zv, W64.Zv, cols, st)) != cudaSuccess) return e;
     if ((e = launch_f2d(W32.Xv, W64.Xv, cols, st)) != cudaSuccess) return e;
+    if (W32.Qv && W64.Qv) {
+        if ((e = launch_f2d(W32.Qv, W64.Qv, cols, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(W64.Qt, W32.Qt, sizeof(double) * std::max(mem, 1), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return e;
+    }
     if ((e = launch_f2d(W32.zp.v, W64.zp.v, nm, st)) != cudaSuccess) return e;
     if ((e = launch_f2d(W32.xip.v, W64.xip.v, nm, st)) != cudaSuccess) return e;
     const size_t tb = sizeof(double) * std::max(mem, 1);
@@ -861,17 +868,18 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     DevProb<float> P32{};
     DevWork<float> W32{};
     const int mem = std::max(settings->mem, 1);
-    lay_out<double>(A, H, mem, w->D.grid, P64, W64, nullptr);
-    if (w->has32) lay_out<float>(A, H, mem, w->D.grid, P32, W32, (const int*)1);
+    const bool qr = settings->direction == SCS_DIR_AA_QR;
+    lay_out<double>(A, H, mem, qr, w->D.grid, P64, W64, nullptr);
+    if (w->has32) lay_out<float>(A, H, mem, qr, w->D.grid, P32, W32, (const int*)1);
     size_t bytes = A.off + sizeof(Args<double>) + sizeof(Args<float>) + 1024;
     ce = cudaMalloc((void**)&w->arena, bytes);
     if (ce != cudaSuccess) { set_err(w->err, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(ce)); memcpy(g_err, w->err, 512); delete w; return SCS_ENOMEM; }
     w->arena_bytes = bytes;
     A.off = 0;
     A.base = w->arena;
-    lay_out<double>(A, H, mem, w->D.grid, w->P64, w->W64, nullptr);
+    lay_out<double>(A, H, mem, qr, w->D.grid, w->P64, w->W64, nullptr);
     if (w->has32) {
-        lay_out<float>(A, H, mem, w->D.grid, w->P32, w->W32, (const int*)1);
+        lay_out<float>(A, H, mem, qr, w->D.grid, w->P32, w->W32, (const int*)1);
         w->P32.A.ptr = w->P64.A.ptr;
         w->P32.A.col = w->P64.A.col;
         w->P32.A.perm = w->P64.A.perm;
@@ -1354,6 +1362,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     const int mem = std::max(settings->mem, 1);
+    const bool qr = settings->direction == SCS_DIR_AA_QR;
     b->hoff.resize(B + 1, 0);
     for (int qi = 0; qi < B; ++qi) {
         const HostProb& h = b->H[b->order[qi]];
@@ -1368,7 +1377,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
         DevState* st32 = A.take<DevState>(B);
         for (int qi = 0; qi < B; ++qi) {
             const HostProb& h = b->H[b->order[qi]];
-            lay_out<double>(A, h, mem, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
+            lay_out<double>(A, h, mem, qr, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
             b->a64[qi].slot = 0;
             if (real && b->shared && qi > 0) {
                 b->a64[qi].P.A = b->a64[0].P.A;
@@ -1378,7 +1387,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
                 b->a64[qi].P.s_off = b->a64[0].P.s_off;
             }
             if (b->has32) {
-                lay_out<float>(A, h, mem, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
+                lay_out<float>(A, h, mem, qr, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
                 b->a32[qi].slot = 0;
                 if (real) {
                     DevProb<float>& p = b->a32[qi].P;

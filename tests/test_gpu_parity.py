@@ -79,12 +79,12 @@ def test_linsys_and_T_parity(name, team):
 
 
 @pytest.mark.parametrize("team", TEAMS)
-@pytest.mark.parametrize("direction", [B.DIR_AA, B.DIR_RB])
+@pytest.mark.parametrize("direction", [B.DIR_AA, B.DIR_RB, B.DIR_AA_QR])
 @pytest.mark.parametrize("name", list(PROBS))
 def test_solve_parity_fp64(name, direction, team):
     prob = PROBS[name]
     eps = 1e-6
-    c0 = 0.99 if direction == B.DIR_AA else 0.1
+    c0 = 0.1 if direction == B.DIR_RB else 0.99
     kw = dict(direction=direction, mem=10, c0=c0, eps=eps, max_iters=20000, cg_rtol=1e-12)
     work = B.Work(prob, team=team, **kw)
     x, y, s, info = work.solve()
@@ -123,7 +123,7 @@ def test_km_iterates_match_oracle():
 
 
 @pytest.mark.parametrize("branch", ["K0", "K1"])
-@pytest.mark.parametrize("direction,mem", [(B.DIR_AA, 3), (B.DIR_RB, 2)])
+@pytest.mark.parametrize("direction,mem", [(B.DIR_AA, 3), (B.DIR_RB, 2), (B.DIR_AA_QR, 3), (B.DIR_AA_QR, 5)])
 def test_k0_k1_iterates_match_oracle(direction, mem, branch):
     """Every step forced to K0 (c0 = 1e300) or to K1 at alpha = 1 (c0 = 0,
     c1 = 1e300): u+ = u + d with Anderson or restarted Broyden directions (on
@@ -134,7 +134,7 @@ def test_k0_k1_iterates_match_oracle(direction, mem, branch):
     iters = 12
     forced = dict(c0=1e300) if branch == "K0" else dict(c0=0.0, c1=1e300)
     kw = dict(direction=direction, mem=mem, eps=1e-30, max_iters=iters, cg_rtol=1e-14, cg_max=5000, **forced)
-    okw = dict(kw, direction=O.DIR_AA if direction == B.DIR_AA else O.DIR_RB)
+    okw = dict(kw, direction={B.DIR_AA: O.DIR_AA, B.DIR_RB: O.DIR_RB, B.DIR_AA_QR: O.DIR_AA_QR}[direction])
     ref = O.Oracle(prob, **okw).solve()
     key = "k0" if branch == "K0" else "k1"
     assert getattr(ref["info"], key) == iters

@@ -76,11 +76,14 @@ def test_rb_mem0_uses_only_current_pair():
         assert D.count == 0
 
 
+@pytest.mark.parametrize("kind", [O.DIR_AA, O.DIR_AA_QR])
 @pytest.mark.parametrize("mem", [1, 3, 5, 10])
-def test_aa_matches_lstsq(mem):
+def test_aa_matches_lstsq(mem, kind):
+    # both least-squares solvers of the AA direction (regularised normal equations, and
+    # the QR factorisation updated as pairs enter and leave the window) against lstsq
     N = 40
     rng = np.random.default_rng(20 + mem)
-    D = O.Direction(O.DIR_AA, N, mem, aa_reg=1e-14)
+    D = O.Direction(kind, N, mem, aa_reg=1e-14)
     Zs, Xs = [], []
     D(rng.standard_normal(N))
     for it in range(2 * mem + 2):
@@ -130,3 +133,17 @@ def test_aa_mem0_is_minus_residual():
     D(rng.standard_normal(N))
     Ru = rng.standard_normal(N)
     np.testing.assert_allclose(D(Ru, rng.standard_normal(N), rng.standard_normal(N)), -Ru)
+
+
+def test_aa_qr_skips_rank_deficient_pair():
+    # a pair whose xi lies in the span of the stored ones is not stored by the QR variant
+    N = 20
+    rng = np.random.default_rng(8)
+    D = O.Direction(O.DIR_AA_QR, N, 4)
+    D(rng.standard_normal(N))
+    x1, x2 = rng.standard_normal(N), rng.standard_normal(N)
+    D(rng.standard_normal(N), rng.standard_normal(N), x1)
+    D(rng.standard_normal(N), rng.standard_normal(N), x2)
+    assert D.count == 2
+    D(rng.standard_normal(N), rng.standard_normal(N), 0.3 * x1 - 2.0 * x2)
+    assert D.count == 2

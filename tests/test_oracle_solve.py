@@ -59,12 +59,13 @@ def _k0_oracle_path(prob, direction, mem, iters, branch="K0", **extra):
     return path
 
 
+@pytest.mark.parametrize("kind", [O.DIR_AA, O.DIR_AA_QR])
 @pytest.mark.parametrize("branch", ["K0", "K1"])
 @pytest.mark.parametrize("mem", [1, 3, 5])
-def test_k0_path_is_anderson_acceleration(mem, branch):
+def test_k0_path_is_anderson_acceleration(mem, branch, kind):
     prob = W.planted(seed=21, n=40, l=30, soc=[4, 4], f=2, nnz=500)
     iters = 12
-    path = _k0_oracle_path(prob, O.DIR_AA, mem, iters, branch=branch, aa_reg=1e-15)
+    path = _k0_oracle_path(prob, kind, mem, iters, branch=branch, aa_reg=1e-15)
     ref = O.Oracle(prob, cg_rtol=1e-15, cg_max=10000)
     # Anderson acceleration (Walker and Ni) of g = T: f = g(u) - u = -Ru,
     # u+ = g(u) - G gamma with gamma = argmin ||f - F gamma|| over the last
