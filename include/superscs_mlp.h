@@ -107,15 +107,18 @@ void scs_mlp_destroy(scs_mlp *mlp);
 #define SCS_MLP_READ_W3T 22
 int scs_mlp_read(scs_mlp *mlp, int32_t what, void *out, int64_t *rows, int64_t *cols, int32_t *elem_bytes);
 
-/* GEMM kernels of the network.  SCS_MLP_GEMM_MMA: warp-level BF16 MMA
- * (m16n8k16) from shared memory.  SCS_MLP_GEMM_TCGEN05: fifth-generation
- * tensor cores (tcgen05.mma, accumulator in tensor memory), 128 x 128 tiles.
- * Both compute C = A B^T in FP32 from BF16 operands; their results differ
- * only in FP32 summation order. */
+/* GEMM kernels of the network.  SCS_MLP_GEMM_TCGEN05 (the default):
+ * fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory),
+ * 128 x 128 tiles fed by TMA from tensor maps (128-byte swizzle, a four-stage
+ * ring, producer / MMA / epilogue warps), K split across CTAs with a
+ * fixed-order reduction when the tiles alone would leave most SMs idle.
+ * SCS_MLP_GEMM_MMA: warp-level BF16 MMA (m16n8k16) from shared memory.  Both
+ * compute C = A B^T in FP32 from BF16 operands; their results differ only in
+ * FP32 summation order, and each is deterministic. */
 #define SCS_MLP_GEMM_MMA 0
 #define SCS_MLP_GEMM_TCGEN05 1
 
-/* Choose the GEMM kernel of a network (default SCS_MLP_GEMM_MMA). */
+/* Choose the GEMM kernel of a network (default SCS_MLP_GEMM_TCGEN05). */
 int scs_mlp_set_gemm(scs_mlp *mlp, int32_t impl);
 
 /* C (M x N, FP32, row stride ldc) = A (M x K, BF16, row stride lda) times

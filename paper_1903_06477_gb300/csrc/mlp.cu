@@ -3,9 +3,9 @@
 //
 // Every product is written as C = A B^T with both operands K-contiguous (the
 // backward pass works on transposed copies made by a tiled transpose kernel)
-// and runs on one of two BF16 kernels with FP32 accumulation: gemm_nt, the
-// warp-level MMA (m16n8k16) on 128x128x32 tiles staged by cp.async, or
-// gemm_nt_tc, tcgen05.mma with the accumulator in tensor memory.
+// and runs on one of two BF16 kernels with FP32 accumulation: gemm_nt_tc
+// (default), tcgen05.mma fed by TMA with the accumulator in tensor memory, or
+// gemm_nt, the warp-level MMA (m16n8k16) on 128x128x32 tiles staged by cp.async.
 #include <cuda.h>  // CUtensorMap and its enums (types only: the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -776,7 +776,7 @@ extern "C" int scs_mlp_create(int32_t din, int32_t dh, int32_t dout, int32_t max
     n->maxB = maxB;
     n->ldin = pad8(din);
     n->ldout = pad8(dout);
-    n->gemm_impl = SCS_MLP_GEMM_MMA;
+    n->gemm_impl = SCS_MLP_GEMM_TCGEN05;
     n->st = (cudaStream_t)stream;
     const int Bp = pad8(maxB);
     n->oW1 = 0;

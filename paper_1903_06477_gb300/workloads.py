@@ -403,3 +403,82 @@ def logreg(seed=0, p=100, q=120, lam=10.0, density=1.0, frac_nz=0.1):
     c = np.concatenate([np.zeros(p), lam * np.ones(p), np.ones(q), np.zeros(2 * q)])
     return dict(A=A, b=b, c=c, f=0, l=l, q=[], s=[], ep=2 * q, ed=0,
                 meta=dict(p=p, q=q, lam=lam, samples=Asmp, w0=w0))
+
+
+def lasso_paper(seed=0, n=631, kappa=10.0, mu_frac=0.1, frac_nz=0.1, noise=0.01):
+    """The LASSO family of Sec. 5.3: F of m = ceil(n/5) rows and n columns with
+    condition number kappa, in the epigraph form of `lasso`.  Readings (the
+    paper does not say how kappa is imposed or what scale mu has): F = U
+    diag(sigma) V^T with U, V orthonormal (QR of Gaussians) and sigma
+    log-spaced from 1 down to 1/kappa; mu = mu_frac ||F^T g||_inf (mu_frac in
+    {0.01, 0.1, 1}; at 1 the minimiser is 0); x planted with frac_nz N(0,1)
+    nonzeros, g = F x + noise N(0,1)."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n / 5))
+    U, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    sig = kappa ** (-np.arange(m) / max(m - 1, 1))
+    F = (U * sig) @ V.T
+    xt = np.zeros(n)
+    idx = rng.choice(n, size=max(1, int(round(frac_nz * n))), replace=False)
+    xt[idx] = rng.standard_normal(idx.size)
+    g = F @ xt + noise * rng.standard_normal(m)
+    P = lasso(F=sp.csr_matrix(F), g=g, mu_frac=mu_frac)
+    P["meta"].update(kappa=kappa, sigma=sig, xplant=xt)
+    return P
+
+
+def pca_sdp(seed=0, d=50, lam=2.0, k_nz=None, spike=5.0):
+    """The sparse PCA SDP of Sec. 5.2, maximise trace(S Z) - lam ||Z||_1 subject
+    to trace(Z) = 1, Z PSD, as a cone program in z = svec(Z) and t >= |z|:
+        minimise -<svec(S), z> + lam (sum_diag t + sqrt2 sum_offdiag t)
+    (svec scales off-diagonal entries by sqrt2, so sum_{i != j} |Z_ij| is
+    sqrt2 times the off-diagonal |z|).  Rows: one zero-cone row trace(Z) = 1,
+    orthant rows t - z >= 0 and t + z >= 0, one PSD block s = z of order d.
+    S (a reading; the paper gives no recipe): a sample covariance B B^T / (2d)
+    of a d x 2d Gaussian B plus spike * v v^T with v a unit vector of k_nz
+    (default d/10) nonzeros."""
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((d, 2 * d))
+    k_nz = max(1, d // 10) if k_nz is None else k_nz
+    v = np.zeros(d)
+    idx = rng.choice(d, size=k_nz, replace=False)
+    v[idx] = rng.standard_normal(k_nz)
+    v /= np.linalg.norm(v)
+    S = B @ B.T / (2 * d) + spike * np.outer(v, v)
+    k = d * (d + 1) // 2
+    sv = _svec(S)
+    diag = np.zeros(k, bool)
+    o = 0
+    for j in range(d):
+        diag[o] = True
+        o += d - j
+    n = 2 * k
+    rows, cols, vals = [], [], []
+    dz = np.nonzero(diag)[0]
+    rows += [0] * len(dz); cols += list(dz); vals += [1.0] * len(dz)
+    e = np.arange(k)
+    rows += list(1 + e); cols += list(e); vals += [1.0] * k              # t - z >= 0
+    rows += list(1 + e); cols += list(k + e); vals += [-1.0] * k
+    rows += list(1 + k + e); cols += list(e); vals += [-1.0] * k         # t + z >= 0
+    rows += list(1 + k + e); cols += list(k + e); vals += [-1.0] * k
+    rows += list(1 + 2 * k + e); cols += list(e); vals += [-1.0] * k     # s = z in the PSD cone
+    m = 1 + 3 * k
+    A = _csr(np.array(rows), np.array(cols), np.array(vals), m, n)
+    b = np.zeros(m)
+    b[0] = 1.0
+    c = np.concatenate([-sv, lam * np.where(diag, 1.0, math.sqrt(2.0))])
+    return dict(A=A, b=b, c=c, f=1, l=2 * k, q=[], s=[d], meta=dict(S=S, lam=lam, d=d, v=v))
+
+
+def sgm(times, sigma=10.0):
+    """Shifted geometric mean of Sec. 5.1 with shift sigma (seconds): failed
+    problems (inf or nan) count as 100 times the largest finite time; the
+    printed formula lacks the 1/|P| of a mean, read here as
+    exp(mean(ln(max(1, sigma + t)))) - sigma."""
+    t = np.asarray(times, float)
+    ok = np.isfinite(t)
+    if not ok.any():
+        return float("inf")
+    t = np.where(ok, t, 100.0 * t[ok].max())
+    return float(np.exp(np.mean(np.log(np.maximum(1.0, sigma + t)))) - sigma)
