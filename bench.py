@@ -599,6 +599,84 @@ def run_c5(args):
     return 0
 
 
+def sweep_family(name, seeds):
+    """The paper's synthetic families (Sec. 5.2-5.4) as (label, problem) pairs:
+    LASSO n in {631,1000,1585,2512}, kappa in {10,215,4600,1e5}, mu in
+    {0.01,0.1,1}; l1-logistic p in {80,100}, q in {50,100,120}, lambda in
+    {10,20,50}; sparse-PCA SDP d = 50 (orders above 64 exceed the PSD kernel),
+    lambda in {0.1,2,5}; `seeds` instances of every grid point."""
+    from paper_1903_06477_gb300 import workloads as W
+    out = []
+    if name == "lasso":
+        for n in (631, 1000, 1585, 2512):
+            for kappa in (10.0, 215.0, 4600.0, 1e5):
+                for mu in (0.01, 0.1, 1.0):
+                    for sd in range(seeds):
+                        out.append((f"n{n}_k{kappa:g}_mu{mu:g}_{sd}",
+                                    lambda n=n, kappa=kappa, mu=mu, sd=sd: W.lasso_paper(sd, n, kappa, mu)))
+    elif name == "logreg":
+        for p in (80, 100):
+            for q in (50, 100, 120):
+                for lam in (10.0, 20.0, 50.0):
+                    for sd in range(seeds):
+                        out.append((f"p{p}_q{q}_l{lam:g}_{sd}",
+                                    lambda p=p, q=q, lam=lam, sd=sd: W.logreg(sd, p, q, lam)))
+    elif name == "pca":
+        for lam in (0.1, 2.0, 5.0):
+            for sd in range(seeds):
+                out.append((f"d50_l{lam:g}_{sd}", lambda lam=lam, sd=sd: W.pca_sdp(sd, 50, lam)))
+    else:
+        raise SystemExit(f"unknown family {name}")
+    return out
+
+
+def run_sweep(args):
+    """sgm10 (Sec. 5.1) of the time to eps = 1e-4 over one of the paper's
+    families: every instance solved on its own through scs_setup / scs_solve
+    (time = scs_solve to status, setup excluded; AA mem 10, FP64), and, with
+    --sweep-oracle, by the FP64 oracle on one host thread."""
+    import torch
+    from paper_1903_06477_gb300 import binding as B
+    from paper_1903_06477_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fam = sweep_family(args.sweep, args.sweep_seeds)
+    kw = dict(direction=0, mem=10, eps=1e-4, max_iters=100000, cg_rtol=1e-10, cg_adapt=1e-2)
+    gpu_t, cpu_t, solved, solved_cpu, iters = [], [], 0, 0, []
+    st = torch.cuda.current_stream()
+    for label, make in fam:
+        prob = make()
+        w = B.Work(prob, stream=st, **kw)
+        w.solve()  # warm-up of this instance's first solve
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _, _, _, info = w.solve()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ok = info["status"] in (B.SOLVED, B.INFEASIBLE, B.UNBOUNDED)
+        gpu_t.append(e0.elapsed_time(e1) / 1e3 if ok else float("inf"))
+        solved += ok
+        iters.append(info["iters"])
+        w.close()
+        if args.sweep_oracle:
+            from oracle import oracle as O
+            t0 = time.perf_counter()
+            out = O.Oracle(prob, **kw).solve()
+            okc = out["info"].status in (O.SOLVED, O.INFEASIBLE, O.UNBOUNDED)
+            cpu_t.append(time.perf_counter() - t0 if okc else float("inf"))
+            solved_cpu += okc
+    line = {"metric": f"sgm10 of time-to-1e-4 over the Sec. 5 {args.sweep} family (shifted geometric mean, "
+                      f"sigma = 10 s)", "value": W.sgm(gpu_t), "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "instances": len(fam), "success": solved / len(fam), "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.sweep} family of the paper, {args.sweep_seeds} seed(s) per grid point",
+                       "eps": 1e-4, "direction": "AA mem 10"},
+            "mean_s": float(np.mean([t for t in gpu_t if np.isfinite(t)])), "median_iters": float(np.median(iters)),
+            "cpu_baseline": None if not cpu_t else {"value": W.sgm(cpu_t), "unit": "s", "cores": 1, "kind": "oracle",
+                                                    "sample": "the same instances, FP64 oracle, one thread",
+                                                    "success": solved_cpu / len(fam), **host_info()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gemm(args):
     """Profiling aid for the warm-start network's GEMMs: both kernels
     (m16n8k16 and tcgen05) on the products of the 2000-1024-1024-22004
@@ -691,6 +769,10 @@ def main():
     ap.add_argument("--products", type=int, default=0,
                     help="profiling aid: set up the workload, run this many sparse products (see --op) and exit")
     ap.add_argument("--op", default="a", choices=["a", "at"], help="product for --products: A x or A^T y")
+    ap.add_argument("--sweep", default="lasso", choices=["lasso", "logreg", "pca"],
+                    help="family of --workload sweep")
+    ap.add_argument("--sweep-seeds", type=int, default=1)
+    ap.add_argument("--sweep-oracle", action="store_true", help="also time the FP64 oracle on every instance")
     ap.add_argument("--gemm", action="store_true",
                     help="profiling aid: time the warm-start network's GEMM kernels (both) and exit")
     args = ap.parse_args()
@@ -704,6 +786,8 @@ def main():
         return run_batch(args)
     if args.workload == "c5":
         return run_c5(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
 
     import torch
     from paper_1903_06477_gb300 import binding as B
