@@ -375,7 +375,7 @@ def run_batch(args):
     kw = dict(direction=0, mem=10, eps=1e-5, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5)
     if args.threads > 0:
         kw["threads"] = args.threads
-    for key in ("mixed_switch", "mixed_resume", "mixed_refine", "mixed_stall"):
+    for key in ("mixed_switch", "mixed_resume", "mixed_refine", "mixed_stall", "linsys_direct"):
         if getattr(args, key) is not None:
             kw[key] = getattr(args, key)
     prec = B.MIXED if args.precision == "mixed" else B.FP64
@@ -758,6 +758,8 @@ def main():
     ap.add_argument("--mixed-switch", type=float, default=None)
     ap.add_argument("--mixed-stall", type=int, default=None)
     ap.add_argument("--mixed-resume", type=int, default=None, help="1: the FP64 phase continues the FP32 loop state")
+    ap.add_argument("--linsys-direct", type=int, default=None,
+                    help="1: block-team instances solve their linear systems by a dense Cholesky factor")
     ap.add_argument("--mixed-refine", type=int, default=None,
                     help="1: the FP64 phase solves by iterative refinement with FP32 corrections")
     ap.add_argument("--instances", type=int, default=4096, help="batch size of the c4 workload")
@@ -958,6 +960,9 @@ def main():
             "cg_iters_fp32": last["cg_iters_fp32"], "mat_passes": list(last["mat_passes"]),
             "cg_iters_ir": last["cg_iters_ir"], "mat_passes_ir": last["mat_passes_ir"], "ir_sweeps": last["ir_sweeps"],
             "kkt_fp32": last["kkt_fp32"], "steps_k0_k1_k2_bt": [last["k0"], last["k1"], last["k2"], last["backtracks"]],
+            "part_ms": {"fp64": [round(1e3 * v, 3) for v in last["part_s"][0]],
+                        "fp32": [round(1e3 * v, 3) for v in last["part_s"][1]],
+                        "order": "termination, direction, linear solves, CG loops inside them, rest"},
             "kernel_ms": [1e3 * last["kernel_s"][0], 1e3 * last["kernel_s"][1]],
             "pobj": last["pobj"], "err_vs_fp64": last.get("err_vs_fp64"),
             "fp64_time_to_eps_s": None if fp64_ms is None else fp64_ms / 1e3,

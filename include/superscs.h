@@ -134,6 +134,12 @@ typedef struct {
                                Sec. 4.1 by iterative refinement -- residuals with the FP64 matrix,
                                corrections by CG with the FP32 copy -- so its FP64 work is a few
                                sparse products per solve; 0: plain FP64 CG */
+    int32_t linsys_direct;  /* 1: instances run by one thread block (the block team, every batch
+                               instance) with n <= 4096 form I + A^T A densely at setup, factor it
+                               L L^T in each precision (the "direct" solve Sec. 4.1 names beside CG)
+                               and solve each linear system by two blocked triangular solves; the
+                               factor takes n^2 words per precision.  0 (default): CG.  Ignored by
+                               the grid team.  A non-positive pivot makes setup fail with SCS_EINVAL */
 } scs_settings;
 
 typedef struct {
@@ -164,6 +170,9 @@ typedef struct {
                                hand-over, packing, copies to the host staging), CUDA events on the
                                stream it runs on; the same in every instance's info */
     int32_t team;           /* execution team that ran: SCS_TEAM_BLOCK (k_block) or SCS_TEAM_GRID (k_grid) */
+    double part_s[2][5];    /* device time of the parts of Algorithm 1 in the FP64 [0] and FP32 [1]
+                               phase: termination tests, directions, linear solves (all), the CG
+                               loops inside them, the rest (steps, line searches, projections) */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */

@@ -44,6 +44,7 @@ class Settings(C.Structure):
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
         ("warm_fallback", C.c_int32), ("mixed_resume", C.c_int32), ("mixed_refine", C.c_int32),
+        ("linsys_direct", C.c_int32),
     ]
 
 
@@ -58,12 +59,14 @@ class Info(C.Structure):
         ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32), ("warm_fallback_taken", C.c_int32),
         ("kkt_fp32", C.c_double), ("mat_passes_ir", C.c_int64), ("cg_iters_ir", C.c_int64),
         ("ir_sweeps", C.c_int64), ("batch_device_s", C.c_double), ("team", C.c_int32),
+        ("part_s", (C.c_double * 5) * 2),
     ]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         for k in ("kernel_s", "mat_passes"):
             d[k] = list(d[k])
+        d["part_s"] = [list(r) for r in d["part_s"]]
         return d
 
 

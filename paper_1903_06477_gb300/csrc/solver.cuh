@@ -21,7 +21,7 @@ constexpr int PSD_MAX = 64;  // largest PSD order
 constexpr int PSD_LD = PSD_MAX + 1;  // row stride bound of a block's matrices in shared memory
 
 enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5,
-            MODE_RESID = 6, MODE_SPMV = 7 };
+            MODE_RESID = 6, MODE_SPMV = 7, MODE_FACTOR = 8 };
 enum { ST_SOLVED = 1, ST_INFEASIBLE = -1, ST_UNBOUNDED = -2, ST_MAX_ITERS = -3, ST_TIME_LIMIT = -4,
        ST_NUMERICAL = -5, ST_STALLED = -6 };
 
@@ -72,6 +72,11 @@ struct DevState {
     long long mat_passes_ir;  // FP32 passes of the refinement corrections (FP64 phase)
     long long cg_iters_ir;    // FP32 CG iterations of the refinement corrections (FP64 phase)
     long long ir_sweeps;      // refinement sweeps (FP32 correction solves)
+    // device time (globaltimer, read by the leader thread between team barriers) of the parts of
+    // Algorithm 1: [0] termination tests, [1] directions, [2] linear solves (all of minv / its
+    // refinement variant), [3] the CG loops inside them, [4] everything else (K0 steps, line
+    // searches, projections, updates)
+    double part_ns[5];
 };
 
 // Column-blocked sliced ELL, the grid team's layout for large matrices.  CTA b
@@ -175,6 +180,8 @@ template <typename T>
 struct DevWork {
     IrBufs ir;
     Resume* res;  // loop state handed from the FP32 to the FP64 phase (SCS_MIXED)
+    T* chol;      // direct solves: n x n row-major, lower triangle = Cholesky factor of I + A^T A (else null)
+    int* chol_fail;  // set by MODE_FACTOR if a pivot was not positive (the factor is then not used)
     HV<T> u, ut, ub, Ru, d, dt, wb, Rw, zp, xip, zt;
     T* g;       // n+m: g = M^{-1}(c, b)
     T* ws[2];   // CG warm starts (n) for the u~ and d~ systems
@@ -729,6 +736,112 @@ __device__ int cg_loop(Team& tm, const Sell<T>& A, const Sell<T>& AT, int n, CgB
 }
 
 // ---------------------------------------------------------------------------
+// Direct solves of (I + A^T A) x = b (the "direct" alternative Sec. 4.1 names
+// beside CG), for one CTA per instance: the matrix is formed column by column
+// as e_j + A^T (A e_j) with the solver's own sparse products, factored
+// L L^T in place (right-looking, one column per step), and each solve is a
+// forward and a backward substitution in blocks of 32: warp 0 solves the
+// 32 x 32 diagonal block with shuffles, then the whole CTA updates the rows
+// outside it (two CTA barriers per block).
+// ---------------------------------------------------------------------------
+constexpr int CHOL_B = 32;
+
+template <typename T, class Team>
+__device__ void chol_factor(Team& tm, const DevProb<T>& P, const DevWork<T>& W)
+{
+    const int n = P.n;
+    T* L = W.chol;
+    T* ej = W.cp;
+    T* y = W.tm;
+    for (int j = 0; j < n; ++j) {
+        for (int i = tm.rank(); i < n; i += tm.size()) ej[i] = i == j ? T(1) : T(0);
+        tm.sync();
+        spmv(tm, P.A, ej, [&](int i, T v) { y[i] = v; });
+        tm.sync();
+        spmv(tm, P.AT, y, [&](int i, T v) {
+            if (i >= j) L[(size_t)i * n + j] = v + (i == j ? T(1) : T(0));
+        });
+        tm.sync();
+    }
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            const T djj = L[(size_t)j * n + j];
+            if (!(djj > T(0))) bad = 1;
+            L[(size_t)j * n + j] = djj > T(0) ? sqrt(djj) : T(1);
+        }
+        __syncthreads();
+        const T d = L[(size_t)j * n + j];
+        for (int i = j + 1 + tm.rank(); i < n; i += tm.size()) L[(size_t)i * n + j] /= d;
+        __syncthreads();
+        const int r = n - j - 1;
+        for (long long idx = tm.rank(); idx < (long long)r * r; idx += tm.size()) {
+            const int ii = j + 1 + (int)(idx / r), kk = j + 1 + (int)(idx % r);
+            if (kk <= ii) L[(size_t)ii * n + kk] -= L[(size_t)ii * n + j] * L[(size_t)kk * n + j];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(W.chol_fail, 1);
+    __syncthreads();
+}
+
+// b (n, in place) <- (L L^T)^{-1} b; zb: CHOL_B values of shared memory
+template <typename T, class Team>
+__device__ void chol_solve(Team& tm, const T* L, int n, T* b, T* zb)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // forward: L z = b
+    for (int jb = 0; jb < n; jb += CHOL_B) {
+        const int w = min(CHOL_B, n - jb);
+        if (warp == 0) {
+            T v = lane < w ? b[jb + lane] : T(0);
+            for (int c = 0; c < w; ++c) {
+                const T zc = __shfl_sync(FULL_MASK, v, c) / L[(size_t)(jb + c) * n + jb + c];
+                if (lane == c) v = zc;
+                if (lane > c && lane < w) v -= L[(size_t)(jb + lane) * n + jb + c] * zc;
+            }
+            if (lane < w) {
+                b[jb + lane] = v;
+                zb[lane] = v;
+            }
+        }
+        __syncthreads();
+        for (int i = jb + w + tm.rank(); i < n; i += tm.size()) {
+            T acc = b[i];
+            const T* row = L + (size_t)i * n + jb;
+            for (int c = 0; c < w; ++c) acc -= row[c] * zb[c];
+            b[i] = acc;
+        }
+        __syncthreads();
+    }
+    // backward: L^T x = z
+    for (int jb = ((n - 1) / CHOL_B) * CHOL_B; jb >= 0; jb -= CHOL_B) {
+        const int w = min(CHOL_B, n - jb);
+        if (warp == 0) {
+            T v = lane < w ? b[jb + lane] : T(0);
+            for (int c = w - 1; c >= 0; --c) {
+                const T xc = __shfl_sync(FULL_MASK, v, c) / L[(size_t)(jb + c) * n + jb + c];
+                if (lane == c) v = xc;
+                if (lane < c) v -= L[(size_t)(jb + c) * n + jb + lane] * xc;
+            }
+            if (lane < w) {
+                b[jb + lane] = v;
+                zb[lane] = v;
+            }
+        }
+        __syncthreads();
+        for (int k = tm.rank(); k < jb; k += tm.size()) {
+            T acc = b[k];
+            for (int c = 0; c < w; ++c) acc -= L[(size_t)(jb + c) * n + k] * zb[c];
+            b[k] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // M^{-1}(a, e) for M = [I A^T; -A I]: x = (I + A^T A)^{-1}(a - A^T e) by CG
 // warm-started from x (in place), y = e + A x written to W.py.  Returns the CG
 // iterations; htp = <c, x> + <b, y>.  CG stops when ||res|| <= rtol ||rhs||.
@@ -760,8 +873,16 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     if (rhs2 == 0.0) {
         for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
         tm.sync();
+    } else if (W.chol != nullptr && !Team::kGrid) {
+        // direct: x <- x + (L L^T)^{-1} r, the residual of the warm start solved exactly
+        __shared__ T zb[CHOL_B];
+        chol_solve<T>(tm, W.chol, n, r, zb);
+        for (int j = tm.rank(); j < n; j += tm.size()) x[j] += r[j];
+        tm.sync();
     } else if (sqrt(rr) > tol) {
+        const unsigned long long tc0 = tm.leader() ? gtimer() : 0ull;
         it = cg_loop<T>(tm, P.A, P.AT, n, CgBufs<T>{r, W.cp, W.cq, tmv}, x, rr, tol, cg_max);
+        if (tm.leader()) W.st->part_ns[3] += (double)(gtimer() - tc0);
     }
     T hb = 0, hc = 0;
     T* py = W.py;
@@ -838,8 +959,10 @@ __device__ int minv_ir(Team& tm, const DevProb<double>& P, const DevWork<double>
             }
             double red3[1] = {(double)acc32};
             tm.reduce(red3);
+            const unsigned long long tc0 = tm.leader() ? gtimer() : 0ull;
             const int k = cg_loop<float>(tm, ir.A, ir.AT, n, CgBufs<float>{ir.r, ir.p, ir.q, ir.tm}, ir.x, red3[0],
                                          fmax(want, IR_FLOOR) * sqrt(red3[0]), cg_max - it);
+            if (tm.leader()) W.st->part_ns[3] += (double)(gtimer() - tc0);
             it += k;
             passes32 += 2 * k;
             ++sweeps;
@@ -896,6 +1019,7 @@ __device__ int linsys(Team& tm, const DevProb<T>& P, const DevWork<T>& W, HV<T> 
     T* x = W.ws[slot];
     double htp;
     int it;
+    const unsigned long long tl0 = tm.leader() ? gtimer() : 0ull;
     if constexpr (sizeof(T) == sizeof(double)) {
         it = refine ? minv_ir(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol)
                     : minv(tm, P, W, r.v, r.v + n, x, rtol, cg_max, htp, atol);
@@ -908,6 +1032,7 @@ __device__ int linsys(Team& tm, const DevProb<T>& P, const DevWork<T>& W, HV<T> 
     for (int i = tm.rank(); i < m; i += tm.size()) out.v[n + i] = W.py[i] - tt * W.g[n + i];
     if (tm.leader()) *out.t = tau;
     tm.sync();
+    if (tm.leader()) W.st->part_ns[2] += (double)(gtimer() - tl0);
     return it;
 }
 
@@ -2055,6 +2180,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         W.st->mat_passes_ir = 0;
         W.st->cg_iters_ir = 0;
         W.st->ir_sweeps = 0;
+        for (int k = 0; k < 5; ++k) W.st->part_ns[k] = 0.0;
         W.st->psd_resid = 0.0;
         W.st->fallback = 0;
     }
@@ -2133,8 +2259,17 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             status = ST_NUMERICAL;
             break;
         }
+        unsigned long long tp = tm.leader() ? gtimer() : 0ull;  // start of this part
+        auto part_end = [&](int k) {
+            if (tm.leader()) {
+                const unsigned long long t = gtimer();
+                W.st->part_ns[k] += (double)(t - tp);
+                tp = t;
+            }
+        };
         if (nu % check_every == 0) {
             const int st = termination(tm, P, W, S.eps, deadline, to);
+            part_end(0);
             if (st != 0) {
                 status = st;
                 need_final_check = false;
@@ -2164,6 +2299,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             }
         }
         // direction d (Sec. 4.4)
+        part_end(4);
         if (S.direction == 0)
             aa_direction(tm, P, W, S, have_pair, nz2, ds, G, sm_rhs, sm_L, sm_t);
         else if (S.direction == 3)
@@ -2175,8 +2311,14 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             if (tm.leader()) *W.d.t = 0.0;
             tm.sync();
         }
+        part_end(1);
         const double atol = S.cg_adapt > 0.0 ? S.cg_adapt * nRu : 0.0;
         cg_total += linsys(tm, P, W, W.d, W.dt, 1, S.cg_rtol, S.cg_max, hg, atol, S.refine != 0);
+        double lin0 = 0.0;  // linear-solve time so far (a K2 step adds its own below)
+        if (tm.leader()) {
+            tp = gtimer();  // the linear solve timed itself
+            lin0 = W.st->part_ns[2];
+        }
         if (nRu <= S.c0 * eta) {
             // K0
             eta = nRu;
@@ -2264,6 +2406,11 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             }
         }
         have_pair = true;
+        // the rest of the step (K0, line search, projections; K2's linear solve timed itself)
+        if (tm.leader()) {
+            const unsigned long long t = gtimer();
+            W.st->part_ns[4] += (double)(t - tp) - (W.st->part_ns[2] - lin0);
+        }
     }
     if (need_final_check && !tm.aborted()) {
         const int st = termination(tm, P, W, S.eps, 0.0, to);
@@ -2323,6 +2470,12 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
                          double* G, double* sm_rhs, double* sm_L, double* sm_t, unsigned char* psd)
 {
     const int n = P.n, m = P.m, nm = n + m;
+    if (mode == MODE_FACTOR) {
+        if constexpr (!Team::kGrid) {
+            if (W.chol) chol_factor(tm, P, W);
+        }
+        return;
+    }
     if (mode == MODE_SETUP) {
         // g = M^{-1}(c, b) from a zero start; ws[0] is zero on entry and left zero
         T* x = W.ws[0];

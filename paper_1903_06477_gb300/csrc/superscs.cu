@@ -379,6 +379,8 @@ static void finish_layouts(HostProb& H, bool sell_A, bool sell_T)
     std::vector<double>().swap(H.Tx);
 }
 
+constexpr int DIRECT_MAX_N = 4096;  // largest n factored densely by the direct linear solves
+
 static int check_settings(const scs_settings* S, char* err)
 {
     if (!S) { set_err(err, "settings must not be NULL"); return SCS_EINVAL; }
@@ -411,7 +413,8 @@ struct Arena {
 
 // layout of one instance's data and work in precision T; base == nullptr only measures
 template <typename T>
-static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, int max_blocks, DevProb<T>& P, DevWork<T>& W,
+static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, bool direct, int max_blocks, DevProb<T>& P,
+                    DevWork<T>& W,
                     const int* shared_idx /* index arrays shared with another precision or null */,
                     DevState* st_ext = nullptr)
 {
@@ -508,6 +511,8 @@ static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, int max_block
     W.st = st_ext ? st_ext : A.take<DevState>(1);
     W.res = A.take<Resume>(1);
     W.ir = IrBufs{};
+    W.chol = direct ? A.take<T>((size_t)n * n) : nullptr;
+    W.chol_fail = A.take<int>(4);
 }
 
 // The FP64 phase of SCS_MIXED reads the FP32 phase's loop state (one shared
@@ -740,6 +745,7 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->warm_fallback = 0;
     o->mixed_resume = 1;
     o->mixed_refine = 1;
+    o->linsys_direct = 0;
     return SCS_OK;
 }
 
@@ -869,17 +875,19 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     DevWork<float> W32{};
     const int mem = std::max(settings->mem, 1);
     const bool qr = settings->direction == SCS_DIR_AA_QR;
-    lay_out<double>(A, H, mem, qr, w->D.grid, P64, W64, nullptr);
-    if (w->has32) lay_out<float>(A, H, mem, qr, w->D.grid, P32, W32, (const int*)1);
+    // direct solves: one CTA per instance only (the factor is formed and used by one CTA)
+    const bool direct = settings->linsys_direct && team == SCS_TEAM_BLOCK && H.n <= DIRECT_MAX_N;
+    lay_out<double>(A, H, mem, qr, direct, w->D.grid, P64, W64, nullptr);
+    if (w->has32) lay_out<float>(A, H, mem, qr, direct, w->D.grid, P32, W32, (const int*)1);
     size_t bytes = A.off + sizeof(Args<double>) + sizeof(Args<float>) + 1024;
     ce = cudaMalloc((void**)&w->arena, bytes);
     if (ce != cudaSuccess) { set_err(w->err, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(ce)); memcpy(g_err, w->err, 512); delete w; return SCS_ENOMEM; }
     w->arena_bytes = bytes;
     A.off = 0;
     A.base = w->arena;
-    lay_out<double>(A, H, mem, qr, w->D.grid, w->P64, w->W64, nullptr);
+    lay_out<double>(A, H, mem, qr, direct, w->D.grid, w->P64, w->W64, nullptr);
     if (w->has32) {
-        lay_out<float>(A, H, mem, qr, w->D.grid, w->P32, w->W32, (const int*)1);
+        lay_out<float>(A, H, mem, qr, direct, w->D.grid, w->P32, w->W32, (const int*)1);
         w->P32.A.ptr = w->P64.A.ptr;
         w->P32.A.col = w->P64.A.col;
         w->P32.A.perm = w->P64.A.perm;
@@ -901,6 +909,16 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     if (cudaMemsetAsync(w->arena, 0, bytes, w->stream) != cudaSuccess) { set_err(w->err, "memset failed"); return fail(SCS_ECUDA); }
     if ((rc = upload<double>(H, w->P64, true, w->stream, w->err))) return fail(rc);
     if (w->has32 && (rc = upload<float>(H, w->P32, false, w->stream, w->err))) return fail(rc);
+    if (direct) {
+        // factor I + A^T A in each precision before g is solved with it
+        DevSettings SF = dev_settings(settings);
+        if ((rc = launch<double>(w->D, w->D.dyn64, make_args(w->P64, w->W64, SF, MODE_FACTOR), w->dargs64, w->queue,
+                                 w->stream, w->err)))
+            return fail(rc);
+        if (w->has32 && (rc = launch<float>(w->D, w->D.dyn32, make_args(w->P32, w->W32, SF, MODE_FACTOR), w->dargs32,
+                                            w->queue, w->stream, w->err)))
+            return fail(rc);
+    }
     if ((rc = run_setup_g<double>(w, w->P64, w->W64, w->dargs64, w->D.dyn64))) return fail(rc);
     if (w->has32 && (rc = run_setup_g<float>(w, w->P32, w->W32, w->dargs32, w->D.dyn32))) return fail(rc);
     if (cudaStreamSynchronize(w->stream) != cudaSuccess) {
@@ -910,6 +928,12 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     int abort_flag = 0;
     cudaMemcpy(&abort_flag, w->W64.abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
     if (abort_flag) { set_err(w->err, "device barrier timed out in setup"); return fail(SCS_ETIMEOUT); }
+    if (direct) {
+        int f64 = 0, f32 = 0;
+        cudaMemcpy(&f64, w->W64.chol_fail, sizeof(int), cudaMemcpyDeviceToHost);
+        if (w->has32) cudaMemcpy(&f32, w->W32.chol_fail, sizeof(int), cudaMemcpyDeviceToHost);
+        if (f64 || f32) { set_err(w->err, "Cholesky factorisation of I + A^T A met a non-positive pivot"); return fail(SCS_EINVAL); }
+    }
     for (auto& e : w->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { set_err(w->err, "cudaEventCreate failed"); return fail(SCS_ECUDA); }
     w->setup_s = now_s() - t0;
@@ -948,6 +972,7 @@ static void fill_info(scs_info* info, const DevState& s)
     info->mat_passes_ir = s.mat_passes_ir;
     info->cg_iters_ir = s.cg_iters_ir;
     info->ir_sweeps = s.ir_sweeps;
+    for (int k = 0; k < 5; ++k) info->part_s[0][k] = s.part_ns[k] * 1e-9;
 }
 
 extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info* info)
@@ -1034,6 +1059,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
             info->mat_passes[1] = st32.mat_passes;
             info->cg_iters_fp32 = st32.cg_iters;
             info->psd_resid_fp32 = st32.psd_resid;
+            for (int k = 0; k < 5; ++k) info->part_s[1][k] = st32.part_ns[k] * 1e-9;
         }
     }
     if (abort_flag || abort32) { set_err(w->err, "device barrier timed out"); return SCS_ETIMEOUT; }
@@ -1363,6 +1389,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     const int mem = std::max(settings->mem, 1);
     const bool qr = settings->direction == SCS_DIR_AA_QR;
+    const bool direct = settings->linsys_direct != 0;
     b->hoff.resize(B + 1, 0);
     for (int qi = 0; qi < B; ++qi) {
         const HostProb& h = b->H[b->order[qi]];
@@ -1377,7 +1404,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
         DevState* st32 = A.take<DevState>(B);
         for (int qi = 0; qi < B; ++qi) {
             const HostProb& h = b->H[b->order[qi]];
-            lay_out<double>(A, h, mem, qr, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
+            lay_out<double>(A, h, mem, qr, direct && h.n <= DIRECT_MAX_N, 1, b->a64[qi].P, b->a64[qi].W, nullptr, real ? st64 + qi : nullptr);
             b->a64[qi].slot = 0;
             if (real && b->shared && qi > 0) {
                 b->a64[qi].P.A = b->a64[0].P.A;
@@ -1387,7 +1414,7 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
                 b->a64[qi].P.s_off = b->a64[0].P.s_off;
             }
             if (b->has32) {
-                lay_out<float>(A, h, mem, qr, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
+                lay_out<float>(A, h, mem, qr, direct && h.n <= DIRECT_MAX_N, 1, b->a32[qi].P, b->a32[qi].W, (const int*)1, real ? st32 + qi : nullptr);
                 b->a32[qi].slot = 0;
                 if (real) {
                     DevProb<float>& p = b->a32[qi].P;
@@ -1465,6 +1492,16 @@ static int batch_finish_setup(scs_batch* b, const scs_settings* settings, scs_ba
     // setup (g = M^{-1}(c, b)) with a provisional shape
     b->threads = settings->threads ? settings->threads : 256;
     b->grid = occupancy_grid(kblock_ptr<double>(), b->threads, b->dyn64, b->sms, B);
+    if (direct) {
+        // factor I + A^T A of every instance (n <= DIRECT_MAX_N) in each precision before g is solved with it
+        CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+        CU(launch_block<double>(b->grid, b->threads, b->dyn64, b->stream, b->d64, B, b->queue, S64, MODE_FACTOR), b->err);
+        if (b->has32) {
+            const int g32 = occupancy_grid(kblock_ptr<float>(), b->threads, b->dyn32, b->sms, B);
+            CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
+            CU(launch_block<float>(g32, b->threads, b->dyn32, b->stream, b->d32, B, b->queue, S32, MODE_FACTOR), b->err);
+        }
+    }
     CU(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream), b->err);
     CU(launch_block<double>(b->grid, b->threads, b->dyn64, b->stream, b->d64, B, b->queue, S64, MODE_SETUP), b->err);
     if (b->has32) {

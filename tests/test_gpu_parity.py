@@ -182,6 +182,30 @@ def test_refined_linsys_matches_oracle(name, team):
         np.testing.assert_allclose(out, ref, rtol=0, atol=1e-9 * (1 + np.abs(ref).max()))
 
 
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+@pytest.mark.parametrize("name", list(PROBS))
+def test_direct_linsys_matches_oracle(name, precision):
+    """(I+Q)^{-1} with I + A^T A factored L L^T at setup (one CTA per instance)
+    against the oracle's CG to 1e-14; then whole solves with direct linear
+    systems (both phases factored in their own precision) reach eps."""
+    prob = PROBS[name]
+    work = B.Work(prob, team=B.TEAM_BLOCK, linsys_direct=1, precision=precision, cg_rtol=1e-14, cg_max=5000)
+    orc = O.Oracle(prob, cg_rtol=1e-14, cg_max=5000)
+    rng = np.random.default_rng(12)
+    for slot in (0, 1, 0):
+        r = rng.standard_normal(work.N) * 3
+        out = work.linsys(r, slot=slot)
+        ref = orc.linsys(r, slot=slot)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-9 * (1 + np.abs(ref).max()))
+    eps = 1e-6
+    w2 = B.Work(prob, team=B.TEAM_BLOCK, linsys_direct=1, precision=precision, eps=eps, max_iters=20000)
+    x, y, s, info = w2.solve()
+    ref = O.Oracle(prob, eps=eps, max_iters=20000).solve()
+    assert info["status"] == B.SOLVED == ref["info"].status, info
+    assert max(_kkt(prob, x, y, s)) <= 1.01 * eps
+    assert abs(info["pobj"] - ref["info"].pobj) <= 10 * eps * (1 + abs(ref["info"].pobj))
+
+
 @pytest.mark.parametrize("team", TEAMS)
 @pytest.mark.parametrize("resume,refine", [(1, 1), (0, 0), (1, 0), (0, 1)])
 def test_mixed_handover_modes(team, resume, refine):
@@ -279,11 +303,12 @@ def test_invalid_inputs_rejected():
         B.Work(prob, mem=99)
 
 
+@pytest.mark.parametrize("direct", [0, 1])
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
-def test_batch_parity(precision):
+def test_batch_parity(precision, direct):
     probs = [W.portfolio(seed=100 + i, k=int(k)) for i, k in enumerate(np.linspace(20, 140, 24))]
     eps = 1e-6
-    batch = B.Batch(probs, precision=precision, eps=eps, max_iters=20000, cg_rtol=1e-12)
+    batch = B.Batch(probs, precision=precision, eps=eps, max_iters=20000, cg_rtol=1e-12, linsys_direct=direct)
     xs, ys, ss, infos = batch.solve()
     for p, x, y, s, info in zip(probs, xs, ys, ss, infos):
         assert info["status"] == B.SOLVED, info
