@@ -758,6 +758,8 @@ def main():
     ap.add_argument("--mixed-switch", type=float, default=None)
     ap.add_argument("--mixed-stall", type=int, default=None)
     ap.add_argument("--mixed-resume", type=int, default=None, help="1: the FP64 phase continues the FP32 loop state")
+    ap.add_argument("--stall-after-tau", type=int, default=None,
+                    help="1: the FP32 phase's stall count starts once tau_ > 0")
     ap.add_argument("--linsys-direct", type=int, default=None,
                     help="1: block-team instances solve their linear systems by a dense Cholesky factor")
     ap.add_argument("--mixed-refine", type=int, default=None,
@@ -822,6 +824,8 @@ def main():
         kw["mixed_stall"] = args.mixed_stall
     if args.mixed_resume is not None:
         kw["mixed_resume"] = args.mixed_resume
+    if args.stall_after_tau is not None:
+        kw["mixed_stall_after_tau"] = args.stall_after_tau
     if args.mixed_refine is not None:
         kw["mixed_refine"] = args.mixed_refine
     for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine"):

@@ -140,6 +140,10 @@ typedef struct {
                                and solve each linear system by two blocked triangular solves; the
                                factor takes n^2 words per precision.  0 (default): CG.  Ignored by
                                the grid team.  A non-positive pivot makes setup fail with SCS_EINVAL */
+    int32_t mixed_stall_after_tau; /* SCS_MIXED, 1 (default): while the FP32 phase's termination test
+                               sees tau_ = 0 its stall window is 5 mixed_stall iterations -- the
+                               residuals of Sec. 4.3 are undefined then and ||Ru|| may plateau while
+                               the iterate turns away from the tau axis; 0: mixed_stall throughout */
 } scs_settings;
 
 typedef struct {

@@ -44,7 +44,7 @@ class Settings(C.Structure):
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
         ("warm_fallback", C.c_int32), ("mixed_resume", C.c_int32), ("mixed_refine", C.c_int32),
-        ("linsys_direct", C.c_int32),
+        ("linsys_direct", C.c_int32), ("mixed_stall_after_tau", C.c_int32),
     ]
 
 

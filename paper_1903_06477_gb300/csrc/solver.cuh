@@ -46,6 +46,7 @@ struct DevSettings {
                            // start's ||Ru0|| after this many iterations
     int save_state;        // 1: write the loop state to W.res when the solve ends (FP32 phase of SCS_MIXED)
     int resume;            // 1: continue from the loop state in W.res instead of starting Algorithm 1 afresh
+    int stall_after_tau;   // 1: the stall count starts only once tau_ > 0 (FP32 phase of SCS_MIXED)
     int refine;            // 1 (FP64 data only): linear systems by iterative refinement, FP64 residuals
                            // and FP32 CG corrections on the FP32 copy of A (W.ir)
 };
@@ -2287,11 +2288,15 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             }
             if (S.stall_iters > 0) {
                 // FP32 phase of SCS_MIXED: stop once ||Ru|| has not dropped 10% below
-                // its best value for stall_iters iterations (the FP32 floor)
+                // its best value for stall_iters iterations (the FP32 floor).  While
+                // tau_ = 0 the residuals of Sec. 4.3 are undefined and the iterate is
+                // still turning away from the tau axis, where ||Ru|| can plateau
+                // without any floor being reached: the window is then five times longer.
+                const int window = (S.stall_after_tau && !isfinite(to.pr)) ? 5 * S.stall_iters : S.stall_iters;
                 if (nRu < 0.9 * best_kkt) {
                     best_kkt = nRu;
                     best_it = nu;
-                } else if (nu - best_it >= S.stall_iters) {
+                } else if (nu - best_it >= window) {
                     status = ST_STALLED;
                     need_final_check = false;
                     break;

@@ -629,6 +629,7 @@ static DevSettings dev_settings(const scs_settings* S)
     D.save_state = 0;
     D.resume = 0;
     D.refine = 0;
+    D.stall_after_tau = S->mixed_stall_after_tau;
     return D;
 }
 
@@ -746,6 +747,7 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->mixed_resume = 1;
     o->mixed_refine = 1;
     o->linsys_direct = 0;
+    o->mixed_stall_after_tau = 1;
     return SCS_OK;
 }
 
