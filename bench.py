@@ -826,9 +826,11 @@ def main():
         kw["mixed_resume"] = args.mixed_resume
     if args.stall_after_tau is not None:
         kw["mixed_stall_after_tau"] = args.stall_after_tau
+    if args.linsys_direct is not None:
+        kw["linsys_direct"] = args.linsys_direct
     if args.mixed_refine is not None:
         kw["mixed_refine"] = args.mixed_refine
-    for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine"):
+    for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine", "linsys_direct"):
         if key in kw:
             cfg[key] = kw[key]
     prec = B.MIXED if args.precision == "mixed" else B.FP64

@@ -341,7 +341,6 @@ __global__ void __launch_bounds__(TC_NTH, 1) gemm_nt_tc(const __grid_constant__ 
         if (ok && !failed) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int q = warp & 3;
-            const int m = m0 + q * 32 + lane;
 #pragma unroll 1
             for (int c0 = 0; c0 < TC_BN; c0 += 32) {
                 unsigned v[32];
@@ -361,19 +360,24 @@ __global__ void __launch_bounds__(TC_NTH, 1) gemm_nt_tc(const __grid_constant__ 
 #pragma unroll
                     for (int t = 0; t < 32; ++t) v[t] = 0u;
                 }
-                if (m < M) {
-                    if (ws) {
-                        // split-K partial tile (FP32, row stride N) of split blockIdx.z
-                        float* row = ws + ((size_t)blockIdx.z * M + m) * N;
+                // stage the warp's 32 x 32 chunk (lane = row) in shared memory -- the ring is idle
+                // once every MMA has completed -- then write it row by row, lane = column, so each
+                // store instruction covers 32 consecutive elements of one row
+                float* stg = reinterpret_cast<float*>(tc_dyn + (ring - sa(tc_dyn))) + (size_t)(warp - 2) * 32 * 33;
 #pragma unroll
-                        for (int t = 0; t < 32; ++t)
-                            if (n0 + c0 + t < N) row[n0 + c0 + t] = __uint_as_float(v[t]);
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < 32; ++t)
-                            if (n0 + c0 + t < N) epi_store(e, m, n0 + c0 + t, __uint_as_float(v[t]));
-                    }
+                for (int t = 0; t < 32; ++t) stg[lane * 33 + t] = __uint_as_float(v[t]);
+                __syncwarp();
+                const int n = n0 + c0 + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int mr = m0 + q * 32 + rr;
+                    if (mr >= M || n >= N) continue;
+                    const float x = stg[rr * 33 + lane];
+                    if (ws)
+                        ws[((size_t)blockIdx.z * M + mr) * N + n] = x;  // split-K partial tile of split z
+                    else
+                        epi_store(e, mr, n, x);
                 }
+                __syncwarp();
             }
         }
     }
