@@ -465,6 +465,7 @@ def run_batch(args):
             "solved": int(sum(1 for r in allres if r[0] == B.SOLVED)),
             "median_iters": float(np.median([r[1] for r in allres])),
             "threads_per_block": tuned, "setup_s": setup_s,
+            "kernel_ms": [1e3 * infos[0]["kernel_s"][0], 1e3 * infos[0]["kernel_s"][1]],
             "time_to_eps_s": total_ms / args.steps / 1e3,
             "fp64_batch_solves_per_s": None if fp64_ms is None else len(probs_all) * args.steps / (fp64_ms / 1e3),
             "speedup_vs_fp64_batch": None if fp64_ms is None else fp64_ms / total_ms,
@@ -498,7 +499,7 @@ def run_c5(args):
     # restarted Broyden (c0 = 0.1) halves the iterations of AA on this family, and FP64 avoids the
     # FP32-phase tail of a few slow instances that a batch would wait for
     kw = dict(direction=B.DIR_RB, mem=10, c0=0.1, precision=B.FP64, eps=eps, max_iters=20000, cg_adapt=1e-2,
-              warm_fallback=50)
+              warm_fallback=args.c5_fallback)
     prob0 = W.lasso(F=F, g=W.lasso_family_rhs(F, seed=1))
 
     def batch_of(gs):
@@ -583,7 +584,7 @@ def run_c5(args):
         "config": {"workload": "parametric LASSO F 2000x5000 1% (n=10001, m=12002), batches of 256 held-out "
                                "instances, MLP 2000-1024-1024-22004", "train_instances": int(Xd.shape[0]),
                    "epochs": args.c5_epochs, "eps": eps, "direction": "RB mem 10, c0 0.1", "precision": "fp64",
-                   "warm_fallback": 50, "family": args.c5_family},
+                   "warm_fallback": args.c5_fallback, "family": args.c5_family},
         "cold_solves_per_s": 256.0 / tc, "warm_solves_per_s_incl_inference": 256.0 / (tw + ti),
         "speedup_warm_vs_cold": tc / (tw + ti),
         "median_iters_cold": float(np.median([i["iters"] for i in cold_i])),
@@ -765,7 +766,9 @@ def main():
     ap.add_argument("--mixed-refine", type=int, default=None,
                     help="1: the FP64 phase solves by iterative refinement with FP32 corrections")
     ap.add_argument("--instances", type=int, default=4096, help="batch size of the c4 workload")
-    ap.add_argument("--c5-train", type=int, default=16384, help="training instances of the learned warm start")
+    ap.add_argument("--c5-train", type=int, default=50000, help="training instances of the learned warm start")
+    ap.add_argument("--c5-fallback", type=int, default=15,
+                    help="outer iterations after which a warm start not below the cold start's ||Ru0|| is abandoned")
     ap.add_argument("--c5-epochs", type=int, default=60)
     ap.add_argument("--c5-family", default="random", choices=["random", "smooth"],
                     help="random: a new 5%% support per instance (the specified family); smooth: fixed support, "

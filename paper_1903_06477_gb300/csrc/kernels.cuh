@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int
     __shared__ SmemFixed sf;
     __shared__ int sidx;
     extern __shared__ __align__(128) unsigned char dyn[];
-    BlockTeam tm{sf.red, nullptr, sf.mbar, sf.ph, nullptr};
+    BlockTeam tm{sf.red, nullptr, sf.mbar, sf.ph, nullptr, sf.L};
     for (;;) {
         if (threadIdx.x == 0) sidx = atomicAdd(queue, 1);
         __syncthreads();

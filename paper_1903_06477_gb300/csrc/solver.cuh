@@ -788,20 +788,34 @@ __device__ void chol_factor(Team& tm, const DevProb<T>& P, const DevWork<T>& W)
     __syncthreads();
 }
 
-// b (n, in place) <- (L L^T)^{-1} b; zb: CHOL_B values of shared memory
+// b (n, in place) <- (L L^T)^{-1} b.  dg: CHOL_B x CHOL_B values of shared
+// memory for the diagonal block, loaded by the whole CTA with coalesced reads
+// before warp 0 solves it; element (r, c) sits at r CHOL_B + (c xor r), so the
+// lanes of a warp reading one column, or one row, hit distinct banks.  zb:
+// CHOL_B values of shared memory.
 template <typename T, class Team>
-__device__ void chol_solve(Team& tm, const T* L, int n, T* b, T* zb)
+__device__ void chol_solve(Team& tm, const T* L, int n, T* b, T* dg, T* zb)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto D = [&](int r, int c) -> T& { return dg[r * CHOL_B + (c ^ r)]; };
+    auto load_diag = [&](int jb, int w) {
+        __syncthreads();  // the previous block's readers are done
+        for (int idx = threadIdx.x; idx < w * CHOL_B; idx += blockDim.x) {
+            const int r = idx / CHOL_B, c = idx % CHOL_B;
+            D(r, c) = c < w ? L[(size_t)(jb + r) * n + jb + c] : T(0);
+        }
+        __syncthreads();
+    };
     // forward: L z = b
     for (int jb = 0; jb < n; jb += CHOL_B) {
         const int w = min(CHOL_B, n - jb);
+        load_diag(jb, w);
         if (warp == 0) {
             T v = lane < w ? b[jb + lane] : T(0);
             for (int c = 0; c < w; ++c) {
-                const T zc = __shfl_sync(FULL_MASK, v, c) / L[(size_t)(jb + c) * n + jb + c];
+                const T zc = __shfl_sync(FULL_MASK, v, c) / D(c, c);
                 if (lane == c) v = zc;
-                if (lane > c && lane < w) v -= L[(size_t)(jb + lane) * n + jb + c] * zc;
+                if (lane > c && lane < w) v -= D(lane, c) * zc;
             }
             if (lane < w) {
                 b[jb + lane] = v;
@@ -820,12 +834,13 @@ __device__ void chol_solve(Team& tm, const T* L, int n, T* b, T* zb)
     // backward: L^T x = z
     for (int jb = ((n - 1) / CHOL_B) * CHOL_B; jb >= 0; jb -= CHOL_B) {
         const int w = min(CHOL_B, n - jb);
+        load_diag(jb, w);
         if (warp == 0) {
             T v = lane < w ? b[jb + lane] : T(0);
             for (int c = w - 1; c >= 0; --c) {
-                const T xc = __shfl_sync(FULL_MASK, v, c) / L[(size_t)(jb + c) * n + jb + c];
+                const T xc = __shfl_sync(FULL_MASK, v, c) / D(c, c);
                 if (lane == c) v = xc;
-                if (lane < c) v -= L[(size_t)(jb + c) * n + jb + lane] * xc;
+                if (lane < c) v -= D(c, lane) * xc;
             }
             if (lane < w) {
                 b[jb + lane] = v;
@@ -848,6 +863,13 @@ __device__ void chol_solve(Team& tm, const T* L, int n, T* b, T* zb)
 // iterations; htp = <c, x> + <b, y>.  CG stops when ||res|| <= rtol ||rhs||.
 // (Block elimination of the linear-system step of Eq. drs; Sec. 4.1 names CG.)
 // ---------------------------------------------------------------------------
+template <typename T, class Team>
+__device__ __forceinline__ bool direct_available(const Team&, const DevWork<T>& W)
+{
+    if constexpr (Team::kGrid) return false;
+    else return W.chol != nullptr;
+}
+
 template <typename T, class Team>
 __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T* a, const T* e, T* x, double rtol,
                     int cg_max, double& htp, double atol = 0.0)
@@ -874,10 +896,13 @@ __device__ int minv(Team& tm, const DevProb<T>& P, const DevWork<T>& W, const T*
     if (rhs2 == 0.0) {
         for (int j = tm.rank(); j < n; j += tm.size()) x[j] = 0;
         tm.sync();
-    } else if (W.chol != nullptr && !Team::kGrid) {
+    } else if (direct_available(tm, W)) {
         // direct: x <- x + (L L^T)^{-1} r, the residual of the warm start solved exactly
-        __shared__ T zb[CHOL_B];
-        chol_solve<T>(tm, W.chol, n, r, zb);
+        if constexpr (!Team::kGrid) {
+            // shared scratch of the CTA: the AA direction's Cholesky array (idle during a linear
+            // solve) for the diagonal block, the reduction rows for the block's solution
+            chol_solve<T>(tm, W.chol, n, r, reinterpret_cast<T*>(tm.scratch), reinterpret_cast<T*>(tm.red));
+        }
         for (int j = tm.rank(); j < n; j += tm.size()) x[j] += r[j];
         tm.sync();
     } else if (sqrt(rr) > tol) {

@@ -88,6 +88,7 @@ struct BlockTeam {
     unsigned long long* mbar;  // per-warp mbarriers
     unsigned* ph;              // per-warp mbarrier phase bits
     int* abort_flag;
+    double* scratch;           // AAMAX * AAMAX doubles of shared memory, free during linear solves
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }
     __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
