@@ -144,6 +144,11 @@ typedef struct {
                                sees tau_ = 0 its stall window is 5 mixed_stall iterations -- the
                                residuals of Sec. 4.3 are undefined then and ||Ru|| may plateau while
                                the iterate turns away from the tau axis; 0: mixed_stall throughout */
+    double psd_recheck_tol; /* SCS_MIXED with PSD cones: every FP32 eigendecomposition of a PSD block
+                               (Sec. 2, cone (ii)) is checked in FP64, ||X V - V L||_F / ||X||_F; a
+                               block above this bound is decomposed again in FP64 and projected from
+                               that.  Default 1e-4, ten times the largest residual of converged FP32
+                               Jacobi sweeps on order-64 blocks; 0 redoes every block; must be >= 0 */
 } scs_settings;
 
 typedef struct {
@@ -177,6 +182,8 @@ typedef struct {
     double part_s[2][5];    /* device time of the parts of Algorithm 1 in the FP64 [0] and FP32 [1]
                                phase: termination tests, directions, linear solves (all), the CG
                                loops inside them, the rest (steps, line searches, projections) */
+    int64_t psd_redo_fp32;  /* PSD projections of the FP32 phase recomputed in FP64 (eigen-residual
+                               above psd_recheck_tol) */
 } scs_info;
 
 typedef struct scs_work scs_work;   /* opaque; owns all device memory of one problem */
@@ -259,6 +266,13 @@ int scs_residuals_noalloc(int32_t m, int32_t n, const int64_t *Ap, const int32_t
 int scs_linsys(scs_work *work, const double *r, double *out, int32_t slot);
 /* out = Pi_C(v), C = R^n x K* x R_+ (Sec. 3.1; projection step of Eq. drs). */
 int scs_project_cone(scs_work *work, const double *v, double *out);
+/* The same projection in the bulk precision SCS_FP64 or (works set up with
+ * SCS_MIXED) as the FP32 phase runs it -- FP32 data, FP32 Jacobi eigensolves
+ * with the FP64 recheck and redo of psd_recheck_tol.  stats (may be NULL)
+ * receives [0] the largest relative eigen-residual of the FP32 eigensolves
+ * and [1] the number of PSD blocks decomposed again in FP64 (both 0 for
+ * SCS_FP64).  Pointers host or device; SCS_EINVAL on bad arguments. */
+int scs_project_cone_prec(scs_work *work, int32_t precision, const double *v, double *out, double *stats);
 /* Tu = u + Pi_C(2u~ - u) - u~ and Ru = u - Tu (Sec. 4.1-4.2); either may be NULL. */
 int scs_apply_T(scs_work *work, const double *u, double *Tu, double *Ru);
 

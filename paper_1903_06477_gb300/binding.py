@@ -44,7 +44,7 @@ class Settings(C.Structure):
         ("mixed_cg_rtol", C.c_double), ("mixed_stall", C.c_int32), ("mixed_max_iters", C.c_int32),
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
         ("warm_fallback", C.c_int32), ("mixed_resume", C.c_int32), ("mixed_refine", C.c_int32),
-        ("linsys_direct", C.c_int32), ("mixed_stall_after_tau", C.c_int32),
+        ("linsys_direct", C.c_int32), ("mixed_stall_after_tau", C.c_int32), ("psd_recheck_tol", C.c_double),
     ]
 
 
@@ -59,7 +59,7 @@ class Info(C.Structure):
         ("psd_resid_fp32", C.c_double), ("threads_per_block", C.c_int32), ("warm_fallback_taken", C.c_int32),
         ("kkt_fp32", C.c_double), ("mat_passes_ir", C.c_int64), ("cg_iters_ir", C.c_int64),
         ("ir_sweeps", C.c_int64), ("batch_device_s", C.c_double), ("team", C.c_int32),
-        ("part_s", (C.c_double * 5) * 2),
+        ("part_s", (C.c_double * 5) * 2), ("psd_redo_fp32", C.c_int64),
     ]
 
     def as_dict(self):
@@ -86,6 +86,7 @@ _SIGS = [
     ("scs_set_warm", C.c_int, [C.c_void_p, C.c_void_p]),
     ("scs_linsys", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("scs_project_cone", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("scs_project_cone_prec", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_apply_T", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     ("scs_spmv", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -257,6 +258,14 @@ class Work:
         out = np.empty(self.N)
         _check(lib().scs_project_cone(self.h, _ptr(v), _ptr(out)), self.h)
         return out
+
+    def project_cone_prec(self, v, precision):
+        """Pi_C(v) as the given precision's phase computes it; returns (out, [max eigen-residual, blocks redone])."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.empty(self.N)
+        stats = np.zeros(2)
+        _check(lib().scs_project_cone_prec(self.h, precision, _ptr(v), _ptr(out), _ptr(stats)), self.h)
+        return out, stats
 
     def residuals(self, x, y, s, out=None):
         """(pr, dr, gap) of Sec. 4.3 for a candidate; arrays host or CUDA."""

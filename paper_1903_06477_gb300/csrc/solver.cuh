@@ -49,6 +49,8 @@ struct DevSettings {
     int stall_after_tau;   // 1: the stall count starts only once tau_ > 0 (FP32 phase of SCS_MIXED)
     int refine;            // 1 (FP64 data only): linear systems by iterative refinement, FP64 residuals
                            // and FP32 CG corrections on the FP32 copy of A (W.ir)
+    double psd_tol;        // FP32 eigensolves: a PSD block whose FP64-evaluated relative eigen-residual
+                           // exceeds this is decomposed again in FP64
 };
 
 // State of Algorithm 1 at the end of the FP32 phase of SCS_MIXED, so that the
@@ -78,6 +80,7 @@ struct DevState {
     // refinement variant), [3] the CG loops inside them, [4] everything else (K0 steps, line
     // searches, projections, updates)
     double part_ns[5];
+    long long psd_redo;    // PSD blocks of the FP32 phase decomposed again in FP64 (eigen-residual above psd_tol)
 };
 
 // Column-blocked sliced ELL, the grid team's layout for large matrices.  CTA b
@@ -1338,9 +1341,32 @@ __device__ PsdSmem<T> psd_smem(unsigned char* base)
     return s;
 }
 
+// Where the FP32 eigensolves report to: the largest relative eigen-residual
+// (FP64-evaluated), the count of blocks decomposed again in FP64, and the
+// bound above which that happens.
+struct PsdCheck {
+    double* resid;
+    long long* redo;
+    double tol;
+};
+
+// FP64 Jacobi of the block whose FP64 copy X0 is in shared memory (FP32
+// eigensolves only).  The FP32 X and V are dead by now: the FP64
+// eigenvectors overlay them (2 PSD_MAX x PSD_LD floats = PSD_MAX x PSD_LD
+// doubles), the rotation cosines and sines the FP32 cs / sn and lam arrays.
+// X0 leaves with the eigenvalues on its diagonal, V64 with the eigenvectors.
+static __device__ __noinline__ void psd_redo_fp64(PsdSmem<float>& sm, int dp, int ld)
+{
+    double* V64 = reinterpret_cast<double*>(sm.X);
+    double* cs64 = reinterpret_cast<double*>(sm.cs);
+    double* sn64 = reinterpret_cast<double*>(sm.lam);
+    __syncthreads();
+    jacobi_block<double>(sm.X0, V64, dp, ld, sm.pp, sm.qq, cs64, sn64, sm.red, 1e-26, 20);
+}
+
 template <typename T, class Team, class Op>
 __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned char* psd_base,
-                             double* psd_resid = nullptr)
+                             PsdCheck ck = PsdCheck{nullptr, nullptr, 0.0})
 {
     const int n = P.n;
     const int lin = n + P.f + P.l;
@@ -1427,9 +1453,30 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                 }
                 r2 = block_sum(r2, sm.red);
                 x2 = block_sum(x2, sm.red);
-                if (threadIdx.x == 0 && x2 > 0.0 && psd_resid) {
-                    const double rel = sqrt(r2 / x2);
-                    atomicMax((unsigned long long*)psd_resid, (unsigned long long)__double_as_longlong(rel));
+                // block_sum hands every thread the same sums, so the decision
+                // to decompose the block again in FP64 is uniform in the CTA
+                const double rel = x2 > 0.0 ? sqrt(r2 / x2) : 0.0;
+                if (threadIdx.x == 0 && ck.resid)
+                    atomicMax((unsigned long long*)ck.resid, (unsigned long long)__double_as_longlong(rel));
+                if (rel > ck.tol && ck.redo) {
+                    psd_redo_fp64(sm, dp, ld);
+                    if (threadIdx.x == 0) atomicAdd((unsigned long long*)ck.redo, 1ull);
+                    const double* V64 = reinterpret_cast<const double*>(sm.X);
+                    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+                        const int i = idx / d, j = idx % d;
+                        if (i < j) continue;
+                        double s = 0.0;
+                        for (int kk = 0; kk < dp; ++kk) {
+                            const double l = sm.X0[kk * ld + kk];
+                            if (l > 0.0) s += V64[i * ld + kk] * l * V64[j * ld + kk];
+                        }
+                        const int e = o + svec_index(d, i, j);
+                        T w, wt;
+                        op.load(e, w, wt);
+                        op.store(e, w, wt, (T)(i == j ? s : s * 1.41421356237309504880));
+                    }
+                    __syncthreads();
+                    continue;
                 }
             }
             for (int i = threadIdx.x; i < dp; i += blockDim.x) {
@@ -2208,6 +2255,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         W.st->ir_sweeps = 0;
         for (int k = 0; k < 5; ++k) W.st->part_ns[k] = 0.0;
         W.st->psd_resid = 0.0;
+        W.st->psd_redo = 0;
         W.st->fallback = 0;
     }
     // residual of the cold start, the yardstick of the warm-start fallback
@@ -2219,7 +2267,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         tm.sync();
         cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, 0.0, S.refine != 0);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, &W.st->psd_resid);
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
         double red[1] = {(double)op.acc0};
         tm.reduce(red);
         nRu_cold = sqrt(red[0]);
@@ -2232,7 +2280,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
     double nRu;
     {
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, &W.st->psd_resid);
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
         double red[1] = {(double)op.acc0};
         tm.reduce(red);
         nRu = sqrt(red[0]);
@@ -2353,7 +2401,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             // K0
             eta = nRu;
             OpK0<T> op{W.u, W.ut, W.ub, W.Ru, W.d, W.dt, W.zp, W.xip, T(0), T(0)};
-            project_pass(tm, P, op, psd, &W.st->psd_resid);
+            project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
             double red[2] = {(double)op.acc0, (double)op.acc1};
             tm.reduce(red);
             nRu = sqrt(red[0]);
@@ -2364,7 +2412,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             for (int ls = 0; ls <= S.ls_max; ++ls) {
                 if (ls == S.ls_max) alpha = 0.0;
                 OpTrial<T> op{W.u, W.ut, W.d, W.dt, W.wb, W.Rw, alpha, T(0), T(0)};
-                project_pass(tm, P, op, psd, &W.st->psd_resid);
+                project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
                 double red[2] = {(double)op.acc0, (double)op.acc1};
                 tm.reduce(red);
                 const double nRw = sqrt(red[0]);
@@ -2424,7 +2472,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
                     nz2 = red2[0];
                     cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol, S.refine != 0);
                     OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
-                    project_pass(tm, P, opr, psd, &W.st->psd_resid);
+                    project_pass(tm, P, opr, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
                     double red3[1] = {(double)opr.acc0};
                     tm.reduce(red3);
                     nRu = sqrt(red3[0]);
@@ -2666,7 +2714,11 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
     }
     // single operators: io_in (FP64, N) -> u (T), results to io_out / io_out2
     for (int i = tm.rank(); i < nm; i += tm.size()) W.u.v[i] = (T)W.io_in[i];
-    if (tm.leader()) *W.u.t = W.io_in[nm];
+    if (tm.leader()) {
+        *W.u.t = W.io_in[nm];
+        W.st->psd_resid = 0.0;
+        W.st->psd_redo = 0;
+    }
     tm.sync();
     if (mode == MODE_LINSYS) {
         // slot 0 / 1: the CG warm start of u~ / d~; + 2: by iterative refinement (FP64 data only)
@@ -2675,14 +2727,14 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
         if (tm.leader()) W.io_out[nm] = *W.ut.t;
     } else if (mode == MODE_PROJECT) {
         OpProject<T> op{W.u.v, W.u.t, W.ub.v, W.ub.t};
-        project_pass(tm, P, op, psd, &W.st->psd_resid);
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ub.v[i];
         if (tm.leader()) W.io_out[nm] = *W.ub.t;
     } else if (mode == MODE_APPLY_T) {
         linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, W.st->hg);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, &W.st->psd_resid);
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) {
             W.io_out[i] = (double)W.u.v[i] - (double)W.Ru.v[i];

@@ -392,6 +392,7 @@ static int check_settings(const scs_settings* S, char* err)
     if (!(S->sigma > 0 && S->sigma < 1)) { set_err(err, "sigma must lie in (0,1)"); return SCS_EINVAL; }
     if (S->precision != SCS_FP64 && S->precision != SCS_MIXED) { set_err(err, "bad precision"); return SCS_EINVAL; }
     if (S->threads != 0 && (S->threads < 32 || S->threads > 1024 || S->threads % 32)) { set_err(err, "threads must be a multiple of 32 in 32..1024"); return SCS_EINVAL; }
+    if (!(S->psd_recheck_tol >= 0)) { set_err(err, "psd_recheck_tol must be >= 0"); return SCS_EINVAL; }
     return SCS_OK;
 }
 
@@ -630,6 +631,7 @@ static DevSettings dev_settings(const scs_settings* S)
     D.resume = 0;
     D.refine = 0;
     D.stall_after_tau = S->mixed_stall_after_tau;
+    D.psd_tol = S->psd_recheck_tol;
     return D;
 }
 
@@ -748,6 +750,7 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->mixed_refine = 1;
     o->linsys_direct = 0;
     o->mixed_stall_after_tau = 1;
+    o->psd_recheck_tol = 1e-4;
     return SCS_OK;
 }
 
@@ -1061,6 +1064,7 @@ extern "C" int scs_solve(scs_work* w, double* x, double* y, double* s, scs_info*
             info->mat_passes[1] = st32.mat_passes;
             info->cg_iters_fp32 = st32.cg_iters;
             info->psd_resid_fp32 = st32.psd_resid;
+            info->psd_redo_fp32 = st32.psd_redo;
             for (int k = 0; k < 5; ++k) info->part_s[1][k] = st32.part_ns[k] * 1e-9;
         }
     }
@@ -1144,6 +1148,36 @@ static int single_op(scs_work* w, int mode, int slot, const double* in, double* 
     if (out) CU(cudaMemcpyAsync(out, w->W64.io_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     if (out2) CU(cudaMemcpyAsync(out2, w->W64.io_out2, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
     CU(cudaStreamSynchronize(w->stream), w->err);
+    return SCS_OK;
+}
+
+extern "C" int scs_project_cone_prec(scs_work* w, int32_t precision, const double* v, double* out, double* stats)
+{
+    if (!w || !v || !out) { set_err(w ? w->err : g_err, "NULL argument"); return SCS_EINVAL; }
+    if (precision == SCS_FP64) {
+        const int rc = single_op(w, MODE_PROJECT, 0, v, out, nullptr);
+        if (rc == SCS_OK && stats) {
+            const double z[2] = {0.0, 0.0};
+            CU(cudaMemcpy(stats, z, sizeof z, cudaMemcpyDefault), w->err);
+        }
+        return rc;
+    }
+    if (precision != SCS_MIXED) { set_err(w->err, "bad precision"); return SCS_EINVAL; }
+    if (!w->has32) { set_err(w->err, "work was not set up with SCS_MIXED"); return SCS_EINVAL; }
+    const int N = w->H.n + w->H.m + 1;
+    CU(cudaMemcpyAsync(w->W32.io_in, v, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    DevSettings S = dev_settings(&w->S);
+    Args<float> a = make_args(w->P32, w->W32, S, MODE_PROJECT, 0);
+    int rc = launch<float>(w->D, w->D.dyn32, a, w->dargs32, w->queue, w->stream, w->err);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, w->W32.io_out, sizeof(double) * N, cudaMemcpyDefault, w->stream), w->err);
+    DevState st;
+    CU(cudaMemcpyAsync(&st, w->W32.st, sizeof st, cudaMemcpyDeviceToHost, w->stream), w->err);
+    CU(cudaStreamSynchronize(w->stream), w->err);
+    if (stats) {
+        const double s2[2] = {st.psd_resid, (double)st.psd_redo};
+        CU(cudaMemcpy(stats, s2, sizeof s2, cudaMemcpyDefault), w->err);
+    }
     return SCS_OK;
 }
 
@@ -1742,6 +1776,7 @@ extern "C" int scs_batch_solve(scs_batch* b, double* const* x, double* const* y,
                 info->cg_iters_fp32 = t.cg_iters;
                 info->mat_passes[1] = t.mat_passes;
                 info->psd_resid_fp32 = t.psd_resid;
+                info->psd_redo_fp32 = t.psd_redo;
                 info->kernel_s[1] = ms32 * 1e-3;
             }
             info->setup_s = b->setup_s;

@@ -367,6 +367,58 @@ def test_psd_projection_large_blocks(team):
         np.testing.assert_allclose(work.project_cone(v), orc.proj_C(v), rtol=0, atol=1e-10)
 
 
+def _psd_segments(prob, n):
+    """(start, length) of each PSD block's svec rows in an HSDE vector (x, y, tau)."""
+    o = n + prob["f"] + prob["l"] + int(sum(prob["q"]))
+    segs = []
+    for d in prob["s"]:
+        segs.append((o, d * (d + 1) // 2))
+        o += d * (d + 1) // 2
+    return segs
+
+
+@pytest.mark.parametrize("team", TEAMS)
+def test_psd_fp32_recheck_redoes_blocks_in_fp64(team):
+    """Sec. 2, cone (ii): the FP32 phase's eigensolves are checked in FP64 and a block above
+    psd_recheck_tol is decomposed again in FP64.  With the bound 0 every block is redone: its
+    projection is then the exact one of the FP32-rounded block, so (projection being
+    1-Lipschitz) it lies within a few FP32 roundings of the FP64 oracle's, ||.||_F per block.
+    With the default bound no converged FP32 eigensolve is redone."""
+    prob = W.planted(seed=43, n=40, l=10, psd=[64, 33, 17, 2], nnz=2000)
+    orc = O.Oracle(prob)
+    u32 = 2.0 ** -24
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(40 + prob["A"].shape[0] + 1) * 2
+    ref = orc.proj_C(v)
+    segs = _psd_segments(prob, 40)
+    forced = B.Work(prob, team=team, precision=B.MIXED, psd_recheck_tol=0.0)
+    out, stats = forced.project_cone_prec(v, B.MIXED)
+    assert stats[1] == len(prob["s"])
+    for o, k in segs:
+        err = np.linalg.norm(out[o:o + k] - ref[o:o + k])
+        assert err <= 6 * u32 * np.linalg.norm(v[o:o + k]), (o, k, err)
+    default = B.Work(prob, team=team, precision=B.MIXED)
+    out_d, stats_d = default.project_cone_prec(v, B.MIXED)
+    assert stats_d[1] == 0 and 0 < stats_d[0] < 1e-4
+    for o, k in segs:
+        assert np.linalg.norm(out_d[o:o + k] - ref[o:o + k]) <= 1e-4 * np.linalg.norm(v[o:o + k])
+    # the FP64 form reports nothing and matches the oracle
+    out64, stats64 = default.project_cone_prec(v, B.FP64)
+    assert list(stats64) == [0.0, 0.0]
+    np.testing.assert_allclose(out64, ref, rtol=0, atol=1e-10)
+
+
+def test_psd_fp32_redo_in_a_solve():
+    """A mixed solve with every FP32 PSD projection redone in FP64 still reaches eps."""
+    prob = W.planted(seed=42, n=300, l=200, psd=[16] * 6 + [9, 33], nnz=6000)
+    eps = 1e-5
+    work = B.Work(prob, precision=B.MIXED, eps=eps, max_iters=20000, cg_adapt=1e-2, psd_recheck_tol=0.0)
+    x, y, s, info = work.solve()
+    assert info["status"] == B.SOLVED, info
+    assert max(_kkt(prob, x, y, s)) <= eps * 1.01
+    assert info["psd_redo_fp32"] >= info["iters_fp32"] * len(prob["s"])
+
+
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
 def test_planted_sdp_small(precision):
     prob = W.planted(seed=42, n=300, l=200, psd=[16] * 6 + [9, 33], nnz=6000)
@@ -382,6 +434,7 @@ def test_planted_sdp_small(precision):
     assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
     if precision == B.MIXED:
         assert 0 < info["psd_resid_fp32"] < 1e-4  # FP64 recheck of the FP32 eigensolves
+        assert info["psd_redo_fp32"] == 0  # converged FP32 eigensolves stay below the default bound
 
 
 def test_batch_autotuned_mixed():
