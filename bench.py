@@ -761,6 +761,8 @@ def main():
     ap.add_argument("--mixed-resume", type=int, default=None, help="1: the FP64 phase continues the FP32 loop state")
     ap.add_argument("--stall-after-tau", type=int, default=None,
                     help="1: the FP32 phase's stall count starts once tau_ > 0")
+    ap.add_argument("--spmv-path", type=int, default=None,
+                    help="grid-team sparse products: 0 automatic, 1/2 sliced ELL, 3 column-blocked, 4 tiles")
     ap.add_argument("--linsys-direct", type=int, default=None,
                     help="1: block-team instances solve their linear systems by a dense Cholesky factor")
     ap.add_argument("--mixed-refine", type=int, default=None,
@@ -833,7 +835,10 @@ def main():
         kw["linsys_direct"] = args.linsys_direct
     if args.mixed_refine is not None:
         kw["mixed_refine"] = args.mixed_refine
-    for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine", "linsys_direct"):
+    if args.spmv_path is not None:
+        kw["spmv_path"] = args.spmv_path
+    for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine", "linsys_direct",
+                "spmv_path"):
         if key in kw:
             cfg[key] = kw[key]
     prec = B.MIXED if args.precision == "mixed" else B.FP64

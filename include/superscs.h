@@ -116,12 +116,16 @@ typedef struct {
     double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
-    int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- the column-blocked
-                               layout (vector slices staged in shared memory, one CTA per SM) where
-                               each (CTA, column block) holds at least 1024 entries on average, else
-                               sliced ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL,
-                               TMA-staged stream; 3: column-blocked wherever the layout fits shared
-                               memory.
+    int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- two-dimensional tiles
+                               (one row block x column block per CTA, the vector's column block
+                               resident in shared memory, partial sums added by a second pass) where
+                               a split fits shared memory and the tiles hold at least 4096 entries
+                               on average, else the column-blocked layout (each CTA's rows against
+                               every column block, vector slices staged per block) where each (CTA,
+                               column block) holds at least 1024 entries on average, else sliced
+                               ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL, TMA-staged
+                               stream; 3: column-blocked wherever the layout fits shared memory;
+                               4: tiles wherever a split fits, else as 3.
                                The block team always uses sliced ELL. */
     int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
                                after this many iterations is abandoned for the cold start */
@@ -299,6 +303,18 @@ int scs_spmv(scs_work *work, int32_t precision, int32_t op, const double *in, co
 int scs_cb_layout_check(int32_t rows, int32_t cols, const int64_t *Ap, const int32_t *Ai, const double *Ax,
                         int32_t ctas, int32_t compute_warps, int32_t elem_bytes, int32_t vectors,
                         int64_t smem_bytes, const double *x, double *y, int64_t *stats);
+/* The same for the two-dimensional tiled layout (tiles of a row block times
+ * a column block, one per CTA, the column block's slice of x resident in
+ * shared memory, partial sums per column block added in block order by a
+ * second pass): builds it (forced, whatever the size), checks its invariants
+ * and replays y = A x as the tile passes and the second pass compute it, in
+ * FP64.  stats[8]: [0] violated invariants, [1] column blocks (0: no split
+ * fits), [2] row blocks, [3] lanes per row, [4] stored entries, [5] dynamic
+ * shared memory, [6] chunks, [7] metadata words per chunk.  SCS_EINVAL on
+ * bad input. */
+int scs_tile_layout_check(int32_t rows, int32_t cols, const int64_t *Ap, const int32_t *Ai, const double *Ax,
+                          int32_t ctas, int32_t compute_warps, int32_t elem_bytes, int32_t vectors,
+                          int64_t smem_bytes, const double *x, double *y, int64_t *stats);
 
 /* Device-side timing (globaltimer between team barriers, inside one launch)
  * of the solver's building blocks on this problem, for roofline measurement:

@@ -93,6 +93,9 @@ _SIGS = [
     ("scs_cb_layout_check", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                       C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    ("scs_tile_layout_check", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                        C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     ("scs_residuals", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("scs_residuals_noalloc", C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 10),
     ("scs_finish", None, [C.c_void_p]),
@@ -315,6 +318,23 @@ def cb_layout_check(A, x, ctas=152, compute_warps=15, elem_bytes=4, vectors=1, s
     _check(lib().scs_cb_layout_check(A.shape[0], A.shape[1], _ptr(Ap), _ptr(Ai), _ptr(Ax), ctas, compute_warps,
                                      elem_bytes, vectors, smem_bytes, _ptr(x), _ptr(y), _ptr(st)))
     keys = ("violations", "column_blocks", "block_width", "lanes", "entries", "smem_bytes", "stages", "meta_words")
+    return y, dict(zip(keys, st.tolist()))
+
+
+def tile_layout_check(A, x, ctas=152, compute_warps=15, elem_bytes=4, vectors=1, smem_bytes=209536):
+    """Host-only check of the two-dimensional tiled layout of the CSR matrix A
+    (see scs_tile_layout_check): returns (y = A x replayed through the tiles
+    and the partial-sum pass, stats dict)."""
+    A = A.tocsr()
+    Ap = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    Ai = np.ascontiguousarray(A.indices, dtype=np.int32)
+    Ax = np.ascontiguousarray(A.data, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(A.shape[0])
+    st = np.zeros(8, dtype=np.int64)
+    _check(lib().scs_tile_layout_check(A.shape[0], A.shape[1], _ptr(Ap), _ptr(Ai), _ptr(Ax), ctas, compute_warps,
+                                       elem_bytes, vectors, smem_bytes, _ptr(x), _ptr(y), _ptr(st)))
+    keys = ("violations", "column_blocks", "row_blocks", "lanes", "entries", "smem_bytes", "chunks", "meta_words")
     return y, dict(zip(keys, st.tolist()))
 
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <numeric>
 #include <vector>
@@ -13,10 +14,15 @@
 struct CbLayout {
     int ncb = 0, cw = 0, cols = 0, nw = 0, V = 1, acc_rows = 0, ms = 0, S = 0, stage_off = 0, stage_bytes = 0,
         off_x = 0, off_col = 0, off_val = 0, esize = 8;
-    std::vector<int> rbnd, meta;
+    // two-dimensional tiles (tile = 1): R row blocks x ncb column blocks, tile
+    // g = r * ncb + k on CTA g; its chunks are [cbeg[g], cbeg[g+1]) of meta
+    int tile = 0, R = 0, rows = 0, nv = 1;
+    std::vector<int> rbnd, meta, cbeg;
     std::vector<uint16_t> col;
     std::vector<double> val;
     size_t dyn() const { return ncb ? (size_t)stage_off + (size_t)S * stage_bytes : 0; }
+    // partial sums of a tiled product: two buffers of nv vectors x ncb column blocks x rows
+    size_t part_elems() const { return tile ? (size_t)2 * nv * ncb * rows : 0; }
 };
 
 // ---------------------------------------------------------------------------
@@ -133,6 +139,66 @@ static int cb_meta_words(int nw, int ns, int H)
     return 5 + (nw + 1) + (ns + 1) + (ns * H + 1) / 2;
 }
 
+// Entry placement inside a slice.  Every lane of a step gathers one element
+// of the vector slice from shared memory; lanes whose elements share a bank
+// are served one after another.  The row of each lane is fixed, but which of
+// its entries goes to which step is free, so each step takes, lane by lane,
+// the row's remaining entry in the least-used bank (FP32: column mod 32 over
+// the warp; FP64: column mod 16 within each half-warp, which is served
+// separately).  Padding lanes point at a column in a free bank (value 0).  A
+// staged slice starts at a shift that is the same for all its elements, so
+// distinct banks stay distinct.  rem[rr] holds the CSR indices of the
+// entries of the slice's row rr (consumed); the slice's nsteps x 32 entries
+// are written at C.col / C.val [e0, ...) for column block k.
+static void cb_place_slice(CbLayout& C, std::vector<std::vector<int>>& rem, size_t e0, int nsteps, int k, int cw,
+                           int cols, int V, const std::vector<int>& ci, const std::vector<double>& vx)
+{
+    const int H = 32 / V;
+    const int nbank = C.esize == 8 ? 16 : 32;
+    const int len_k = std::min(cw, cols - k * cw);
+    for (int t = 0; t < nsteps; ++t) {
+        int cnt[2][32] = {};
+        bool pad[32] = {};
+        for (int q = 0; q < V; ++q)
+            for (int rr = 0; rr < H; ++rr) {
+                const int lane = q * H + rr, half = nbank == 16 ? lane >> 4 : 0;
+                std::vector<int>& rl = rem[rr];
+                if (rl.empty()) {
+                    pad[lane] = true;
+                    continue;
+                }
+                size_t best = 0;
+                int bc = 1 << 30;
+                for (size_t i = 0; i < rl.size(); ++i) {
+                    const int c = cnt[half][(ci[rl[i]] - k * cw) % nbank];
+                    if (c < bc) {
+                        bc = c;
+                        best = i;
+                    }
+                }
+                const int e = rl[best];
+                rl[best] = rl.back();
+                rl.pop_back();
+                const int lc = ci[e] - k * cw;
+                cnt[half][lc % nbank]++;
+                const size_t idx = e0 + (size_t)t * 32 + lane;
+                C.col[idx] = (uint16_t)lc;
+                C.val[idx] = vx[e];
+            }
+        for (int lane = 0; lane < 32; ++lane) {
+            if (!pad[lane]) continue;
+            const int half = nbank == 16 ? lane >> 4 : 0;
+            int bb = 0;
+            for (int b2 = 1; b2 < nbank && b2 < len_k; ++b2)
+                if (cnt[half][b2] < cnt[half][bb]) bb = b2;
+            cnt[half][bb]++;
+            const size_t idx = e0 + (size_t)t * 32 + lane;
+            C.col[idx] = (uint16_t)bb;
+            C.val[idx] = 0.0;
+        }
+    }
+}
+
 // Build the column-blocked layout of a CSR matrix (rows x cols) for the row
 // ranges rb, nw compute warps per CTA, blocks of cw columns and a ring of S
 // stages.
@@ -165,61 +231,7 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
     std::vector<long long> load;
     int ms = 4;
     long long max_e = 0;
-    // Entry placement inside a slice.  Every lane of a step gathers one
-    // element of the vector slice from shared memory; lanes whose elements
-    // share a bank are served one after another.  The row of each lane is
-    // fixed, but which of its entries goes to which step is free, so each
-    // step takes, lane by lane, the row's remaining entry in the least-used
-    // bank (FP32: column mod 32 over the warp; FP64: column mod 16 within each
-    // half-warp, which is served separately).  Padding lanes point at a
-    // column in a free bank (value 0).  A staged slice starts at a shift that
-    // is the same for all its elements, so distinct banks stay distinct.
-    const int nbank = C.esize == 8 ? 16 : 32;
     std::vector<std::vector<int>> rem(32);
-    auto place_slice = [&](size_t e0, int nsteps, int k) {
-        const int len_k = std::min(cw, cols - k * cw);
-        for (int t = 0; t < nsteps; ++t) {
-            int cnt[2][32] = {};
-            bool pad[32] = {};
-            for (int q = 0; q < V; ++q)
-                for (int rr = 0; rr < H; ++rr) {
-                    const int lane = q * H + rr, half = nbank == 16 ? lane >> 4 : 0;
-                    std::vector<int>& rl = rem[rr];
-                    if (rl.empty()) {
-                        pad[lane] = true;
-                        continue;
-                    }
-                    size_t best = 0;
-                    int bc = 1 << 30;
-                    for (size_t i = 0; i < rl.size(); ++i) {
-                        const int c = cnt[half][(ci[rl[i]] - k * cw) % nbank];
-                        if (c < bc) {
-                            bc = c;
-                            best = i;
-                        }
-                    }
-                    const int e = rl[best];
-                    rl[best] = rl.back();
-                    rl.pop_back();
-                    const int lc = ci[e] - k * cw;
-                    cnt[half][lc % nbank]++;
-                    const size_t idx = e0 + (size_t)t * 32 + lane;
-                    C.col[idx] = (uint16_t)lc;
-                    C.val[idx] = vx[e];
-                }
-            for (int lane = 0; lane < 32; ++lane) {
-                if (!pad[lane]) continue;
-                const int half = nbank == 16 ? lane >> 4 : 0;
-                int bb = 0;
-                for (int b2 = 1; b2 < nbank && b2 < len_k; ++b2)
-                    if (cnt[half][b2] < cnt[half][bb]) bb = b2;
-                cnt[half][bb]++;
-                const size_t idx = e0 + (size_t)t * 32 + lane;
-                C.col[idx] = (uint16_t)bb;
-                C.val[idx] = 0.0;
-            }
-        }
-    };
     for (int b = 0; b < G; ++b) {
         const int r0 = rb[b], R = rb[b + 1] - r0;
         bk.build(r0, R, ncb, cw, rp, ci);
@@ -254,7 +266,7 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
                     const int len = bk.cnt[(size_t)k * R + lr];
                     for (int j = 0; j < len; ++j) rem[rr].push_back(bk.epos[q0 + j]);
                 }
-                place_slice(e0, steps[sl], k);
+                cb_place_slice(C, rem, e0, steps[sl], k, cw, cols, V, ci, vx);
                 t += steps[sl];
             }
             sstart[ns] = t;
@@ -351,3 +363,239 @@ static void plan_cb(int rows, int cols, const std::vector<int>& rp, const std::v
     C = CbLayout();
 }
 
+
+// ---------------------------------------------------------------------------
+// two-dimensional tiles (grid team)
+// ---------------------------------------------------------------------------
+// Tile (r, k) is row block r (rows rb[r] .. rb[r+1], balanced on entries)
+// times column block k (cw columns) and runs on CTA r * ncb + k, which keeps
+// only that column block of the multiplied vector in shared memory, copied
+// once per product.  The tile's rows with entries in the block, by count
+// descending, form slices of H = 32 / V rows (sliced ELL as above);
+// consecutive slices are grouped into chunks that fit one stage of the copy
+// ring (metadata, 16-bit column offsets, values), and inside a chunk the
+// slices are dealt to the compute warps.  Every row of a tile lies in one
+// slice, so its sum is complete when its slice is done: it goes to a
+// per-tile row array in shared memory, which is written to the partial sums
+// part[k][row] (global) once the tile is done; a second pass over the rows
+// adds the ncb partials in block order.  Chunk metadata (ms words per chunk;
+// the chunks of tile g are cbeg[g] .. cbeg[g+1]):
+//   [0] E0  [1] E1  [2], [3] E0, E1 of the tile's chunk S later (0, 0: none)
+//   [4] ns: slices  [5 .. 5+nw] first slice of each warp (nw+1 values)
+//   [6+nw .. 6+nw+ns] slice start steps from E0 (ns+1 values)
+//   then ns * H 16-bit row indices inside the row block (0xFFFF: none), two
+//   per word, low half first.
+// Chunks hold at most e_cap entries and ms_cap metadata words.  Returns false
+// if one slice alone exceeds them.
+static bool build_tile(int cols, const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<double>& vx,
+                       const std::vector<int>& rb, int Cn, int cw, int nw, int S, int V, long long e_cap, int ms_cap,
+                       CbLayout& L)
+{
+    const int R = (int)rb.size() - 1;
+    const int H = 32 / V;
+    L.tile = 1;
+    L.R = R;
+    L.ncb = Cn;
+    L.cw = cw;
+    L.cols = cols;
+    L.nw = nw;
+    L.V = V;
+    L.S = S;
+    L.rbnd = rb;
+    L.col.clear();
+    L.val.clear();
+    L.cbeg.assign((size_t)R * Cn + 1, 0);
+    struct Chunk {
+        long long e0, e1;
+        std::vector<int> words;  // [4] onwards
+    };
+    std::vector<Chunk> chunks;
+    CbBuckets bk;
+    std::vector<int> rows_k, steps, sub, warp, order;
+    std::vector<long long> load;
+    std::vector<std::vector<int>> rem(32);
+    int ms = 4;
+    for (int r = 0; r < R; ++r) {
+        const int r0 = rb[r], Rr = rb[r + 1] - r0;
+        bk.build(r0, Rr, Cn, cw, rp, ci);
+        for (int k = 0; k < Cn; ++k) {
+            L.cbeg[(size_t)r * Cn + k] = (int)chunks.size();
+            bk.sorted_rows(k, Rr, rows_k);
+            cb_slice_steps(bk, k, Rr, rows_k, V, steps);
+            const int nst = (int)steps.size();
+            for (int sl = 0; sl < nst;) {
+                // the longest run of slices within both caps
+                long long e = 0;
+                int ns = 0;
+                while (sl + ns < nst) {
+                    const long long add = 32LL * steps[sl + ns];
+                    if (e + add > e_cap || cb_meta_words(nw, ns + 1, H) > ms_cap) break;
+                    e += add;
+                    ++ns;
+                }
+                if (ns == 0) return false;
+                sub.assign(steps.begin() + sl, steps.begin() + sl + ns);
+                cb_deal(sub, nw, warp, load);
+                order.resize(ns);
+                std::iota(order.begin(), order.end(), 0);
+                std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return warp[a] < warp[c]; });
+                Chunk ch;
+                ch.e0 = (long long)L.col.size();
+                std::vector<int> wstart(nw + 1, 0), sstart(ns + 1, 0);
+                std::vector<uint16_t> srow((size_t)ns * H, 0xFFFF);
+                int w = 0, t = 0;
+                for (int oi = 0; oi < ns; ++oi) {
+                    const int ls = order[oi], gs = sl + ls;
+                    while (w <= warp[ls]) wstart[w++] = oi;
+                    sstart[oi] = t;
+                    const size_t e0 = L.col.size();
+                    const size_t size = (size_t)steps[gs] * 32;
+                    L.col.resize(e0 + size, 0);
+                    L.val.resize(e0 + size, 0.0);
+                    for (int rr = 0; rr < H; ++rr) {
+                        const size_t pos = (size_t)gs * H + rr;
+                        rem[rr].clear();
+                        if (pos >= rows_k.size()) continue;
+                        const int lr = rows_k[pos];
+                        srow[(size_t)oi * H + rr] = (uint16_t)lr;
+                        const size_t q0 = (size_t)bk.start[(size_t)k * Rr + lr];
+                        const int len = bk.cnt[(size_t)k * Rr + lr];
+                        for (int j = 0; j < len; ++j) rem[rr].push_back(bk.epos[q0 + j]);
+                    }
+                    cb_place_slice(L, rem, e0, steps[gs], k, cw, cols, V, ci, vx);
+                    t += steps[gs];
+                }
+                sstart[ns] = t;
+                while (w <= nw) wstart[w++] = ns;
+                ch.e1 = (long long)L.col.size();
+                ch.words.push_back(ns);
+                ch.words.insert(ch.words.end(), wstart.begin(), wstart.end());
+                ch.words.insert(ch.words.end(), sstart.begin(), sstart.end());
+                for (int i = 0; i < ns * H; i += 2) {
+                    const unsigned lo = srow[i], hi = i + 1 < ns * H ? srow[i + 1] : 0xFFFFu;
+                    ch.words.push_back((int)(lo | (hi << 16)));
+                }
+                ms = std::max(ms, 4 + (int)ch.words.size());
+                chunks.push_back(std::move(ch));
+                sl += ns;
+            }
+        }
+    }
+    L.cbeg[(size_t)R * Cn] = (int)chunks.size();
+    if (L.col.size() >= (1ull << 31)) return false;
+    ms = (ms + 3) & ~3;
+    L.ms = ms;
+    L.meta.assign(chunks.size() * (size_t)ms, 0);
+    for (int g = 0; g < R * Cn; ++g)
+        for (int j = L.cbeg[g]; j < L.cbeg[g + 1]; ++j) {
+            const Chunk& ch = chunks[j];
+            int* m = L.meta.data() + (size_t)j * ms;
+            m[0] = (int)ch.e0;
+            m[1] = (int)ch.e1;
+            if (j + S < L.cbeg[g + 1]) {
+                m[2] = (int)chunks[j + S].e0;
+                m[3] = (int)chunks[j + S].e1;
+            }
+            std::copy(ch.words.begin(), ch.words.end(), m + 4);
+        }
+    return true;
+}
+
+// Plan (and build) the tiled copy of one matrix in one precision for G CTAs
+// of nw compute warps and nv vectors per product, in dyn_max bytes of dynamic
+// shared memory laid out as [row sums of one tile | vector slice | S stages
+// of (metadata | col | val)].  The splits G = R x ncb that fit (rows per
+// block below 0xFFFF, stages of at least 16 KB) are ranked by estimated time
+// -- the partial sums written and read back, the vector slices copied, a
+// fixed cost per chunk -- and the first one whose slices all fit a stage is
+// built (a long row in a narrow split can need more than a stage; wider
+// splits shorten it).  Leaves L empty (ncb = 0) where no split works or,
+// unless forced, where the tiles would hold fewer than 4096 entries on
+// average.
+static void plan_tile(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
+                      const std::vector<double>& vx, int G, int nw, int esize, int nv, size_t dyn_max, bool force,
+                      CbLayout& L)
+{
+    constexpr int S = 2;
+    L = CbLayout();
+    L.esize = esize;
+    const long long nnz = rp[rows];
+    if (nw < 1 || G < 1 || rows < 1 || cols < 1 || (!force && nnz < 4096LL * G)) return;
+    const int E = 16 / esize;
+    struct Split {
+        int Cn, cw, acc_rows;
+        long long acc_bytes, slice_bytes, stage;
+        std::vector<int> rb;
+    };
+    auto split = [&](int Cn, Split& sp) {
+        const int R = G / Cn;
+        sp.Cn = Cn;
+        sp.cw = (int)((((long long)cols + Cn - 1) / Cn + 3) & ~3LL);
+        if (sp.cw > 65536 || (long long)(Cn - 1) * sp.cw >= cols || R > rows) return false;
+        sp.rb = cb_row_bounds(rows, rp, R);
+        sp.acc_rows = 0;
+        for (int r = 0; r < R; ++r) sp.acc_rows = std::max(sp.acc_rows, sp.rb[r + 1] - sp.rb[r]);
+        if (sp.acc_rows >= 0xFFFF) return false;
+        sp.acc_bytes = ((long long)sp.acc_rows * esize + 15) & ~15LL;
+        sp.slice_bytes = ((long long)(sp.cw + 2 * E) * esize + 15) & ~15LL;
+        sp.stage = ((long long)dyn_max - sp.acc_bytes - sp.slice_bytes) / S & ~15LL;
+        return sp.stage >= 16384;
+    };
+    std::vector<std::pair<double, int>> cand;
+    for (int Cn = 1; Cn <= G; ++Cn) {
+        Split sp;
+        if (G % Cn || !split(Cn, sp)) continue;
+        const double bytes = (double)nv * (2.0 * Cn * rows + (double)G * sp.cw) * esize;
+        const double chunks = std::ceil(1.15 * (double)nnz * (2 + esize) / G / (0.85 * sp.stage)) * nv;
+        cand.emplace_back(bytes / 6.8e12 + chunks * 0.3e-6, Cn);
+    }
+    std::sort(cand.begin(), cand.end());
+    for (const auto& cd : cand) {
+        Split sp;
+        split(cd.second, sp);
+        const int Cn = sp.Cn, R = G / Cn;
+        const int V = cb_pick_lanes(rp, ci, sp.rb, nw, Cn, sp.cw);
+        const int H = 32 / V;
+        // metadata share of a stage from the mean slice (sampled row blocks):
+        // 1 + H/2 words per slice against 32 x steps entries of 2 + esize bytes
+        long long nslices = 0, nsteps = 0;
+        {
+            CbBuckets bk;
+            std::vector<int> rows_k, steps;
+            const int stride = std::max(1, R / 8);
+            for (int r = 0; r < R; r += stride) {
+                const int Rr = sp.rb[r + 1] - sp.rb[r];
+                bk.build(sp.rb[r], Rr, Cn, sp.cw, rp, ci);
+                for (int k = 0; k < Cn; ++k) {
+                    bk.sorted_rows(k, Rr, rows_k);
+                    cb_slice_steps(bk, k, Rr, rows_k, V, steps);
+                    nslices += (long long)steps.size();
+                    for (int st : steps) nsteps += st;
+                }
+            }
+        }
+        const double per_slice_meta = 4.0 * (1 + H / 2.0);
+        const double per_slice_entries =
+            32.0 * (2 + esize) * std::max(1.0, (double)nsteps / std::max<long long>(nslices, 1));
+        const double frac = std::min(0.5, 1.3 * per_slice_meta / (per_slice_meta + per_slice_entries));
+        const int ms_cap = std::max(cb_meta_words(nw, 1, H) + 4, (int)(frac * sp.stage / 4) & ~3);
+        // entries: 2-byte offsets and esize-byte values, each region 16-byte aligned
+        const long long e_cap = ((sp.stage - 4LL * ms_cap - 32) / (2 + esize)) & ~31LL;
+        L = CbLayout();
+        L.esize = esize;
+        if (e_cap < 32 || !build_tile(cols, rp, ci, vx, sp.rb, Cn, sp.cw, nw, S, V, e_cap, ms_cap, L)) continue;
+        long long max_e = 0;
+        const size_t nch = L.meta.size() / (size_t)L.ms;
+        for (size_t j = 0; j < nch; ++j) max_e = std::max<long long>(max_e, L.meta[j * L.ms + 1] - L.meta[j * L.ms]);
+        L.rows = rows;
+        L.nv = nv;
+        L.acc_rows = sp.acc_rows;
+        L.off_x = (int)sp.acc_bytes;
+        L.stage_off = (int)(sp.acc_bytes + sp.slice_bytes);
+        L.off_col = (4 * L.ms + 15) & ~15;
+        L.off_val = L.off_col + (int)((2 * max_e + 15) & ~15LL);
+        L.stage_bytes = L.off_val + (int)((max_e * esize + 15) & ~15LL);
+        if ((long long)L.stage_bytes <= sp.stage) return;
+    }
+    L = CbLayout();
+}

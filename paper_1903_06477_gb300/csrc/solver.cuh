@@ -127,11 +127,19 @@ struct Cblk {
     int S;            // stages in the copy ring (2..CB_MAX_STAGES)
     int stage_off;    // byte offset of stage 0 in dynamic shared memory
     int stage_bytes;  // bytes per stage (multiple of 16)
-    int off_x, off_col, off_val;  // byte offsets inside a stage
+    int off_x, off_col, off_val;  // byte offsets inside a stage (tiles: off_x = the vector slice's offset
+                                  // in dynamic shared memory, after the tile's row sums)
     const int* rbnd;
     const int* meta;
     const unsigned short* col;
     const T* val;
+    // two-dimensional tiles (tile = 1; layout in cb_layout.h): R row blocks of
+    // rbnd, ncb column blocks, tile g = r * ncb + k on CTA g with chunks
+    // [cbeg[g], cbeg[g+1]) of meta; part holds two buffers of nv x ncb x rows
+    // partial sums
+    int tile, R, rows, nv;
+    const int* cbeg;
+    T* part;
 };
 
 // Sliced ELL with row sorting (SELL-H-sigma) and V lanes per row, H = 32 / V
@@ -620,6 +628,216 @@ __device__ void cb_spmv(const GridTeam& tm, const Cblk<T>& C, const T* x1, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// two-dimensional tiled product (grid team): y = M x (NV = 1) or M x1, M x2
+// ---------------------------------------------------------------------------
+
+// One chunk from its stage: compute warp w runs its slices against the
+// resident vector slice xs; each row's sum (reduced over its V lanes) is
+// final and is stored to the tile's row array at the start of dynamic shared
+// memory (every row of a tile lies in exactly one slice, so the stores never
+// meet).
+template <typename T>
+__device__ __forceinline__ void tile_chunk(int nw, int H, unsigned mt_off, unsigned xs_off, unsigned col_off,
+                                           unsigned val_off)
+{
+    extern __shared__ __align__(128) unsigned char cb_sm[];
+    const int* mt = (const int*)(cb_sm + mt_off);
+    const T* xs = (const T*)(cb_sm + xs_off);
+    const unsigned short* scol = (const unsigned short*)(cb_sm + col_off);
+    const T* sval = (const T*)(cb_sm + val_off);
+    T* acc = (T*)cb_sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ns = mt[4];
+    const int* wl = mt + 5;
+    const int* st = wl + nw + 1;
+    const unsigned short* sr = (const unsigned short*)(st + ns + 1);
+    const int s_hi = wl[w + 1];
+    for (int s = wl[w]; s < s_hi; ++s) {
+        const int t1 = st[s + 1];
+        int t = st[s];
+        T a0 = 0, a1 = 0;
+        if constexpr (sizeof(T) == 4) {
+            // four steps per trip, the tail predicated (offset 0, value 0)
+            T a2 = 0, a3 = 0;
+            for (; t < t1; t += 4) {
+                const bool o1 = t + 1 < t1, o2 = t + 2 < t1, o3 = t + 3 < t1;
+                const int c0 = scol[t * 32 + lane];
+                const int c1 = o1 ? (int)scol[t * 32 + 32 + lane] : 0;
+                const int c2 = o2 ? (int)scol[t * 32 + 64 + lane] : 0;
+                const int c3 = o3 ? (int)scol[t * 32 + 96 + lane] : 0;
+                const T v0 = sval[t * 32 + lane];
+                const T v1 = o1 ? sval[t * 32 + 32 + lane] : T(0);
+                const T v2 = o2 ? sval[t * 32 + 64 + lane] : T(0);
+                const T v3 = o3 ? sval[t * 32 + 96 + lane] : T(0);
+                a0 = fmaT(v0, xs[c0], a0);
+                a1 = fmaT(v1, xs[c1], a1);
+                a2 = fmaT(v2, xs[c2], a2);
+                a3 = fmaT(v3, xs[c3], a3);
+            }
+            a0 += a2;
+            a1 += a3;
+        } else {
+            for (; t + 2 <= t1; t += 2) {
+                const int c0 = scol[t * 32 + lane], c1 = scol[t * 32 + 32 + lane];
+                const T v0 = sval[t * 32 + lane], v1 = sval[t * 32 + 32 + lane];
+                a0 = fmaT(v0, xs[c0], a0);
+                a1 = fmaT(v1, xs[c1], a1);
+            }
+            if (t < t1) a0 = fmaT(sval[t * 32 + lane], xs[scol[t * 32 + lane]], a0);
+        }
+        T a = a0 + a1;
+        for (int o = H; o < 32; o <<= 1) a += __shfl_xor_sync(FULL_MASK, a, o);
+        if (lane < H) {
+            const int r = sr[s * H + lane];
+            if (r != 0xFFFF) acc[r] = a;
+        }
+    }
+}
+
+// This CTA's tile of M x: the vector slice is copied once (completing on
+// mbarrier 2 CB_MAX_STAGES, its uses counted in ph[CB_MAX_STAGES]), the
+// chunks stream through the ring of S stages as the column-blocked segments
+// do (full barriers tm.mbar[0..S-1], empty barriers tm.mbar[CB_MAX_STAGES +
+// s]), the row sums collect in shared memory and go to part[k][rows of the
+// block] at the end.  Returns false if a wait ran out of time (the abort
+// flag is then set and the copies still in flight are waited for, bounded,
+// before returning).
+template <typename T>
+__device__ bool tile_pass(const GridTeam& tm, const Cblk<T>& C, const T* x, T* part, unsigned long long pol)
+{
+    constexpr int E = 16 / (int)sizeof(T);
+    const int S = C.S, ncb = C.ncb, nw = C.nw, H = 32 / C.V, ms = C.ms, cw = C.cw, cols = C.cols, rows = C.rows;
+    const int off_col = C.off_col, off_val = C.off_val, stage_bytes = C.stage_bytes, off_x = C.off_x;
+    const int* meta = C.meta;
+    const unsigned short* gcol = C.col;
+    const T* gval = C.val;
+    unsigned char* const dsm = tm.dsm;
+    unsigned char* st0 = dsm + C.stage_off;
+    unsigned long long* mbar = tm.mbar;
+    unsigned* ph = tm.ph;
+    int* abort_flag = tm.abort_flag;
+    const int g = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (g >= C.R * ncb) return true;  // no tile on this CTA (uniform in the CTA)
+    const int r = g / ncb, k = g % ncb;
+    const int r0 = ro(C.rbnd + r), Rr = ro(C.rbnd + r + 1) - r0;
+    const int c0 = ro(C.cbeg + g), nch = ro(C.cbeg + g + 1) - c0;
+    const int mis = (int)(((uintptr_t)x & 15) / sizeof(T));
+    T* acc = (T*)dsm;
+    auto stage = [=](int s) { return st0 + (size_t)s * stage_bytes; };
+    auto full = [=](int s) { return smem_addr(&mbar[s]); };
+    auto empty = [=](int s) { return smem_addr(&mbar[CB_MAX_STAGES + s]); };
+    const unsigned xbar = smem_addr(&mbar[2 * CB_MAX_STAGES]);
+    __syncthreads();  // shared memory free (earlier users done), ph current
+    for (int i = threadIdx.x; i < Rr; i += blockDim.x) acc[i] = 0;
+    __syncthreads();  // the row sums are zero before any warp stores one
+    bool ok = true;
+    int issued = 0;
+    if (nch > 0) {
+        if (w == nw) {
+            // producer warp: lane 0 issues every copy
+            if (lane == 0) {
+                auto issue = [=](int j, int e0, int e1) {
+                    const int s = j % S;
+                    unsigned char* d = stage(s);
+                    const unsigned ne = (unsigned)(e1 - e0);
+                    const unsigned mb = (unsigned)ms * 4u;
+                    mbar_expect_tx(full(s), mb + ne * (2u + (unsigned)sizeof(T)));
+                    tma_load_1d_plain(smem_addr(d), meta + (size_t)(c0 + j) * ms, mb, full(s));
+                    if (ne) {
+                        tma_load_1d(smem_addr(d + off_col), gcol + e0, ne * 2u, full(s), pol);
+                        tma_load_1d(smem_addr(d + off_val), gval + e0, ne * (unsigned)sizeof(T), full(s), pol);
+                    }
+                };
+                // x was written by generic stores (other CTAs, before the last
+                // grid barrier) and is read here by the async proxy
+                fence_proxy_async_all();
+                const int len = min(cw, cols - k * cw);
+                const unsigned xb = (unsigned)((mis + len + E - 1) / E) * 16u;
+                mbar_expect_tx(xbar, xb);
+                tma_load_1d_plain(smem_addr(dsm + off_x), x + (size_t)k * cw - mis, xb, xbar);
+                const int npro = min(S, nch);
+                for (int j = 0; j < npro; ++j)
+                    issue(j, ro(meta + (size_t)(c0 + j) * ms), ro(meta + (size_t)(c0 + j) * ms + 1));
+                issued = npro;
+                for (int j = S; j < nch; ++j) {
+                    const int s = j % S;
+                    if (!mbar_wait(empty(s), (ph[s] + j / S - 1) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    // the stage's header names the chunk S after its own
+                    const int* h = (const int*)stage(s);
+                    const int ne0 = h[2], ne1 = h[3];
+                    fence_proxy_async();  // the stage was read through the generic proxy
+                    issue(j, ne0, ne1);
+                    issued = j + 1;
+                }
+            }
+        } else {
+            if (!mbar_wait(xbar, ph[CB_MAX_STAGES] & 1u, abort_flag)) ok = false;
+            for (int j = 0; ok && j < nch; ++j) {
+                const int s = j % S;
+                if (!mbar_wait(full(s), (ph[s] + j / S) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned so = (unsigned)(stage(s) - dsm);
+                tile_chunk<T>(nw, H, so, (unsigned)off_x + mis * (unsigned)sizeof(T), so + off_col, so + off_val);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty(s));
+            }
+        }
+    }
+    const bool all_ok = __syncthreads_and(ok);
+    if (!all_ok && w == nw && lane == 0 && nch > 0) {
+        // the slice copy and the copies of the last S issued chunks may still be in flight
+        mbar_wait(xbar, ph[CB_MAX_STAGES] & 1u, nullptr);
+        for (int j = max(0, issued - S); j < issued; ++j) mbar_wait(full(j % S), (ph[j % S] + j / S) & 1u, nullptr);
+    }
+    __syncthreads();  // everyone has read ph for this pass
+    if (threadIdx.x == 0 && nch > 0) {
+        for (int s = 0; s < S; ++s) ph[s] += (unsigned)((nch - s + S - 1) / S);
+        ph[CB_MAX_STAGES] += 1u;
+    }
+    if (!all_ok) return false;
+    T* out = part + (size_t)k * rows + r0;
+    for (int i = threadIdx.x; i < Rr; i += blockDim.x) out[i] = acc[i];
+    return true;
+}
+
+// The tiled product: one tile pass per vector into its partial sums, a grid
+// barrier, then epi(row, sum) (or epi(row, sum1, sum2)) for every row, the
+// sum over the column blocks taken in block order (deterministic), rows dealt
+// like the team's vector loops.  The partial sums alternate between two
+// buffers by the parity of the barrier count at entry: the next product of
+// this matrix either starts one barrier later (the other buffer) or after a
+// barrier that every CTA reaches only once it has read this one.
+template <typename T, int NV, class Epi>
+__device__ void tile_spmv(GridTeam& tm, const Cblk<T>& C, const T* x1, const T* x2, Epi& epi)
+{
+    const unsigned long long pol = evict_first_policy();
+    const int rows = C.rows, ncb = C.ncb;
+    T* part = C.part + (size_t)(tm.epoch & 1ull) * C.nv * ncb * rows;
+    if (!tile_pass<T>(tm, C, x1, part, pol)) return;
+    if constexpr (NV == 2) {
+        if (!tile_pass<T>(tm, C, x2, part + (size_t)ncb * rows, pol)) return;
+    }
+    tm.sync();
+    for (int i = tm.rank(); i < rows; i += tm.size()) {
+        T s1 = 0;
+        for (int k = 0; k < ncb; ++k) s1 += part[(size_t)k * rows + i];
+        if constexpr (NV == 1) {
+            epi(i, s1);
+        } else {
+            T s2 = 0;
+            for (int k = 0; k < ncb; ++k) s2 += part[(size_t)(ncb + k) * rows + i];
+            epi(i, s1, s2);
+        }
+    }
+}
+
 template <typename T, class Team, class XF, class Epi>
 __device__ __forceinline__ void spmv_f(const Team& tm, const Sell<T>& S, XF xf, Epi epi)
 {
@@ -630,11 +848,14 @@ __device__ __forceinline__ void spmv_f(const Team& tm, const Sell<T>& S, XF xf, 
 }
 
 template <typename T, class Team, class Epi>
-__device__ __forceinline__ void spmv(const Team& tm, const Sell<T>& S, const T* x, Epi epi)
+__device__ __forceinline__ void spmv(Team& tm, const Sell<T>& S, const T* x, Epi epi)
 {
     if constexpr (Team::kGrid) {
         if (S.cb.ncb > 0) {
-            cb_spmv<T, 1>(tm, S.cb, x, x, epi);
+            if (S.cb.tile)
+                tile_spmv<T, 1>(tm, S.cb, x, x, epi);
+            else
+                cb_spmv<T, 1>(tm, S.cb, x, x, epi);
             return;
         }
     }
@@ -643,11 +864,14 @@ __device__ __forceinline__ void spmv(const Team& tm, const Sell<T>& S, const T* 
 }
 
 template <typename T, class Team, class Epi>
-__device__ __forceinline__ void spmv2(const Team& tm, const Sell<T>& S, const T* x1, const T* x2, Epi epi)
+__device__ __forceinline__ void spmv2(Team& tm, const Sell<T>& S, const T* x1, const T* x2, Epi epi)
 {
     if constexpr (Team::kGrid) {
         if (S.cb.ncb > 0) {
-            cb_spmv<T, 2>(tm, S.cb, x1, x2, epi);
+            if (S.cb.tile)
+                tile_spmv<T, 2>(tm, S.cb, x1, x2, epi);
+            else
+                cb_spmv<T, 2>(tm, S.cb, x1, x2, epi);
             return;
         }
     }

@@ -252,6 +252,121 @@ extern "C" int scs_cb_layout_check(int32_t rows, int32_t cols, const int64_t* Ap
     return SCS_OK;
 }
 
+// Host-side check of the tiled layout (see superscs.h): build it, verify its
+// invariants and replay the product as the tile passes (row sums per tile)
+// and the second pass (partials added in block order) compute it, in FP64.
+extern "C" int scs_tile_layout_check(int32_t rows, int32_t cols, const int64_t* Ap, const int32_t* Ai,
+                                     const double* Ax, int32_t ctas, int32_t compute_warps, int32_t elem_bytes,
+                                     int32_t vectors, int64_t smem_bytes, const double* x, double* y, int64_t* stats)
+{
+    if (rows <= 0 || cols <= 0 || !Ap || !Ai || !Ax || !x || !y || !stats || ctas < 1 || compute_warps < 1 ||
+        (elem_bytes != 4 && elem_bytes != 8) || (vectors != 1 && vectors != 2) || smem_bytes < 4096)
+        return SCS_EINVAL;
+    if (Ap[0] != 0 || Ap[rows] >= (1ll << 31)) return SCS_EINVAL;
+    std::vector<int> rp(rows + 1), ci(Ap[rows]);
+    std::vector<double> vx(Ax, Ax + Ap[rows]);
+    for (int i = 0; i <= rows; ++i) rp[i] = (int)Ap[i];
+    for (long long e = 0; e < Ap[rows]; ++e) {
+        if (Ai[e] < 0 || Ai[e] >= cols) return SCS_EINVAL;
+        ci[e] = Ai[e];
+    }
+    HostProb::Cb C;
+    plan_tile(rows, cols, rp, ci, vx, ctas, compute_warps, elem_bytes, vectors, (size_t)smem_bytes, true, C);
+    for (int k = 0; k < 8; ++k) stats[k] = 0;
+    if (C.ncb == 0) return SCS_OK;  // no split fits: the solver would use another layout
+    long long bad = 0;
+    auto req = [&](bool c) { if (!c) ++bad; };
+    const int E = 16 / elem_bytes, H = 32 / C.V, S = C.S, nw = compute_warps, Cn = C.ncb, R = C.R;
+    req(C.tile == 1 && R * Cn <= ctas && R >= 1 && C.rows == rows && C.nv == vectors);
+    req(C.part_elems() == (size_t)2 * vectors * Cn * rows);
+    req(C.cw % 4 == 0 && C.cw <= 65536 && (long long)Cn * C.cw >= cols && (long long)(Cn - 1) * C.cw < cols);
+    req(C.dyn() <= (size_t)smem_bytes);
+    req(C.off_x % 16 == 0 && C.off_x >= C.acc_rows * elem_bytes && C.stage_off % 16 == 0);
+    req((long long)C.stage_off - C.off_x >= (long long)((C.cw + 2 * E - 1) / E) * 16);
+    req(C.ms % 4 == 0 && C.stage_bytes % 16 == 0 && C.off_col % 16 == 0 && C.off_val % 16 == 0);
+    req(C.off_col >= 4 * C.ms && C.off_val >= C.off_col && C.stage_bytes >= C.off_val);
+    req((int)C.rbnd.size() == R + 1 && C.rbnd[0] == 0 && C.rbnd[R] == rows);
+    req((int)C.cbeg.size() == R * Cn + 1 && C.cbeg[0] == 0 && (size_t)C.cbeg[R * Cn] * C.ms == C.meta.size());
+    // part[k][row], as the tile passes leave it (rows a tile does not reach stay 0)
+    std::vector<double> part((size_t)Cn * rows, 0.0);
+    long long prev_end = 0;
+    std::vector<double> acc;
+    std::vector<char> seen;
+    for (int r = 0; r < R; ++r) {
+        const int r0 = C.rbnd[r], Rr = C.rbnd[r + 1] - r0;
+        req(Rr >= 0 && Rr <= C.acc_rows && Rr < 0xFFFF);
+        for (int k = 0; k < Cn; ++k) {
+            const int g = r * Cn + k;
+            const int len = std::min(C.cw, cols - k * C.cw);
+            acc.assign(std::max(Rr, 1), 0.0);
+            seen.assign(std::max(Rr, 1), 0);
+            req(C.cbeg[g + 1] >= C.cbeg[g]);
+            for (int j = C.cbeg[g]; j < C.cbeg[g + 1]; ++j) {
+                const int* mt = C.meta.data() + (size_t)j * C.ms;
+                const int e0 = mt[0], e1 = mt[1], ns = mt[4];
+                req(e0 == prev_end && e1 >= e0 && e0 % 32 == 0 && e1 % 32 == 0);
+                req((long long)(e1 - e0) * 2 <= C.off_val - C.off_col &&
+                    (long long)(e1 - e0) * elem_bytes <= C.stage_bytes - C.off_val);
+                if (j + S < C.cbeg[g + 1]) {
+                    const int* m2 = C.meta.data() + (size_t)(j + S) * C.ms;
+                    req(mt[2] == m2[0] && mt[3] == m2[1]);
+                }
+                req(cb_meta_words(nw, ns, H) <= C.ms);
+                prev_end = e1;
+                const int* wl = mt + 5;
+                const int* st = wl + nw + 1;
+                const uint16_t* sr = (const uint16_t*)(st + ns + 1);
+                req(wl[0] == 0 && wl[nw] == ns && st[0] == 0 && (long long)st[ns] * 32 == e1 - e0);
+                for (int w = 0; w < nw; ++w) {
+                    req(wl[w] <= wl[w + 1]);
+                    for (int sl = wl[w]; sl < wl[w + 1]; ++sl) {
+                        req(st[sl + 1] > st[sl]);
+                        double a[32] = {};
+                        for (int t = st[sl]; t < st[sl + 1]; ++t)
+                            for (int lane = 0; lane < 32; ++lane) {
+                                const size_t idx = (size_t)e0 + 32 * (size_t)t + lane;
+                                const int c = C.col[idx];
+                                req(c < len);
+                                a[lane] += C.val[idx] * x[(size_t)k * C.cw + std::min(c, len - 1)];
+                            }
+                        for (int rr = 0; rr < H; ++rr) {
+                            double sum = 0;
+                            for (int q = 0; q < C.V; ++q) sum += a[q * H + rr];
+                            const int rw = sr[sl * H + rr];
+                            if (rw == 0xFFFF) {
+                                req(sum == 0.0);
+                                continue;
+                            }
+                            // every row of a tile lies in one slice: its sum is stored, not added
+                            req(rw < Rr && !seen[rw]);
+                            if (rw < Rr) {
+                                seen[rw] = 1;
+                                acc[rw] = sum;
+                            }
+                        }
+                    }
+                }
+            }
+            for (int lr = 0; lr < Rr; ++lr) part[(size_t)k * rows + r0 + lr] = acc[lr];
+        }
+    }
+    req(prev_end == (long long)C.col.size());
+    for (int i = 0; i < rows; ++i) {
+        double s = 0;
+        for (int k = 0; k < Cn; ++k) s += part[(size_t)k * rows + i];
+        y[i] = s;
+    }
+    stats[0] = bad;
+    stats[1] = Cn;
+    stats[2] = R;
+    stats[3] = C.V;
+    stats[4] = (int64_t)C.col.size();
+    stats[5] = (int64_t)C.dyn();
+    stats[6] = C.cbeg[R * Cn];
+    stats[7] = C.ms;
+    return SCS_OK;
+}
+
 static int pick_lanes(long long nnz, int rows)
 {
     const double avg = rows > 0 ? (double)nnz / rows : 0.0;
@@ -393,6 +508,7 @@ static int check_settings(const scs_settings* S, char* err)
     if (S->precision != SCS_FP64 && S->precision != SCS_MIXED) { set_err(err, "bad precision"); return SCS_EINVAL; }
     if (S->threads != 0 && (S->threads < 32 || S->threads > 1024 || S->threads % 32)) { set_err(err, "threads must be a multiple of 32 in 32..1024"); return SCS_EINVAL; }
     if (!(S->psd_recheck_tol >= 0)) { set_err(err, "psd_recheck_tol must be >= 0"); return SCS_EINVAL; }
+    if (S->spmv_path < 0 || S->spmv_path > 4) { set_err(err, "spmv_path must be in 0..4"); return SCS_EINVAL; }
     return SCS_OK;
 }
 
@@ -457,6 +573,12 @@ static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, bool direct, 
         dc.meta = A.take<int>(hc.meta.size());
         dc.col = A.take<unsigned short>(hc.col.size());
         dc.val = A.take<T>(hc.val.size());
+        dc.tile = hc.tile;
+        dc.R = hc.R;
+        dc.rows = hc.rows;
+        dc.nv = hc.nv;
+        dc.cbeg = hc.tile ? A.take<int>(hc.cbeg.size()) : nullptr;
+        dc.part = hc.tile ? A.take<T>(hc.part_elems()) : nullptr;
     };
     lay_cb(sizeof(T) == 8 ? H.cA64 : H.cA32, P.A.cb);
     lay_cb(sizeof(T) == 8 ? H.cAT64 : H.cAT32, P.AT.cb);
@@ -575,7 +697,7 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         if (hc.ncb == 0) return SCS_OK;
         int r;
         if ((r = put_i(hc.rbnd, dc.rbnd)) || (r = put_i(hc.meta, dc.meta)) || (r = put_u16(hc.col, dc.col)) ||
-            (r = put_t(hc.val, dc.val)))
+            (r = put_t(hc.val, dc.val)) || (hc.tile && (r = put_i(hc.cbeg, dc.cbeg))))
             return r;
         return SCS_OK;
     };
@@ -816,7 +938,7 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     // column-blocked products for the grid team (one CTA per SM): built here,
     // where the grid and the block size are known
     bool cb = false;
-    if (team == SCS_TEAM_GRID && (settings->spmv_path == 0 || settings->spmv_path == 3)) {
+    if (team == SCS_TEAM_GRID && (settings->spmv_path == 0 || settings->spmv_path >= 3)) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa64{}, fa32{};
@@ -826,14 +948,25 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
         if ((size_t)optin > stat + 2048) {
             const size_t dyn_max = ((size_t)optin - stat - 1024) & ~size_t(15);
             const int G = w->D.sms, nw = w->D.threads / 32 - 1;  // compute warps; the last warp copies
-            const bool force = settings->spmv_path == 3;
+            const bool force = settings->spmv_path >= 3;
+            const bool tiles = settings->spmv_path == 0 || settings->spmv_path == 4;
+            const bool force_tiles = settings->spmv_path == 4;
             HostProb& Hm = w->H;
+            // tiles where a split fits, else the column-blocked layout (each on its own host thread)
+            auto plan = [&](bool transposed, int esize, int nv, HostProb::Cb& L) {
+                const int rows = transposed ? Hm.n : Hm.m, cols = transposed ? Hm.m : Hm.n;
+                const auto& rp = transposed ? Hm.Tp : Hm.Ap;
+                const auto& ci = transposed ? Hm.Ti : Hm.Ai;
+                const auto& vx = transposed ? Hm.Tx : Hm.Ax;
+                if (tiles) plan_tile(rows, cols, rp, ci, vx, G, nw, esize, nv, dyn_max, force_tiles, L);
+                if (L.ncb == 0) plan_cb(rows, cols, rp, ci, vx, G, nw, esize, nv, dyn_max, force, L);
+            };
             std::vector<std::thread> th;
-            th.emplace_back([&] { plan_cb(Hm.m, Hm.n, Hm.Ap, Hm.Ai, Hm.Ax, G, nw, 8, 1, dyn_max, force, Hm.cA64); });
-            th.emplace_back([&] { plan_cb(Hm.n, Hm.m, Hm.Tp, Hm.Ti, Hm.Tx, G, nw, 8, 2, dyn_max, force, Hm.cAT64); });
+            th.emplace_back([&] { plan(false, 8, 1, Hm.cA64); });
+            th.emplace_back([&] { plan(true, 8, 2, Hm.cAT64); });
             if (w->has32) {
-                th.emplace_back([&] { plan_cb(Hm.m, Hm.n, Hm.Ap, Hm.Ai, Hm.Ax, G, nw, 4, 1, dyn_max, force, Hm.cA32); });
-                th.emplace_back([&] { plan_cb(Hm.n, Hm.m, Hm.Tp, Hm.Ti, Hm.Tx, G, nw, 4, 2, dyn_max, force, Hm.cAT32); });
+                th.emplace_back([&] { plan(false, 4, 1, Hm.cA32); });
+                th.emplace_back([&] { plan(true, 4, 2, Hm.cAT32); });
             }
             for (auto& t : th) t.join();
             cb = H.cA64.ncb || H.cAT64.ncb || H.cA32.ncb || H.cAT32.ncb;

@@ -9,6 +9,9 @@ the bulk precision (the two extra roundings are those of a_ij and x_j to
 FP32; in FP64 they are exact).  spmv_path 3 forces the layout on problems
 too small for the automatic rule, so several column blocks, rows ranges
 with no rows, skewed row lengths and vectors at odd offsets are all covered.
+spmv_path 4 does the same for the two-dimensional tiles, whose sums add the
+column blocks' partials in a second pass (k + ncb terms: the bound's k is
+raised by the number of column blocks, at most 152).
 """
 import numpy as np
 import pytest
@@ -63,7 +66,7 @@ def _problems():
 PROBS = _problems()
 
 
-def _check_products(work, prob, precision, u, seed):
+def _check_products(work, prob, precision, u, seed, extra=0):
     A = prob["A"].tocsr()
     AT = A.T.tocsr()
     rng = np.random.default_rng(seed)
@@ -74,30 +77,34 @@ def _check_products(work, prob, precision, u, seed):
     kT = int(np.diff(AT.indptr).max(initial=0))
     absA, absT = abs(A), abs(AT)
     out = work.spmv(x, op=0, precision=precision)
-    bound = _gamma(kA + 2, u) * (absA @ np.abs(x)) + 1e-300
+    bound = _gamma(kA + 2 + extra, u) * (absA @ np.abs(x)) + 1e-300
     assert np.all(np.abs(out - A @ x) <= bound)
     out = work.spmv(y, op=1, precision=precision)
-    bound = _gamma(kT + 2, u) * (absT @ np.abs(y)) + 1e-300
+    bound = _gamma(kT + 2 + extra, u) * (absT @ np.abs(y)) + 1e-300
     assert np.all(np.abs(out - AT @ y) <= bound)
     o1, o2 = work.spmv(y, op=2, precision=precision, v2=y2)
     assert np.all(np.abs(o1 - AT @ y) <= bound)
-    bound2 = _gamma(kT + 2, u) * (absT @ np.abs(y2)) + 1e-300
+    bound2 = _gamma(kT + 2 + extra, u) * (absT @ np.abs(y2)) + 1e-300
     assert np.all(np.abs(o2 - AT @ y2) <= bound2)
 
 
 @pytest.mark.parametrize("name", list(PROBS))
-@pytest.mark.parametrize("path", [3, 1, 2])  # column-blocked, sliced ELL, sliced ELL with a TMA-staged stream
+@pytest.mark.parametrize("path", [4, 3, 1, 2])  # tiles, column-blocked, sliced ELL, sliced ELL with a TMA-staged stream
 def test_products_match_definition(name, path):
     prob = PROBS[name]
     work = B.Work(prob, team=B.TEAM_GRID, precision=B.MIXED, spmv_path=path)
-    _check_products(work, prob, B.FP64, U64, seed=1)
-    _check_products(work, prob, B.MIXED, U32, seed=2)
+    extra = 152 if path == 4 else 0  # the partials of at most 152 column blocks
+    _check_products(work, prob, B.FP64, U64, seed=1, extra=extra)
+    _check_products(work, prob, B.MIXED, U32, seed=2, extra=extra)
+    # a second product right after the first (partial-sum buffers alternate)
+    _check_products(work, prob, B.MIXED, U32, seed=3, extra=extra)
 
 
+@pytest.mark.parametrize("path", [4, 3])
 @pytest.mark.parametrize("name", ["multi_block", "skewed"])
-def test_column_blocked_linsys_and_T_match_oracle(name):
+def test_column_blocked_linsys_and_T_match_oracle(name, path):
     prob = PROBS[name]
-    work = B.Work(prob, team=B.TEAM_GRID, spmv_path=3, cg_rtol=1e-14, cg_max=5000)
+    work = B.Work(prob, team=B.TEAM_GRID, spmv_path=path, cg_rtol=1e-14, cg_max=5000)
     orc = O.Oracle(prob, cg_rtol=1e-14, cg_max=5000)
     rng = np.random.default_rng(3)
     r = rng.standard_normal(work.N) * 3
@@ -111,11 +118,12 @@ def test_column_blocked_linsys_and_T_match_oracle(name):
     np.testing.assert_allclose(Ru, Rr, rtol=0, atol=1e-9 * (1 + np.abs(Tr).max()))
 
 
+@pytest.mark.parametrize("path", [4, 3])
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
-def test_column_blocked_solve_reaches_planted_optimum(precision):
+def test_column_blocked_solve_reaches_planted_optimum(precision, path):
     prob = PROBS["multi_block"]
     eps = 1e-6
-    kw = dict(team=B.TEAM_GRID, spmv_path=3, precision=precision, eps=eps, max_iters=20000, cg_adapt=1e-2)
+    kw = dict(team=B.TEAM_GRID, spmv_path=path, precision=precision, eps=eps, max_iters=20000, cg_adapt=1e-2)
     work = B.Work(prob, **kw)
     x, y, s, info = work.solve()
     assert info["status"] == B.SOLVED, info
