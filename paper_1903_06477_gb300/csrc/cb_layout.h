@@ -512,11 +512,13 @@ static bool build_tile(int cols, const std::vector<int>& rp, const std::vector<i
 // splits shorten it).  Leaves L empty (ncb = 0) where no split works or,
 // unless forced, where the tiles would hold fewer than 4096 entries on
 // average.
+constexpr int TILE_STAGES = 2;  // stages of the tiles' copy ring
+
 static void plan_tile(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
                       const std::vector<double>& vx, int G, int nw, int esize, int nv, size_t dyn_max, bool force,
                       CbLayout& L)
 {
-    constexpr int S = 2;
+    constexpr int S = TILE_STAGES;
     L = CbLayout();
     L.esize = esize;
     const long long nnz = rp[rows];
