@@ -116,16 +116,17 @@ typedef struct {
     double mixed_switch;    /* FP32 phase hands over to FP64 once max(pr,dr,gap) <= this (SCS_MIXED) */
     double cg_adapt;        /* > 0: inside the loop CG also stops at ||res|| <= cg_adapt ||Ru||
                                (not in the paper; 0 keeps the fixed relative tolerance) */
-    int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- two-dimensional tiles
-                               (one row block x column block per CTA, the vector's column block
-                               resident in shared memory, partial sums added by a second pass) where
-                               a split fits shared memory and the tiles hold at least 4096 entries
-                               on average, else the column-blocked layout (each CTA's rows against
-                               every column block, vector slices staged per block) where each (CTA,
+    int32_t spmv_path;      /* sparse products of the grid team.  0: automatic -- the column-blocked
+                               layout (each CTA's rows against every column block, vector slices
+                               staged in shared memory per block, one CTA per SM) where each (CTA,
                                column block) holds at least 1024 entries on average, else sliced
                                ELL; 1: sliced ELL, direct streaming loads; 2: sliced ELL, TMA-staged
                                stream; 3: column-blocked wherever the layout fits shared memory;
-                               4: tiles wherever a split fits, else as 3.
+                               4: two-dimensional tiles (one row block x column block per CTA, the
+                               vector's column block resident in shared memory, partial sums added
+                               by a second pass) wherever a split fits, else as 3.  The tiles
+                               measured 10-15% slower than the column-blocked layout on the 1e7-
+                               nonzero benchmark matrix, so the automatic rule does not take them.
                                The block team always uses sliced ELL. */
     int32_t warm_fallback;  /* > 0: a warm start whose ||Ru|| is not below the cold start's ||Ru0||
                                after this many iterations is abandoned for the cold start */
@@ -145,9 +146,12 @@ typedef struct {
                                factor takes n^2 words per precision.  0 (default): CG.  Ignored by
                                the grid team.  A non-positive pivot makes setup fail with SCS_EINVAL */
     int32_t mixed_stall_after_tau; /* SCS_MIXED, 1 (default): while the FP32 phase's termination test
-                               sees tau_ = 0 its stall window is 5 mixed_stall iterations -- the
-                               residuals of Sec. 4.3 are undefined then and ||Ru|| may plateau while
-                               the iterate turns away from the tau axis; 0: mixed_stall throughout */
+                               sees tau_ = 0, or max(pr, dr, gap) above 100 mixed_switch, its stall
+                               window is 5 mixed_stall iterations -- the residuals of Sec. 4.3 are
+                               undefined with tau_ = 0 and ||Ru|| may plateau while the iterate turns
+                               away from the tau axis, and a plateau that far above the hand-over
+                               level is a pause of Algorithm 1, not the FP32 floor; 0: mixed_stall
+                               throughout */
     double psd_recheck_tol; /* SCS_MIXED with PSD cones: every FP32 eigendecomposition of a PSD block
                                (Sec. 2, cone (ii)) is checked in FP64, ||X V - V L||_F / ||X||_F; a
                                block above this bound is decomposed again in FP64 and projected from

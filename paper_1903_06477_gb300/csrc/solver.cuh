@@ -2588,8 +2588,13 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
                 // its best value for stall_iters iterations (the FP32 floor).  While
                 // tau_ = 0 the residuals of Sec. 4.3 are undefined and the iterate is
                 // still turning away from the tau axis, where ||Ru|| can plateau
-                // without any floor being reached: the window is then five times longer.
-                const int window = (S.stall_after_tau && !isfinite(to.pr)) ? 5 * S.stall_iters : S.stall_iters;
+                // without any floor being reached; a plateau with max(pr, dr, gap) still
+                // above 100 times the hand-over level is not the FP32 floor either (the
+                // FP32 phases measured here level off within a few times of it).  In
+                // both cases the window is five times longer.
+                const double kkt = fmax(to.pr, fmax(to.dr, to.gap));
+                const bool far = !isfinite(to.pr) || (S.switch_kkt > 0.0 && kkt > 100.0 * S.switch_kkt);
+                const int window = (S.stall_after_tau && far) ? 5 * S.stall_iters : S.stall_iters;
                 if (nRu < 0.9 * best_kkt) {
                     best_kkt = nRu;
                     best_it = nu;

@@ -949,16 +949,15 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
             const size_t dyn_max = ((size_t)optin - stat - 1024) & ~size_t(15);
             const int G = w->D.sms, nw = w->D.threads / 32 - 1;  // compute warps; the last warp copies
             const bool force = settings->spmv_path >= 3;
-            const bool tiles = settings->spmv_path == 0 || settings->spmv_path == 4;
-            const bool force_tiles = settings->spmv_path == 4;
+            const bool tiles = settings->spmv_path == 4;
             HostProb& Hm = w->H;
-            // tiles where a split fits, else the column-blocked layout (each on its own host thread)
+            // tiles on request where a split fits, else the column-blocked layout (each on its own host thread)
             auto plan = [&](bool transposed, int esize, int nv, HostProb::Cb& L) {
                 const int rows = transposed ? Hm.n : Hm.m, cols = transposed ? Hm.m : Hm.n;
                 const auto& rp = transposed ? Hm.Tp : Hm.Ap;
                 const auto& ci = transposed ? Hm.Ti : Hm.Ai;
                 const auto& vx = transposed ? Hm.Tx : Hm.Ax;
-                if (tiles) plan_tile(rows, cols, rp, ci, vx, G, nw, esize, nv, dyn_max, force_tiles, L);
+                if (tiles) plan_tile(rows, cols, rp, ci, vx, G, nw, esize, nv, dyn_max, true, L);
                 if (L.ncb == 0) plan_cb(rows, cols, rp, ci, vx, G, nw, esize, nv, dyn_max, force, L);
             };
             std::vector<std::thread> th;

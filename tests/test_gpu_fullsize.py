@@ -64,7 +64,7 @@ def test_c2_full_bench_solve(c2):
     """The benchmark's configuration: AA(10), eps 1e-6, FP32 phase with FP64
     refinement, adaptive CG tolerance."""
     eps = 1e-6
-    kw = dict(direction=0, mem=10, eps=eps, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5)
+    kw = dict(direction=0, mem=10, eps=eps, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=3e-5)
     work = B.Work(c2, precision=B.MIXED, **kw)
     x, y, s, info = work.solve()
     assert info["status"] == B.SOLVED, info
