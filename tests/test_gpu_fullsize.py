@@ -103,11 +103,13 @@ def test_c3_full_bench_solve(c3):
 
 def test_c4_full_batch():
     """4096 portfolio SOCPs (k ~ U{20..400}) in one persistent launch per
-    phase, FP32 bulk with FP64 refinement, eps 1e-5: every instance solved
+    phase, FP32 bulk with FP64 refinement, linear systems by the dense
+    Cholesky factor (the benchmark's form), eps 1e-5: every instance solved
     with its KKT residuals at eps; a sample against the oracle's solve."""
     probs = W.c4_portfolios(4096)
     eps = 1e-5
-    kw = dict(direction=0, mem=10, eps=eps, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5)
+    kw = dict(direction=0, mem=10, eps=eps, max_iters=20000, cg_rtol=1e-10, cg_adapt=1e-2, mixed_switch=1e-5,
+              linsys_direct=1)
     batch = B.Batch(probs, precision=B.MIXED, **kw)
     xs, ys, ss, infos = batch.solve()
     for p, x, y, s, info in zip(probs, xs, ys, ss, infos):
