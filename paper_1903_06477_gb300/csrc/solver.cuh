@@ -246,6 +246,18 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 // turn; xf(c) supplies the gathered vector entry, epi(row, sum) consumes the
 // row result (only lanes q = 0 call it)
 // ---------------------------------------------------------------------------
+// Matrix entries of the sliced-ELL products: the grid team streams its large
+// matrices past L1 (evict-first in L2); the block team's instance is small and
+// re-read by every product of its solve, so its entries are cached in L1.
+template <bool Stream, typename V>
+__device__ __forceinline__ V ldm(const V* p, unsigned long long pol)
+{
+    if constexpr (Stream)
+        return ld_stream(p, pol);
+    else
+        return ro(p);
+}
+
 template <typename T, class Team, class XF, class Epi>
 __device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf, Epi& epi)
 {
@@ -261,17 +273,17 @@ __device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf,
         T a0 = 0, a1 = 0;
         int t = 0;
         for (; t + 4 <= tc; t += 4) {
-            const int c0 = ld_stream(cp + 32 * t, pol), c1 = ld_stream(cp + 32 * (t + 1), pol),
-                      c2 = ld_stream(cp + 32 * (t + 2), pol), c3 = ld_stream(cp + 32 * (t + 3), pol);
-            const T v0 = ld_stream(vp + 32 * t, pol), v1 = ld_stream(vp + 32 * (t + 1), pol),
-                    v2 = ld_stream(vp + 32 * (t + 2), pol), v3 = ld_stream(vp + 32 * (t + 3), pol);
+            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol), c1 = ldm<Team::kGrid>(cp + 32 * (t + 1), pol),
+                      c2 = ldm<Team::kGrid>(cp + 32 * (t + 2), pol), c3 = ldm<Team::kGrid>(cp + 32 * (t + 3), pol);
+            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol), v1 = ldm<Team::kGrid>(vp + 32 * (t + 1), pol),
+                    v2 = ldm<Team::kGrid>(vp + 32 * (t + 2), pol), v3 = ldm<Team::kGrid>(vp + 32 * (t + 3), pol);
             const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
             a0 = fmaT(v0, x0, a0);
             a1 = fmaT(v1, x1, a1);
             a0 = fmaT(v2, x2, a0);
             a1 = fmaT(v3, x3, a1);
         }
-        for (; t < tc; ++t) a0 += ld_stream(vp + 32 * t, pol) * xf(ld_stream(cp + 32 * t, pol));
+        for (; t < tc; ++t) a0 += ldm<Team::kGrid>(vp + 32 * t, pol) * xf(ldm<Team::kGrid>(cp + 32 * t, pol));
         T acc = a0 + a1;
         for (int o = H; o < 32; o <<= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
         const int pos = s * H + lane;
@@ -294,16 +306,16 @@ __device__ __forceinline__ void sell2_v(const Team& tm, const Sell<T>& S, XF1& x
         T a1 = 0, a2 = 0, b1 = 0, b2 = 0;
         int t = 0;
         for (; t + 2 <= tc; t += 2) {
-            const int c0 = ld_stream(cp + 32 * t, pol), c1 = ld_stream(cp + 32 * (t + 1), pol);
-            const T v0 = ld_stream(vp + 32 * t, pol), v1 = ld_stream(vp + 32 * (t + 1), pol);
+            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol), c1 = ldm<Team::kGrid>(cp + 32 * (t + 1), pol);
+            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol), v1 = ldm<Team::kGrid>(vp + 32 * (t + 1), pol);
             a1 += v0 * xf1(c0);
             a2 += v0 * xf2(c0);
             b1 += v1 * xf1(c1);
             b2 += v1 * xf2(c1);
         }
         if (t < tc) {
-            const int c0 = ld_stream(cp + 32 * t, pol);
-            const T v0 = ld_stream(vp + 32 * t, pol);
+            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol);
+            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol);
             a1 += v0 * xf1(c0);
             a2 += v0 * xf2(c0);
         }
