@@ -767,8 +767,6 @@ def main():
     ap.add_argument("--mixed-resume", type=int, default=None, help="1: the FP64 phase continues the FP32 loop state")
     ap.add_argument("--stall-after-tau", type=int, default=None,
                     help="1: the FP32 phase's stall count starts once tau_ > 0")
-    ap.add_argument("--block-smem", type=int, default=None,
-                    help="1: a block-team instance keeps its vectors in shared memory while it runs")
     ap.add_argument("--spmv-path", type=int, default=None,
                     help="grid-team sparse products: 0 automatic, 1/2 sliced ELL, 3 column-blocked, 4 tiles")
     ap.add_argument("--linsys-direct", type=int, default=None,
@@ -845,8 +843,6 @@ def main():
         kw["mixed_refine"] = args.mixed_refine
     if args.spmv_path is not None:
         kw["spmv_path"] = args.spmv_path
-    if args.block_smem is not None:
-        kw["block_smem"] = args.block_smem
     for key in ("cg_adapt", "mixed_switch", "mixed_stall", "mixed_resume", "mixed_refine", "linsys_direct",
                 "spmv_path"):
         if key in kw:

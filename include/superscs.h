@@ -157,12 +157,6 @@ typedef struct {
                                block above this bound is decomposed again in FP64 and projected from
                                that.  Default 1e-4, ten times the largest residual of converged FP32
                                Jacobi sweeps on order-64 blocks; 0 redoes every block; must be >= 0 */
-    int32_t block_smem;     /* 1 (default): a single instance run by one thread block (the block team)
-                               keeps the vectors Algorithm 1 sweeps -- the HSDE vectors, g, the CG
-                               vectors, the direction memory -- in shared memory while each launch
-                               runs (copied in at its start and out at its end) where they fit next
-                               to the other shared-memory users; 0: they stay in global memory.
-                               Batches always keep them in global memory. */
 } scs_settings;
 
 typedef struct {

@@ -45,7 +45,6 @@ class Settings(C.Structure):
         ("mixed_switch", C.c_double), ("cg_adapt", C.c_double), ("spmv_path", C.c_int32),
         ("warm_fallback", C.c_int32), ("mixed_resume", C.c_int32), ("mixed_refine", C.c_int32),
         ("linsys_direct", C.c_int32), ("mixed_stall_after_tau", C.c_int32), ("psd_recheck_tol", C.c_double),
-        ("block_smem", C.c_int32),
     ]
 
 

@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int
 {
     __shared__ SmemFixed sf;
     __shared__ int sidx;
-    __shared__ __align__(16) unsigned char wsm[sizeof(DevWork<T>)];  // an instance's DevWork, relocated
     extern __shared__ __align__(128) unsigned char dyn[];
     BlockTeam tm{sf.red, nullptr, sf.mbar, sf.ph, nullptr, sf.L};
     for (;;) {
@@ -58,40 +57,7 @@ __global__ void __launch_bounds__(1024) k_block(const Args<T>* insts, int B, int
         const int i = sidx;
         __syncthreads();
         if (i >= B) break;
-        const Args<T>& a = insts[i];
-        const int nr = a.rt.n;
-        if (nr == 0) {
-            run_mode<T>(tm, a.P, a.W, S, mode, a.slot, sf.G, sf.rhs, sf.L, sf.t, dyn);
-        } else {
-            // the instance's vectors live in shared memory while it runs: a copy of
-            // its DevWork points there, and the arrays go back to global memory after
-            unsigned char* const rb = dyn + a.rt.base;
-            {
-                const int* src = reinterpret_cast<const int*>(&a.W);
-                int* dst = reinterpret_cast<int*>(wsm);
-                for (int k = threadIdx.x; k < (int)(sizeof(DevWork<T>) / 4); k += blockDim.x) dst[k] = src[k];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0)
-                for (int k = 0; k < nr; ++k)
-                    *reinterpret_cast<unsigned char**>(wsm + a.rt.e[k].field) = rb + a.rt.e[k].off;
-            for (int k = 0; k < nr; ++k) {
-                const Reloc e = a.rt.e[k];
-                const int* g = *reinterpret_cast<int* const*>(reinterpret_cast<const unsigned char*>(&a.W) + e.field);
-                int* s = reinterpret_cast<int*>(rb + e.off);
-                for (int j = threadIdx.x; j < (e.bytes >> 2); j += blockDim.x) s[j] = g[j];
-            }
-            __syncthreads();
-            run_mode<T>(tm, a.P, *reinterpret_cast<const DevWork<T>*>(wsm), S, mode, a.slot, sf.G, sf.rhs, sf.L, sf.t,
-                        dyn);
-            __syncthreads();
-            for (int k = 0; k < nr; ++k) {
-                const Reloc e = a.rt.e[k];
-                int* g = *reinterpret_cast<int* const*>(reinterpret_cast<const unsigned char*>(&a.W) + e.field);
-                const int* s = reinterpret_cast<const int*>(rb + e.off);
-                for (int j = threadIdx.x; j < (e.bytes >> 2); j += blockDim.x) g[j] = s[j];
-            }
-        }
+        run_mode<T>(tm, insts[i].P, insts[i].W, S, mode, insts[i].slot, sf.G, sf.rhs, sf.L, sf.t, dyn);
         __syncthreads();
     }
 }

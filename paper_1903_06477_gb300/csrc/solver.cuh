@@ -214,20 +214,6 @@ struct DevWork {
     DevState* st;
 };
 
-// Shared-memory residence of a block-team instance: each entry names a
-// pointer field of DevWork (its byte offset in the struct) whose array
-// (bytes, a multiple of 4) is copied into dynamic shared memory at byte
-// base + off before the instance runs and back after it; the instance then
-// runs on a copy of DevWork whose fields point there.  n = 0: none.
-struct Reloc {
-    int field, bytes, off;
-};
-constexpr int MAX_RELOC = 40;
-struct RelocTable {
-    int n, base;
-    Reloc e[MAX_RELOC];
-};
-
 template <typename T>
 struct Args {
     DevProb<T> P;
@@ -235,7 +221,6 @@ struct Args {
     DevSettings S;
     int mode;
     int slot;
-    RelocTable rt;
 };
 
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }

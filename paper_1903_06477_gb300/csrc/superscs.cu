@@ -13,7 +13,6 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
-#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -509,7 +508,6 @@ static int check_settings(const scs_settings* S, char* err)
     if (S->precision != SCS_FP64 && S->precision != SCS_MIXED) { set_err(err, "bad precision"); return SCS_EINVAL; }
     if (S->threads != 0 && (S->threads < 32 || S->threads > 1024 || S->threads % 32)) { set_err(err, "threads must be a multiple of 32 in 32..1024"); return SCS_EINVAL; }
     if (!(S->psd_recheck_tol >= 0)) { set_err(err, "psd_recheck_tol must be >= 0"); return SCS_EINVAL; }
-    if (S->block_smem != 0 && S->block_smem != 1) { set_err(err, "block_smem must be 0 or 1"); return SCS_EINVAL; }
     if (S->spmv_path < 0 || S->spmv_path > 4) { set_err(err, "spmv_path must be in 0..4"); return SCS_EINVAL; }
     return SCS_OK;
 }
@@ -766,54 +764,7 @@ struct DevInfo {
     int sms = 0;
     size_t dyn64 = 0, dyn32 = 0;
     bool maxl1 = false;  // grid of one CTA per SM without dynamic shared memory: prefer L1
-    RelocTable rt64{}, rt32{};  // block team: the vectors kept in shared memory while a launch runs
 };
-
-// The block team's shared-memory residence plan for one precision (see
-// RelocTable): every vector of DevWork that Algorithm 1 sweeps -- the eleven
-// HSDE vectors and their tau entries, g, the CG warm starts and scratch
-// vectors, the direction memory -- placed after `base` bytes of dynamic
-// shared memory.  Empty (n = 0) if they need more than `budget` bytes.
-template <typename T>
-static RelocTable plan_reloc(int n, int m, int mem, bool qr, size_t base, size_t budget)
-{
-    RelocTable rt{};
-    const int nm = n + m, mm = std::max(mem, 1);
-    size_t off = 0;
-    auto add = [&](size_t field, size_t bytes) {
-        if (rt.n >= MAX_RELOC) return;
-        rt.e[rt.n++] = Reloc{(int)field, (int)bytes, (int)off};
-        off += (bytes + 15) & ~size_t(15);
-    };
-    using W = DevWork<T>;
-    const size_t hv[] = {offsetof(W, u), offsetof(W, ut), offsetof(W, ub), offsetof(W, Ru), offsetof(W, d),
-                         offsetof(W, dt), offsetof(W, wb), offsetof(W, Rw), offsetof(W, zp), offsetof(W, xip),
-                         offsetof(W, zt)};
-    for (size_t f : hv) {
-        add(f + offsetof(HV<T>, v), sizeof(T) * nm);
-        add(f + offsetof(HV<T>, t), sizeof(double));
-    }
-    add(offsetof(W, g), sizeof(T) * nm);
-    add(offsetof(W, ws), sizeof(T) * n);
-    add(offsetof(W, ws) + sizeof(T*), sizeof(T) * n);
-    add(offsetof(W, cr), sizeof(T) * n);
-    add(offsetof(W, cp), sizeof(T) * n);
-    add(offsetof(W, cq), sizeof(T) * n);
-    add(offsetof(W, tn), sizeof(T) * n);
-    add(offsetof(W, tm), sizeof(T) * m);
-    add(offsetof(W, py), sizeof(T) * m);
-    add(offsetof(W, Zv), sizeof(T) * (size_t)mm * nm);
-    add(offsetof(W, Xv), sizeof(T) * (size_t)mm * nm);
-    add(offsetof(W, Zt), sizeof(double) * mm);
-    add(offsetof(W, Xt), sizeof(double) * mm);
-    if (qr) {
-        add(offsetof(W, Qv), sizeof(T) * (size_t)mm * nm);
-        add(offsetof(W, Qt), sizeof(double) * mm);
-    }
-    if (off > budget || rt.n > MAX_RELOC) return RelocTable{};
-    rt.base = (int)base;
-    return rt;
-}
 
 template <typename T>
 static size_t dyn_smem(const HostProb& H, int threads, bool tma)
@@ -852,9 +803,7 @@ static int launch(const DevInfo& D, size_t dyn, const Args<T>& a, Args<T>* dev_a
         void* kargs[] = {(void*)&a};
         CU(cudaLaunchCooperativeKernel(kgrid_ptr<T>(), dim3(grid), dim3(threads), kargs, dyn, st), err);
     } else {
-        Args<T> ab = a;
-        ab.rt = sizeof(T) == 8 ? D.rt64 : D.rt32;
-        CU(cudaMemcpyAsync(dev_args, &ab, sizeof(Args<T>), cudaMemcpyHostToDevice, st), err);
+        CU(cudaMemcpyAsync(dev_args, &a, sizeof(Args<T>), cudaMemcpyHostToDevice, st), err);
         CU(cudaMemsetAsync(queue, 0, sizeof(int), st), err);
         CU(launch_block<T>(1, threads, dyn, st, dev_args, 1, queue, a.S, a.mode), err);
     }
@@ -924,14 +873,13 @@ extern "C" int scs_default_settings(scs_settings* o)
     o->linsys_direct = 0;
     o->mixed_stall_after_tau = 1;
     o->psd_recheck_tol = 1e-4;
-    o->block_smem = 1;
     return SCS_OK;
 }
 
 template <typename T>
 static Args<T> make_args(const DevProb<T>& P, const DevWork<T>& W, const DevSettings& S, int mode, int slot = 0)
 {
-    Args<T> a{};  // rt.n = 0: no shared-memory residence unless the launch sets it
+    Args<T> a;
     a.P = P;
     a.W = W;
     a.S = S;
@@ -1034,27 +982,6 @@ extern "C" int scs_setup(const scs_data* data, const scs_cone* cone, const scs_s
     w->D.dyn32 = w->has32 ? std::max({dyn_smem<float>(H, w->D.threads, tma), H.cA32.dyn(), H.cAT32.dyn()}) : 0;
     // the FP64 phase of SCS_MIXED also runs FP32 products (refinement corrections)
     if (w->has32) w->D.dyn64 = std::max(w->D.dyn64, w->D.dyn32);
-    if (team == SCS_TEAM_BLOCK && settings->block_smem) {
-        // one CTA runs the whole instance: keep its vectors in shared memory where they fit
-        int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fb{};
-        cudaFuncGetAttributes(&fb, kblock_ptr<double>());
-        const size_t cap = (size_t)std::max(0, optin - (int)fb.sharedSizeBytes - 1024);
-        auto place = [&](auto tag, size_t& dyn, RelocTable& rt) {
-            using TT = decltype(tag);
-            const size_t base = (dyn + 127) & ~size_t(127);
-            if (base >= cap) return;
-            rt = plan_reloc<TT>(H.n, H.m, settings->mem, settings->direction == SCS_DIR_AA_QR, base, cap - base);
-            if (rt.n) {
-                size_t end = base;
-                for (int k = 0; k < rt.n; ++k) end = std::max(end, base + rt.e[k].off + ((rt.e[k].bytes + 15) & ~15));
-                dyn = end;
-            }
-        };
-        place(double{}, w->D.dyn64, w->D.rt64);
-        if (w->has32) place(float{}, w->D.dyn32, w->D.rt32);
-    }
     int rc2 = config_kernels<double>(w->D.dyn64, w->err);
     if (!rc2 && w->has32) rc2 = config_kernels<float>(w->D.dyn32, w->err);
     if (rc2) { memcpy(g_err, w->err, 512); delete w; return rc2; }

@@ -332,22 +332,6 @@ def test_device_pointers_roundtrip():
     np.testing.assert_array_equal(sd.cpu().numpy(), s2)
 
 
-@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
-@pytest.mark.parametrize("name", ["lasso", "planted_mixed_cones"])
-def test_block_team_shared_memory_residence_is_exact(name, precision):
-    """A single block-team instance keeps its vectors in shared memory while it runs
-    (block_smem = 1, the default) or in global memory (0): the arithmetic is the same,
-    so the solves agree bit for bit, iterates and counters included."""
-    prob = PROBS[name]
-    kw = dict(team=B.TEAM_BLOCK, precision=precision, eps=1e-6, max_iters=20000)
-    a = B.Work(prob, block_smem=1, **kw).solve()
-    b = B.Work(prob, block_smem=0, **kw).solve()
-    for u, v in zip(a[:3], b[:3]):
-        np.testing.assert_array_equal(u, v)
-    for key in ("iters", "iters_fp32", "k0", "k1", "k2", "cg_iters", "status"):
-        assert a[3][key] == b[3][key], key
-
-
 def test_repeat_solves_are_deterministic():
     prob = PROBS["planted_c2_small"]
     work = B.Work(prob, team=B.TEAM_GRID, eps=1e-6)
