@@ -36,10 +36,9 @@ FALLBACK_HBM_GBS = 6800.0
 # it was taken on (the digest of KERNEL_SOURCES) and for the same deterministic
 # solve (same outer and CG iteration counts); otherwise the roofline reports null.
 MEASURED_TRAFFIC = {
-    ("c2", "mixed"): {"bytes": 425524747520, "iters_fp32": 113, "cg_iters": 4139,
-                      "digest": "eb697b553cfbbd2906d4d475f3063105acb2611284a2bb0890866e7c8a138513"},
+    ("c2", "mixed"): {"bytes": 515843115776, "iters_fp32": 144, "cg_iters": 3485,
+                      "digest": "3490163287460d2ca8ef39dadd8c3a7e9d9a7c6cc4baa12d37364c6ba76ad5e3"},
 }
-
 
 # the sources that decide what the solver kernels do and which bytes they move:
 # the device code and the host builder of the column-blocked layout
