@@ -609,8 +609,8 @@ def sweep_family(name, seeds):
     """The paper's synthetic families (Sec. 5.2-5.4) as (label, problem) pairs:
     LASSO n in {631,1000,1585,2512}, kappa in {10,215,4600,1e5}, mu in
     {0.01,0.1,1}; l1-logistic p in {80,100}, q in {50,100,120}, lambda in
-    {10,20,50}; sparse-PCA SDP d = 50 (orders above 64 exceed the PSD kernel),
-    lambda in {0.1,2,5}; `seeds` instances of every grid point."""
+    {10,20,50}; sparse-PCA SDP d in {50,120,140,180}, lambda in {0.1,2,5}
+    ("pca500": d = 500); `seeds` instances of every grid point."""
     from paper_1903_06477_gb300 import workloads as W
     out = []
     if name == "lasso":
@@ -627,10 +627,11 @@ def sweep_family(name, seeds):
                     for sd in range(seeds):
                         out.append((f"p{p}_q{q}_l{lam:g}_{sd}",
                                     lambda p=p, q=q, lam=lam, sd=sd: W.logreg(sd, p, q, lam)))
-    elif name == "pca":
-        for lam in (0.1, 2.0, 5.0):
-            for sd in range(seeds):
-                out.append((f"d50_l{lam:g}_{sd}", lambda lam=lam, sd=sd: W.pca_sdp(sd, 50, lam)))
+    elif name in ("pca", "pca500"):
+        for d in ((50, 120, 140, 180) if name == "pca" else (500,)):
+            for lam in (0.1, 2.0, 5.0):
+                for sd in range(seeds):
+                    out.append((f"d{d}_l{lam:g}_{sd}", lambda d=d, lam=lam, sd=sd: W.pca_sdp(sd, d, lam)))
     else:
         raise SystemExit(f"unknown family {name}")
     return out
@@ -783,7 +784,7 @@ def main():
     ap.add_argument("--products", type=int, default=0,
                     help="profiling aid: set up the workload, run this many sparse products (see --op) and exit")
     ap.add_argument("--op", default="a", choices=["a", "at"], help="product for --products: A x or A^T y")
-    ap.add_argument("--sweep", default="lasso", choices=["lasso", "logreg", "pca"],
+    ap.add_argument("--sweep", default="lasso", choices=["lasso", "logreg", "pca", "pca500"],
                     help="family of --workload sweep")
     ap.add_argument("--sweep-seeds", type=int, default=1)
     ap.add_argument("--sweep-oracle", action="store_true", help="also time the FP64 oracle on every instance")

@@ -73,7 +73,9 @@ typedef struct {
     int32_t nq;          /* number of SOCs */
     const int32_t *q;    /* SOC dimensions, each >= 1 (Sec. 2 cone (iii)) */
     int32_t ns;          /* number of PSD blocks */
-    const int32_t *s;    /* PSD orders d, each 1..64 (Sec. 2 cone (ii)) */
+    const int32_t *s;    /* PSD orders d, each 1..1024 (Sec. 2 cone (ii)); blocks up to 64 are
+                            decomposed in shared memory, larger ones in a global-memory workspace
+                            of about 2 d^2 words (plus d^2 doubles for SCS_MIXED) per block */
     int32_t ep;          /* primal exponential cones (Sec. 2 cone (v)), 3 rows each:
                             (x1, x2, x3) with x1 >= x2 exp(x3 / x2), x2 > 0, closure */
     int32_t ed;          /* dual exponential cones, 3 rows each: (y1, y2, y3) with

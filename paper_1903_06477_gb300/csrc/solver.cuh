@@ -17,8 +17,9 @@ namespace sscs {
 
 constexpr int MAXMEM = 64;   // direction memory cap (RB)
 constexpr int AAMAX = 32;    // Anderson memory cap (Gram matrix kept in shared memory)
-constexpr int PSD_MAX = 64;  // largest PSD order
+constexpr int PSD_MAX = 64;  // largest PSD order decomposed in shared memory
 constexpr int PSD_LD = PSD_MAX + 1;  // row stride bound of a block's matrices in shared memory
+constexpr int PSD_BIG_MAX = 1024;    // largest PSD order (orders above PSD_MAX use a global-memory workspace)
 
 enum Mode { MODE_SETUP = 0, MODE_SOLVE = 1, MODE_LINSYS = 2, MODE_PROJECT = 3, MODE_APPLY_T = 4, MODE_PROFILE = 5,
             MODE_RESID = 6, MODE_SPMV = 7, MODE_FACTOR = 8 };
@@ -178,6 +179,10 @@ struct DevProb {
     const int* s_off;  // ns row offsets of the PSD blocks inside s
     int ep, ed;        // primal / dual exponential cones (3 rows each)
     int e_off;         // row offset of the first exponential cone inside s
+    // PSD blocks above PSD_MAX: the Jacobi workspace of block k starts at psd_big + big_off[k]
+    // bytes (laid out by psd_big_smem below; big_off[k] < 0 for blocks decomposed in shared memory)
+    unsigned char* psd_big;
+    const long long* big_off;
 };
 
 // Iterative refinement of the FP64 linear solves (SCS_MIXED, FP64 phase): the
@@ -1561,6 +1566,36 @@ __host__ __device__ constexpr size_t psd_smem_bytes()
            (sizeof(T) == 4 ? sizeof(double) * PSD_MAX * PSD_LD : 0);
 }
 
+// Workspace of one PSD block of order d > PSD_MAX in global memory, with the
+// relative layout of the shared-memory one (X and V adjacent, then cs, sn,
+// lam, pp, qq and, for FP32, X0), so that the FP64 redo's overlays hold:
+// the FP64 eigenvectors over X and V, the FP64 cosines over cs and sn, the
+// FP64 sines over lam.
+template <typename T>
+__host__ __device__ constexpr size_t psd_big_bytes(int d)
+{
+    const size_t dp = (size_t)(d + (d & 1)), ld = dp + 1;
+    const size_t b = sizeof(T) * (2 * dp * ld + 2 * dp) + sizeof(int) * dp + (sizeof(T) == 4 ? 8 * dp * ld : 0);
+    return (b + 15) & ~size_t(15);
+}
+
+template <typename T>
+__device__ PsdSmem<T> psd_big_ws(unsigned char* base, int d, double* red)
+{
+    const int dp = d + (d & 1), ld = dp + 1, half = dp / 2;
+    PsdSmem<T> s;
+    s.X = (T*)base;
+    s.V = s.X + (size_t)dp * ld;
+    s.cs = s.V + (size_t)dp * ld;
+    s.sn = s.cs + half;
+    s.lam = s.sn + half;
+    s.red = red;
+    s.pp = (int*)(s.lam + dp);
+    s.qq = s.pp + half;
+    s.X0 = sizeof(T) == 4 ? (double*)(s.qq + half) : nullptr;
+    return s;
+}
+
 template <typename T>
 __device__ PsdSmem<T> psd_smem(unsigned char* base)
 {
@@ -1652,13 +1687,15 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
         __syncwarp();
     }
     // PSD blocks: one CTA per block, Jacobi eigen-decomposition in shared memory
+    // (orders above PSD_MAX: in the block's workspace in global memory)
     if (P.ns > 0) {
-        PsdSmem<T> sm = psd_smem<T>(psd_base);
+        const PsdSmem<T> sm_small = psd_smem<T>(psd_base);
         for (int k = tm.block(); k < P.ns; k += tm.nblocks()) {
             const int d = ro(P.s_dim + k);
             const int o = n + ro(P.s_off + k);
             const int dp = d + (d & 1);
             const int ld = dp + 1;  // odd row stride: column walks are free of bank conflicts
+            PsdSmem<T> sm = d > PSD_MAX ? psd_big_ws<T>(P.psd_big + ro(P.big_off + k), d, sm_small.red) : sm_small;
             const double isq2 = 0.70710678118654752440;
             __syncthreads();
             for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
@@ -1676,7 +1713,8 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
             }
             __syncthreads();
             const double tol2 = sizeof(T) == 8 ? 1e-26 : 1e-11;
-            jacobi_block<T>(sm.X, sm.V, dp, ld, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2, sizeof(T) == 8 ? 20 : 15);
+            jacobi_block<T>(sm.X, sm.V, dp, ld, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2,
+                            d > PSD_MAX ? 30 : (sizeof(T) == 8 ? 20 : 15));
             if constexpr (sizeof(T) == 4) {
                 // FP64 recheck of the FP32 eigenpairs: ||X V - V diag(l)||_F / ||X||_F
                 double r2 = 0.0, x2 = 0.0;

@@ -399,8 +399,8 @@ static int prepare(const scs_data* d, const scs_cone* k, HostProb& H, char* err,
         H.q.push_back(k->q[i]);
     }
     for (int i = 0; i < k->ns; ++i) {
-        if (k->s[i] < 1 || k->s[i] > PSD_MAX) {
-            set_err(err, "PSD block %d has order %d outside 1..%d", i, k->s[i], PSD_MAX);
+        if (k->s[i] < 1 || k->s[i] > PSD_BIG_MAX) {
+            set_err(err, "PSD block %d has order %d outside 1..%d", i, k->s[i], PSD_BIG_MAX);
             return SCS_EINVAL;
         }
         H.s.push_back(k->s[i]);
@@ -598,6 +598,12 @@ static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, bool direct, 
     P.ep = H.ep;
     P.ed = H.ed;
     P.e_off = H.e_off;
+    // global Jacobi workspaces of the PSD blocks above PSD_MAX (their offsets are uploaded with the problem)
+    size_t big = 0;
+    for (int d : H.s)
+        if (d > PSD_MAX) big += psd_big_bytes<T>(d);
+    P.big_off = H.s.empty() ? nullptr : A.take<long long>(H.s.size());
+    P.psd_big = big ? A.take<unsigned char>(big) : nullptr;
     double* taus = A.take<double>(16);
     HV<T>* hvs[] = {&W.u, &W.ut, &W.ub, &W.Ru, &W.d, &W.dt, &W.wb, &W.Rw, &W.zp, &W.xip, &W.zt};
     for (int i = 0; i < 11; ++i) {
@@ -693,6 +699,21 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         if (!v.empty()) CU(cudaMemcpyAsync((void*)dst, v.data(), 2 * v.size(), cudaMemcpyHostToDevice, st), err);
         return SCS_OK;
     };
+    // byte offsets of the PSD blocks' global Jacobi workspaces (-1: decomposed in shared memory)
+    auto put_big = [&]() -> int {
+        if (H.s.empty()) return SCS_OK;
+        std::vector<long long> off(H.s.size(), -1);
+        long long o = 0;
+        for (size_t k = 0; k < H.s.size(); ++k)
+            if (H.s[k] > PSD_MAX) {
+                off[k] = o;
+                o += (long long)psd_big_bytes<T>(H.s[k]);
+            }
+        CU(cudaMemcpyAsync((void*)P.big_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st),
+           err);
+        CU(cudaStreamSynchronize(st), err);  // off is a local
+        return SCS_OK;
+    };
     auto put_cb = [&](const HostProb::Cb& hc, const Cblk<T>& dc) -> int {
         if (hc.ncb == 0) return SCS_OK;
         int r;
@@ -702,6 +723,7 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         return SCS_OK;
     };
     int rc;
+    if ((rc = put_big())) return rc;
     if (!matrix) {
         if ((rc = put_t(H.b, P.b)) || (rc = put_t(H.c, P.c))) return rc;
         CU(cudaStreamSynchronize(st), err);

@@ -419,6 +419,48 @@ def test_psd_fp32_redo_in_a_solve():
     assert info["psd_redo_fp32"] >= info["iters_fp32"] * len(prob["s"])
 
 
+@pytest.mark.parametrize("team", TEAMS)
+def test_psd_projection_blocks_above_64(team):
+    """PSD blocks above order 64 are decomposed in a global-memory workspace: Pi_C matches
+    the oracle in FP64 (1e-10) and, as the FP32 phase runs it, within the FP32 bound with
+    every block redone in FP64 (psd_recheck_tol = 0) and within 1e-4 ||X||_F by default."""
+    prob = W.planted(seed=44, n=40, l=10, psd=[65, 100, 151, 7], nnz=3000)
+    orc = O.Oracle(prob)
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(40 + prob["A"].shape[0] + 1) * 2
+    ref = orc.proj_C(v)
+    work = B.Work(prob, team=team, precision=B.MIXED)
+    np.testing.assert_allclose(work.project_cone(v), ref, rtol=0, atol=1e-10)
+    out, stats = work.project_cone_prec(v, B.MIXED)
+    assert 0 < stats[0] < 1e-4
+    segs = _psd_segments(prob, 40)
+    for o, k in segs:
+        assert np.linalg.norm(out[o:o + k] - ref[o:o + k]) <= 1e-4 * np.linalg.norm(v[o:o + k])
+    forced = B.Work(prob, team=team, precision=B.MIXED, psd_recheck_tol=0.0)
+    out, stats = forced.project_cone_prec(v, B.MIXED)
+    assert stats[1] == len(prob["s"])
+    for o, k in segs:
+        assert np.linalg.norm(out[o:o + k] - ref[o:o + k]) <= 6 * 2.0 ** -24 * np.linalg.norm(v[o:o + k])
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+def test_sparse_pca_above_64_matches_oracle(precision):
+    """The sparse-PCA SDP of Sec. 5.2 at d = 80 (one PSD block above 64): solved to eps, the
+    objective within 10 eps (1 + |p*|) of the FP64 oracle's solve, Z in the PSD cone."""
+    prob = W.pca_sdp(0, 80, 2.0)
+    eps = 1e-5
+    kw = dict(direction=B.DIR_AA, mem=10, eps=eps, max_iters=20000)
+    work = B.Work(prob, precision=precision, cg_adapt=1e-2, **kw)
+    x, y, s, info = work.solve()
+    assert info["status"] == B.SOLVED, info
+    assert max(_kkt(prob, x, y, s)) <= eps * 1.01
+    check_in_cone(prob, s, dual=False, tol=1e-6)
+    ref = O.Oracle(prob, **kw).solve()
+    assert ref["info"].status == O.SOLVED
+    pstar = ref["info"].pobj
+    assert abs(info["pobj"] - pstar) <= 10 * eps * (1 + abs(pstar))
+
+
 @pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
 def test_planted_sdp_small(precision):
     prob = W.planted(seed=42, n=300, l=200, psd=[16] * 6 + [9, 33], nnz=6000)
