@@ -677,6 +677,7 @@ def run_sweep(args):
             "config": {"workload": f"{args.sweep} family of the paper, {args.sweep_seeds} seed(s) per grid point",
                        "eps": 1e-4, "direction": "AA mem 10"},
             "mean_s": float(np.mean([t for t in gpu_t if np.isfinite(t)])), "median_iters": float(np.median(iters)),
+            "per_instance": [{"label": lab, "s": t, "iters": it} for (lab, _), t, it in zip(fam, gpu_t, iters)],
             "cpu_baseline": None if not cpu_t else {"value": W.sgm(cpu_t), "unit": "s", "cores": 1, "kind": "oracle",
                                                     "sample": "the same instances, FP64 oracle, one thread",
                                                     "success": solved_cpu / len(fam), **host_info()}}
