@@ -664,6 +664,8 @@ def run_sweep(args):
         solved += ok
         iters.append(info["iters"])
         w.close()
+        print(f"# {label}: {gpu_t[-1]:.4f} s, {info['iters']} iterations, status {info['status']}",
+              file=sys.stderr, flush=True)
         if args.sweep_oracle:
             from oracle import oracle as O
             t0 = time.perf_counter()

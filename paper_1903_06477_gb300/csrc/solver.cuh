@@ -180,9 +180,10 @@ struct DevProb {
     int ep, ed;        // primal / dual exponential cones (3 rows each)
     int e_off;         // row offset of the first exponential cone inside s
     // PSD blocks above PSD_MAX: the Jacobi workspace of block k starts at psd_big + big_off[k]
-    // bytes (laid out by psd_big_smem below; big_off[k] < 0 for blocks decomposed in shared memory)
+    // bytes (laid out by psd_big_ws below; big_off[k] < 0 for blocks decomposed in shared memory)
     unsigned char* psd_big;
     const long long* big_off;
+    const long long* v_off;  // byte offset of each PSD block's warm-start eigenvectors in DevWork::psd_v
 };
 
 // Iterative refinement of the FP64 linear solves (SCS_MIXED, FP64 phase): the
@@ -213,6 +214,8 @@ struct DevWork {
     double *io_in, *io_out, *io_out2;      // N-vectors of the single-operator entries
     double* warm;                          // N: warm start (FP64)
     double *x_out, *y_out, *s_out, *u_out; // results (FP64)
+    unsigned char* psd_v;  // PSD blocks: eigenvectors of the last converged decomposition (warm starts)
+    int* psd_vok;          // per PSD block: 1 if psd_v holds them
     double* partials;      // [2][KMAX][blocks] block partials, then [2][KMAX] results
     unsigned* bar;
     int* abort_flag;
@@ -1334,17 +1337,22 @@ __device__ __forceinline__ double block_sum(double x, double* red)
 // Parallel two-sided Jacobi (round-robin pairing, d/2 disjoint rotations per
 // round) on the dp x dp matrix X in shared memory; V receives the
 // eigenvectors as columns.  Rotation formula as in the textbook cyclic method.
+// v_init: V already holds an orthogonal start basis (the rotations are
+// accumulated onto it), else it starts as the identity.  Returns true if the
+// off-diagonal mass fell below tol2 times the total within max_sweeps (the
+// same value in every thread).
 template <typename T>
-__device__ void jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs, T* sn, double* red, double tol2,
-                             int max_sweeps)
+__device__ bool jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs, T* sn, double* red, double tol2,
+                             int max_sweeps, bool v_init = false)
 {
     // X and V are dp x dp with row stride ld = dp + 1 (odd): a warp walking a
     // column touches 32 different banks
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int idx = tid; idx < dp * dp; idx += nt) {
-        const int i = idx / dp, j = idx % dp;
-        V[i * ld + j] = (i == j) ? T(1) : T(0);
-    }
+    if (!v_init)
+        for (int idx = tid; idx < dp * dp; idx += nt) {
+            const int i = idx / dp, j = idx % dp;
+            V[i * ld + j] = (i == j) ? T(1) : T(0);
+        }
     double total = 0.0;
     for (int idx = tid; idx < dp * dp; idx += nt) {
         const T x = X[(idx / dp) * ld + idx % dp];
@@ -1360,7 +1368,7 @@ __device__ void jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs
             if (i != j) off += (double)X[i * ld + j] * (double)X[i * ld + j];
         }
         off = block_sum(off, red);
-        if (off <= tol2 * total || off == 0.0) break;
+        if (off <= tol2 * total || off == 0.0) return true;
         for (int rnd = 0; rnd < dp - 1; ++rnd) {
             for (int k = tid; k < half; k += nt) {
                 int a, b;
@@ -1416,6 +1424,7 @@ __device__ void jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs
             __syncthreads();
         }
     }
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -1579,6 +1588,14 @@ __host__ __device__ constexpr size_t psd_big_bytes(int d)
     return (b + 15) & ~size_t(15);
 }
 
+// warm-start eigenvectors of one PSD block: dp x (dp + 1) elements, 16-byte aligned
+template <typename T>
+__host__ __device__ constexpr size_t psd_v_bytes(int d)
+{
+    const size_t dp = (size_t)(d + (d & 1));
+    return (sizeof(T) * dp * (dp + 1) + 15) & ~size_t(15);
+}
+
 template <typename T>
 __device__ PsdSmem<T> psd_big_ws(unsigned char* base, int d, double* red)
 {
@@ -1619,6 +1636,11 @@ struct PsdCheck {
     double* resid;
     long long* redo;
     double tol;
+    // warm starts: block k's eigenvectors of its last converged decomposition are kept at
+    // vbase + voff[k] bytes (dp x (dp+1) elements of the bulk type), valid while vok[k] != 0
+    unsigned char* vbase;
+    const long long* voff;
+    int* vok;
 };
 
 // FP64 Jacobi of the block whose FP64 copy X0 is in shared memory (FP32
@@ -1713,8 +1735,46 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
             }
             __syncthreads();
             const double tol2 = sizeof(T) == 8 ? 1e-26 : 1e-11;
-            jacobi_block<T>(sm.X, sm.V, dp, ld, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2,
-                            d > PSD_MAX ? 30 : (sizeof(T) == 8 ? 20 : 15));
+            // Warm start: successive projections of a block see nearby matrices, so the
+            // eigenvectors Vp of the last converged decomposition nearly diagonalise this one.
+            // X <- Vp^T X Vp (symmetrised) and V <- Vp, then the sweeps accumulate onto V:
+            // the same eigenpairs, found in a few sweeps instead of a dozen.
+            T* Vp = ck.vbase ? reinterpret_cast<T*>(ck.vbase + ro(ck.voff + k)) : nullptr;
+            const bool warm = Vp && *(volatile const int*)(ck.vok + k) != 0;
+            if (warm) {
+                for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {  // V <- X Vp
+                    const int i = idx / dp, j = idx % dp;
+                    T s = 0;
+                    for (int l = 0; l < dp; ++l) s = fmaT(sm.X[i * ld + l], Vp[l * ld + j], s);
+                    sm.V[i * ld + j] = s;
+                }
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {  // X <- Vp^T V
+                    const int i = idx / dp, j = idx % dp;
+                    T s = 0;
+                    for (int l = 0; l < dp; ++l) s = fmaT(Vp[l * ld + i], sm.V[l * ld + j], s);
+                    sm.X[i * ld + j] = s;
+                }
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {
+                    const int i = idx / dp, j = idx % dp;
+                    if (i < j) {
+                        const T a = T(0.5) * (sm.X[i * ld + j] + sm.X[j * ld + i]);
+                        sm.X[i * ld + j] = a;
+                        sm.X[j * ld + i] = a;
+                    }
+                    sm.V[i * ld + j] = Vp[i * ld + j];
+                }
+                __syncthreads();
+            }
+            const bool conv = jacobi_block<T>(sm.X, sm.V, dp, ld, sm.pp, sm.qq, sm.cs, sm.sn, sm.red, tol2,
+                                              d > PSD_MAX ? 30 : (sizeof(T) == 8 ? 20 : 15), warm);
+            if (Vp) {
+                if (conv)
+                    for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x)
+                        Vp[(idx / dp) * ld + idx % dp] = sm.V[(idx / dp) * ld + idx % dp];
+                if (threadIdx.x == 0) ck.vok[k] = conv ? 1 : 0;
+            }
             if constexpr (sizeof(T) == 4) {
                 // FP64 recheck of the FP32 eigenpairs: ||X V - V diag(l)||_F / ||X||_F
                 double r2 = 0.0, x2 = 0.0;
@@ -1734,7 +1794,10 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                     atomicMax((unsigned long long*)ck.resid, (unsigned long long)__double_as_longlong(rel));
                 if (rel > ck.tol && ck.redo) {
                     psd_redo_fp64(sm, dp, ld);
-                    if (threadIdx.x == 0) atomicAdd((unsigned long long*)ck.redo, 1ull);
+                    if (threadIdx.x == 0) {
+                        atomicAdd((unsigned long long*)ck.redo, 1ull);
+                        if (Vp) ck.vok[k] = 0;  // the FP32 eigenvectors were not good enough to start from
+                    }
                     const double* V64 = reinterpret_cast<const double*>(sm.X);
                     for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
                         const int i = idx / d, j = idx % d;
@@ -2541,7 +2604,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
         tm.sync();
         cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, 0.0, S.refine != 0);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
         double red[1] = {(double)op.acc0};
         tm.reduce(red);
         nRu_cold = sqrt(red[0]);
@@ -2554,7 +2617,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
     double nRu;
     {
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
         double red[1] = {(double)op.acc0};
         tm.reduce(red);
         nRu = sqrt(red[0]);
@@ -2680,7 +2743,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             // K0
             eta = nRu;
             OpK0<T> op{W.u, W.ut, W.ub, W.Ru, W.d, W.dt, W.zp, W.xip, T(0), T(0)};
-            project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+            project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
             double red[2] = {(double)op.acc0, (double)op.acc1};
             tm.reduce(red);
             nRu = sqrt(red[0]);
@@ -2691,7 +2754,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             for (int ls = 0; ls <= S.ls_max; ++ls) {
                 if (ls == S.ls_max) alpha = 0.0;
                 OpTrial<T> op{W.u, W.ut, W.d, W.dt, W.wb, W.Rw, alpha, T(0), T(0)};
-                project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+                project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
                 double red[2] = {(double)op.acc0, (double)op.acc1};
                 tm.reduce(red);
                 const double nRw = sqrt(red[0]);
@@ -2751,7 +2814,7 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
                     nz2 = red2[0];
                     cg_total += linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, hg, atol, S.refine != 0);
                     OpResidual<T> opr{W.u, W.ut, W.ub, W.Ru, T(0)};
-                    project_pass(tm, P, opr, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+                    project_pass(tm, P, opr, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
                     double red3[1] = {(double)opr.acc0};
                     tm.reduce(red3);
                     nRu = sqrt(red3[0]);
@@ -3006,14 +3069,14 @@ __device__ void run_mode(Team& tm, const DevProb<T>& P, const DevWork<T>& W, con
         if (tm.leader()) W.io_out[nm] = *W.ut.t;
     } else if (mode == MODE_PROJECT) {
         OpProject<T> op{W.u.v, W.u.t, W.ub.v, W.ub.t};
-        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) W.io_out[i] = (double)W.ub.v[i];
         if (tm.leader()) W.io_out[nm] = *W.ub.t;
     } else if (mode == MODE_APPLY_T) {
         linsys(tm, P, W, W.u, W.ut, 0, S.cg_rtol, S.cg_max, W.st->hg);
         OpResidual<T> op{W.u, W.ut, W.ub, W.Ru, T(0)};
-        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol});
+        project_pass(tm, P, op, psd, PsdCheck{&W.st->psd_resid, &W.st->psd_redo, S.psd_tol, W.psd_v, P.v_off, W.psd_vok});
         tm.sync();
         for (int i = tm.rank(); i < nm; i += tm.size()) {
             W.io_out[i] = (double)W.u.v[i] - (double)W.Ru.v[i];

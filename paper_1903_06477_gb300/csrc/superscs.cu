@@ -604,6 +604,12 @@ static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, bool direct, 
         if (d > PSD_MAX) big += psd_big_bytes<T>(d);
     P.big_off = H.s.empty() ? nullptr : A.take<long long>(H.s.size());
     P.psd_big = big ? A.take<unsigned char>(big) : nullptr;
+    // warm-start eigenvectors of every PSD block (offsets uploaded with the problem, flags zeroed with the arena)
+    size_t vbytes = 0;
+    for (int d : H.s) vbytes += psd_v_bytes<T>(d);
+    P.v_off = H.s.empty() ? nullptr : A.take<long long>(H.s.size());
+    W.psd_v = vbytes ? A.take<unsigned char>(vbytes) : nullptr;
+    W.psd_vok = H.s.empty() ? nullptr : A.take<int>(H.s.size());
     double* taus = A.take<double>(16);
     HV<T>* hvs[] = {&W.u, &W.ut, &W.ub, &W.Ru, &W.d, &W.dt, &W.wb, &W.Rw, &W.zp, &W.xip, &W.zt};
     for (int i = 0; i < 11; ++i) {
@@ -700,18 +706,24 @@ static int upload(const HostProb& H, const DevProb<T>& P, bool idx, cudaStream_t
         return SCS_OK;
     };
     // byte offsets of the PSD blocks' global Jacobi workspaces (-1: decomposed in shared memory)
+    // and of their warm-start eigenvectors
     auto put_big = [&]() -> int {
         if (H.s.empty()) return SCS_OK;
-        std::vector<long long> off(H.s.size(), -1);
-        long long o = 0;
-        for (size_t k = 0; k < H.s.size(); ++k)
+        std::vector<long long> off(H.s.size(), -1), voff(H.s.size(), 0);
+        long long o = 0, ov = 0;
+        for (size_t k = 0; k < H.s.size(); ++k) {
             if (H.s[k] > PSD_MAX) {
                 off[k] = o;
                 o += (long long)psd_big_bytes<T>(H.s[k]);
             }
+            voff[k] = ov;
+            ov += (long long)psd_v_bytes<T>(H.s[k]);
+        }
         CU(cudaMemcpyAsync((void*)P.big_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st),
            err);
-        CU(cudaStreamSynchronize(st), err);  // off is a local
+        CU(cudaMemcpyAsync((void*)P.v_off, voff.data(), sizeof(long long) * voff.size(), cudaMemcpyHostToDevice, st),
+           err);
+        CU(cudaStreamSynchronize(st), err);  // off and voff are locals
         return SCS_OK;
     };
     auto put_cb = [&](const HostProb::Cb& hc, const Cblk<T>& dc) -> int {
