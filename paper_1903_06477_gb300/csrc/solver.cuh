@@ -215,7 +215,7 @@ struct DevWork {
     double* warm;                          // N: warm start (FP64)
     double *x_out, *y_out, *s_out, *u_out; // results (FP64)
     unsigned char* psd_v;  // PSD blocks: eigenvectors of the last converged decomposition (warm starts)
-    int* psd_vok;          // per PSD block: 1 if psd_v holds them
+    int* psd_vok;          // per PSD block: 0 if psd_v holds nothing, else warm-start generations
     double* partials;      // [2][KMAX][blocks] block partials, then [2][KMAX] results
     unsigned* bar;
     int* abort_flag;
@@ -1637,7 +1637,8 @@ struct PsdCheck {
     long long* redo;
     double tol;
     // warm starts: block k's eigenvectors of its last converged decomposition are kept at
-    // vbase + voff[k] bytes (dp x (dp+1) elements of the bulk type), valid while vok[k] != 0
+    // vbase + voff[k] bytes (dp x (dp+1) elements of the bulk type); vok[k] = 0: none, else the
+    // number of decompositions since the last cold one
     unsigned char* vbase;
     const long long* voff;
     int* vok;
@@ -1738,9 +1739,13 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
             // Warm start: successive projections of a block see nearby matrices, so the
             // eigenvectors Vp of the last converged decomposition nearly diagonalise this one.
             // X <- Vp^T X Vp (symmetrised) and V <- Vp, then the sweeps accumulate onto V:
-            // the same eigenpairs, found in a few sweeps instead of a dozen.
+            // the same eigenpairs, found in a few sweeps instead of a dozen.  vok[k] counts the
+            // generations since the last cold start; V loses orthogonality by a few roundings
+            // per generation, so every PSD_WARM_GEN-th decomposition starts cold again.
+            constexpr int PSD_WARM_GEN = sizeof(T) == 4 ? 16 : 64;
             T* Vp = ck.vbase ? reinterpret_cast<T*>(ck.vbase + ro(ck.voff + k)) : nullptr;
-            const bool warm = Vp && *(volatile const int*)(ck.vok + k) != 0;
+            const int gen = Vp ? *(volatile const int*)(ck.vok + k) : 0;
+            const bool warm = gen > 0 && gen < PSD_WARM_GEN;
             if (warm) {
                 for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x) {  // V <- X Vp
                     const int i = idx / dp, j = idx % dp;
@@ -1773,7 +1778,7 @@ __device__ void project_pass(Team& tm, const DevProb<T>& P, Op& op, unsigned cha
                 if (conv)
                     for (int idx = threadIdx.x; idx < dp * dp; idx += blockDim.x)
                         Vp[(idx / dp) * ld + idx % dp] = sm.V[(idx / dp) * ld + idx % dp];
-                if (threadIdx.x == 0) ck.vok[k] = conv ? 1 : 0;
+                if (threadIdx.x == 0) ck.vok[k] = conv ? (warm ? gen + 1 : 1) : 0;
             }
             if constexpr (sizeof(T) == 4) {
                 // FP64 recheck of the FP32 eigenpairs: ||X V - V diag(l)||_F / ||X||_F
