@@ -1444,29 +1444,54 @@ __device__ bool jacobi_block(T* X, T* V, int dp, int ld, int* pp, int* qq, T* cs
 // ray points) is returned.  The dual cone K* = cl{y3 < 0, -y3 exp(y2/y3) <= e y1}
 // is projected through Moreau's decomposition, Pi_{K*}(v) = v + Pi_K(-v).
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ double expc_F(double rho, double r, double s, double t)
+// F for rho <= 0 given e = e^rho, and for rho > 0 given em = e^-rho (scaled by e^-2rho)
+static __device__ __forceinline__ double expc_Fn(double rho, double e, double r, double s, double t)
 {
-    if (rho <= 0.0) {
-        const double e = exp(rho), e2 = e * e;
-        return r * (1.0 + (1.0 - rho) * e2) - s * (rho + e2) + t * e * (rho * rho - rho + 1.0);
-    }
-    const double em = exp(-rho), em2 = em * em;
+    const double e2 = e * e;
+    return r * (1.0 + (1.0 - rho) * e2) - s * (rho + e2) + t * e * (rho * rho - rho + 1.0);
+}
+static __device__ __forceinline__ double expc_Fp(double rho, double em, double r, double s, double t)
+{
+    const double em2 = em * em;
     return r * ((1.0 - rho) + em2) - s * (rho * em2 + 1.0) + t * em * (rho * rho - rho + 1.0);
 }
+static __device__ __forceinline__ double expc_F(double rho, double r, double s, double t)
+{
+    return rho <= 0.0 ? expc_Fn(rho, exp(rho), r, s, t) : expc_Fp(rho, exp(-rho), r, s, t);
+}
 
-// root of F in [lo, hi] (sign change), by bisection to adjacent doubles
+// Root of F in [lo, hi] (a sign change) to adjacent doubles: regula falsi with the
+// Illinois modification (the retained end's value is halved when the same end is
+// kept twice), a bisection step every fourth iteration so the bracket at least halves
+// that often.  Converges in a dozen evaluations where bisection needs about sixty.
 static __device__ double expc_root(double lo, double hi, double flo, double r, double s, double t)
 {
-    for (int it = 0; it < 2200; ++it) {
+    // both ends exactly (the grid's values carry the incremental exponentials' roundings)
+    flo = expc_F(lo, r, s, t);
+    if (flo == 0.0) return lo;
+    double fhi = expc_F(hi, r, s, t);
+    if (fhi == 0.0) return hi;
+    int kept = 0;  // -1: lo kept last time, +1: hi kept last time
+    for (int it = 0; it < 400; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (!(mid > lo && mid < hi)) break;
-        const double fm = expc_F(mid, r, s, t);
-        if (fm == 0.0) return mid;
-        if ((fm > 0.0) == (flo > 0.0)) {
-            lo = mid;
-            flo = fm;
+        double x = mid;
+        if ((it & 3) != 3) {
+            const double sec = (lo * fhi - hi * flo) / (fhi - flo);
+            if (sec > lo && sec < hi) x = sec;
+        }
+        const double fx = expc_F(x, r, s, t);
+        if (fx == 0.0) return x;
+        if ((fx > 0.0) == (flo > 0.0)) {
+            lo = x;
+            flo = fx;
+            if (kept == 1) fhi *= 0.5;
+            kept = 1;
         } else {
-            hi = mid;
+            hi = x;
+            fhi = fx;
+            if (kept == -1) flo *= 0.5;
+            kept = -1;
         }
     }
     return 0.5 * (lo + hi);
@@ -1540,10 +1565,22 @@ static __device__ void expc_project(double& x1, double& x2, double& x3)
             fa = fb;
         }
     }
-    double xa = -60.0, fa = expc_F(xa, r, s, t);
+    // the grid: e^rho (rho <= 0) and e^-rho (rho > 0) advance by a factor e^(+-1/4) per step and
+    // are evaluated afresh every 16 steps, so the scan takes one exp in 16; the roots are refined
+    // with exact evaluations
+    const double up = exp(0.25), down = exp(-0.25);
+    double xa = -60.0, ea = exp(-60.0), fa = expc_Fn(xa, ea, r, s, t);
+    double emb = 0.0;
     for (int k = 1; k <= 480; ++k) {
         const double xb = -60.0 + 0.25 * k;
-        const double fb = expc_F(xb, r, s, t);
+        double fb;
+        if (k <= 240) {
+            ea = (k & 15) == 0 ? exp(xb) : ea * up;
+            fb = expc_Fn(xb, ea, r, s, t);
+        } else {
+            emb = (k & 15) == 0 || k == 241 ? exp(-xb) : emb * down;
+            fb = expc_Fp(xb, emb, r, s, t);
+        }
         if (fb == 0.0) expc_try_ray(xb, r, s, t, br, bs, bt, bd);
         else if (fa != 0.0 && (fb > 0.0) != (fa > 0.0))
             expc_try_ray(expc_root(xa, xb, fa, r, s, t), r, s, t, br, bs, bt, bd);
