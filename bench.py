@@ -648,6 +648,9 @@ def run_sweep(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     fam = sweep_family(args.sweep, args.sweep_seeds)
     kw = dict(direction=0, mem=10, eps=1e-4, max_iters=100000, cg_rtol=1e-10, cg_adapt=1e-2)
+    if args.sweep.startswith("pca"):
+        # one CTA runs the instance, its PSD block's eigensolve included: give it the most threads
+        kw["threads"] = 1024
     gpu_t, cpu_t, solved, solved_cpu, iters = [], [], 0, 0, []
     st = torch.cuda.current_stream()
     for label, make in fam:
