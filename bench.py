@@ -607,14 +607,16 @@ def run_c5(args):
 
 def sweep_family(name, seeds):
     """The paper's synthetic families (Sec. 5.2-5.4) as (label, problem) pairs:
-    LASSO n in {631,1000,1585,2512}, kappa in {10,215,4600,1e5}, mu in
+    LASSO n in {631,1000,1585} (the paper's 2512 left out), kappa in {10,215,4600,1e5}, mu in
     {0.01,0.1,1}; l1-logistic p in {80,100}, q in {50,100,120}, lambda in
     {10,20,50}; sparse-PCA SDP d in {50,120,140,180}, lambda in {0.1,2,5}
     ("pca500": d = 500); `seeds` instances of every grid point."""
     from paper_1903_06477_gb300 import workloads as W
     out = []
     if name == "lasso":
-        for n in (631, 1000, 1585, 2512):
+        # n = 2512 is left out: the first instance of that size faulted in setup on the GPU with an
+        # illegal address, cause not found (its sparse layouts pass every host-side check)
+        for n in (631, 1000, 1585):
             for kappa in (10.0, 215.0, 4600.0, 1e5):
                 for mu in (0.01, 0.1, 1.0):
                     for sd in range(seeds):
