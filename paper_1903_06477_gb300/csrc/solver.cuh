@@ -157,6 +157,7 @@ struct Sell {
     const int* perm;   // sorted position -> original row (nslices * H entries, -1 past the end)
     const int* wbnd;   // grid team only: warp w owns slices [wbnd[w], wbnd[w+1]) (nnz-balanced), else null
     Cblk<T> cb;        // grid team only: column-blocked copy (cb.ncb > 0), used instead of the above
+    int l1;            // block team: the padded matrix is small enough (48 KB) to keep in L1 across products
 };
 
 constexpr int TMA_CH = 8;  // t-steps (of 32 elements) per staged chunk
@@ -239,16 +240,13 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 // turn; xf(c) supplies the gathered vector entry, epi(row, sum) consumes the
 // row result (only lanes q = 0 call it)
 // ---------------------------------------------------------------------------
-// Matrix entries of the sliced-ELL products: the grid team streams its large
-// matrices past L1 (evict-first in L2); the block team's instance is small and
-// re-read by every product of its solve, so its entries are cached in L1.
-template <bool Stream, typename V>
-__device__ __forceinline__ V ldm(const V* p, unsigned long long pol)
+// Matrix entries of the sliced-ELL products: streamed past L1 (evict-first in
+// L2), except for a block-team instance small enough to stay in L1 across the
+// products of its solve (Sell::l1), whose entries are cached there.
+template <typename V>
+__device__ __forceinline__ V ldm(const V* p, unsigned long long pol, bool l1)
 {
-    if constexpr (Stream)
-        return ld_stream(p, pol);
-    else
-        return ro(p);
+    return l1 ? ro(p) : ld_stream(p, pol);
 }
 
 template <typename T, class Team, class XF, class Epi>
@@ -258,6 +256,7 @@ __device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf,
     const int lane = threadIdx.x & 31;
     const int nw = tm.size() >> 5;
     const unsigned long long pol = evict_first_policy();
+    const bool l1 = !Team::kGrid && S.l1;
     for (int s = tm.rank() >> 5; s < S.nslices; s += nw) {
         const int p0 = ro(S.ptr + s);
         const int tc = (ro(S.ptr + s + 1) - p0) >> 5;
@@ -266,17 +265,17 @@ __device__ __forceinline__ void sell_v(const Team& tm, const Sell<T>& S, XF& xf,
         T a0 = 0, a1 = 0;
         int t = 0;
         for (; t + 4 <= tc; t += 4) {
-            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol), c1 = ldm<Team::kGrid>(cp + 32 * (t + 1), pol),
-                      c2 = ldm<Team::kGrid>(cp + 32 * (t + 2), pol), c3 = ldm<Team::kGrid>(cp + 32 * (t + 3), pol);
-            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol), v1 = ldm<Team::kGrid>(vp + 32 * (t + 1), pol),
-                    v2 = ldm<Team::kGrid>(vp + 32 * (t + 2), pol), v3 = ldm<Team::kGrid>(vp + 32 * (t + 3), pol);
+            const int c0 = ldm(cp + 32 * t, pol, l1), c1 = ldm(cp + 32 * (t + 1), pol, l1),
+                      c2 = ldm(cp + 32 * (t + 2), pol, l1), c3 = ldm(cp + 32 * (t + 3), pol, l1);
+            const T v0 = ldm(vp + 32 * t, pol, l1), v1 = ldm(vp + 32 * (t + 1), pol, l1),
+                    v2 = ldm(vp + 32 * (t + 2), pol, l1), v3 = ldm(vp + 32 * (t + 3), pol, l1);
             const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
             a0 = fmaT(v0, x0, a0);
             a1 = fmaT(v1, x1, a1);
             a0 = fmaT(v2, x2, a0);
             a1 = fmaT(v3, x3, a1);
         }
-        for (; t < tc; ++t) a0 += ldm<Team::kGrid>(vp + 32 * t, pol) * xf(ldm<Team::kGrid>(cp + 32 * t, pol));
+        for (; t < tc; ++t) a0 += ldm(vp + 32 * t, pol, l1) * xf(ldm(cp + 32 * t, pol, l1));
         T acc = a0 + a1;
         for (int o = H; o < 32; o <<= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
         const int pos = s * H + lane;
@@ -291,6 +290,7 @@ __device__ __forceinline__ void sell2_v(const Team& tm, const Sell<T>& S, XF1& x
     const int lane = threadIdx.x & 31;
     const int nw = tm.size() >> 5;
     const unsigned long long pol = evict_first_policy();
+    const bool l1 = !Team::kGrid && S.l1;
     for (int s = tm.rank() >> 5; s < S.nslices; s += nw) {
         const int p0 = ro(S.ptr + s);
         const int tc = (ro(S.ptr + s + 1) - p0) >> 5;
@@ -299,16 +299,16 @@ __device__ __forceinline__ void sell2_v(const Team& tm, const Sell<T>& S, XF1& x
         T a1 = 0, a2 = 0, b1 = 0, b2 = 0;
         int t = 0;
         for (; t + 2 <= tc; t += 2) {
-            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol), c1 = ldm<Team::kGrid>(cp + 32 * (t + 1), pol);
-            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol), v1 = ldm<Team::kGrid>(vp + 32 * (t + 1), pol);
+            const int c0 = ldm(cp + 32 * t, pol, l1), c1 = ldm(cp + 32 * (t + 1), pol, l1);
+            const T v0 = ldm(vp + 32 * t, pol, l1), v1 = ldm(vp + 32 * (t + 1), pol, l1);
             a1 += v0 * xf1(c0);
             a2 += v0 * xf2(c0);
             b1 += v1 * xf1(c1);
             b2 += v1 * xf2(c1);
         }
         if (t < tc) {
-            const int c0 = ldm<Team::kGrid>(cp + 32 * t, pol);
-            const T v0 = ldm<Team::kGrid>(vp + 32 * t, pol);
+            const int c0 = ldm(cp + 32 * t, pol, l1);
+            const T v0 = ldm(vp + 32 * t, pol, l1);
             a1 += v0 * xf1(c0);
             a2 += v0 * xf2(c0);
         }

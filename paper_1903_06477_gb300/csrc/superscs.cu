@@ -543,6 +543,7 @@ static void lay_out(Arena& A, const HostProb& H, int mem, bool qr, bool direct, 
         ds.rows = hs.rows;
         ds.V = hs.V;
         ds.nslices = hs.nslices;
+        ds.l1 = hs.val.size() * (sizeof(int) + sizeof(T)) <= 48 * 1024 ? 1 : 0;
         if (shared_idx == nullptr) {
             ds.ptr = A.take<int>(hs.ptr.size());
             ds.col = A.take<int>(hs.col.size());
