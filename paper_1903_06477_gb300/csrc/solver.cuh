@@ -2678,6 +2678,10 @@ __device__ int superscs(Team& tm, const DevProb<T>& P, const DevWork<T>& W, cons
             W.ws[0][i] = T(0);
             W.ws[1][i] = T(0);
         }
+    // the PSD eigensolves' warm starts live within one solve: a solve neither depends on nor
+    // profits from an earlier one (the flags are read after the next team barrier)
+    if (W.psd_vok)
+        for (int k = tm.rank(); k < P.ns; k += tm.size()) W.psd_vok[k] = 0;
     if (tm.leader() && iter_base == 0) {
         W.st->mat_passes = 0;
         W.st->mat_passes_ir = 0;
