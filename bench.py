@@ -1005,7 +1005,11 @@ def main():
             "fp64_iters": None if fp64_info is None else fp64_info["iters"],
             "speedup_vs_fp64": None if fp64_ms is None else fp64_ms / (total_ms / args.steps),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (4 if prec == B.MIXED else 1),
+            # per mixed solve: the FP32-phase solver kernel, two FP32->FP64 conversions of the CG warm
+            # starts, with mixed_resume the direction memory's (Z, Xi, [Q,] the pending pair), the FP64 phase
+            "gpu_launches": args.steps * ((1 + 2 + (0 if not kw.get("mixed_resume", 1) else
+                                                    4 + (1 if kw.get("direction", 0) == 3 else 0)) + 1)
+                                          if prec == B.MIXED else 1),
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
