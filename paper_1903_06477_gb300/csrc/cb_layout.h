@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 // One column-blocked copy of a matrix in one bulk precision (esize bytes per
@@ -201,7 +202,10 @@ static void cb_place_slice(CbLayout& C, std::vector<std::vector<int>>& rem, size
 
 // Build the column-blocked layout of a CSR matrix (rows x cols) for the row
 // ranges rb, nw compute warps per CTA, blocks of cw columns and a ring of S
-// stages.
+// stages.  The CTAs' segments are independent: a first pass sizes every
+// segment, a prefix sum places them, and a second pass fills them; both
+// passes split the CTAs over host threads, and the result is the same bit
+// for bit whatever the thread count.
 // Returns the largest segment (entries) or -1 if the layout is too large.
 static long long build_cb(int rows, int cols, const std::vector<int>& rp, const std::vector<int>& ci,
                           const std::vector<double>& vx, const std::vector<int>& rb, int nw, int cw, int S,
@@ -219,20 +223,52 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
     C.V = V;
     C.S = S;
     C.rbnd = rb;
-    C.col.clear();
-    C.val.clear();
     struct Seg {
         long long e0, e1;
         std::vector<int> words;  // [4] onwards of the segment's metadata
     };
     std::vector<Seg> segs((size_t)G * ncb);
-    CbBuckets bk;
-    std::vector<int> rows_k, steps, warp, order;
-    std::vector<long long> load;
-    int ms = 4;
-    long long max_e = 0;
-    std::vector<std::vector<int>> rem(32);
-    for (int b = 0; b < G; ++b) {
+    std::vector<long long> seg_len((size_t)G * ncb, 0);
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int T = std::max(1, std::min(G, std::min(8, hw / 4)));
+    auto parallel = [&](auto&& body) {  // body(b) for every CTA b, CTAs dealt round-robin to T threads
+        std::vector<std::thread> th;
+        for (int i = 1; i < T; ++i)
+            th.emplace_back([&, i] {
+                for (int b = i; b < G; b += T) body(b);
+            });
+        for (int b = 0; b < G; b += T) body(b);
+        for (auto& t : th) t.join();
+    };
+    // pass 1: the entries of every segment
+    parallel([&](int b) {
+        thread_local CbBuckets bk;
+        thread_local std::vector<int> rows_k, steps;
+        const int r0 = rb[b], R = rb[b + 1] - r0;
+        bk.build(r0, R, ncb, cw, rp, ci);
+        for (int k = 0; k < ncb; ++k) {
+            bk.sorted_rows(k, R, rows_k);
+            cb_slice_steps(bk, k, R, rows_k, V, steps);
+            long long e = 0;
+            for (int st : steps) e += 32LL * st;
+            seg_len[(size_t)b * ncb + k] = e;
+        }
+    });
+    long long total = 0;
+    for (size_t g = 0; g < segs.size(); ++g) {
+        segs[g].e0 = total;
+        total += seg_len[g];
+        segs[g].e1 = total;
+    }
+    if (total >= (1LL << 31)) return -1;
+    C.col.assign((size_t)total, 0);
+    C.val.assign((size_t)total, 0.0);
+    // pass 2: fill every segment at its place
+    parallel([&](int b) {
+        thread_local CbBuckets bk;
+        thread_local std::vector<int> rows_k, steps, warp, order;
+        thread_local std::vector<long long> load;
+        thread_local std::vector<std::vector<int>> rem(32);
         const int r0 = rb[b], R = rb[b + 1] - r0;
         bk.build(r0, R, ncb, cw, rp, ci);
         for (int k = 0; k < ncb; ++k) {
@@ -244,18 +280,14 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
             std::iota(order.begin(), order.end(), 0);
             std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return warp[a] < warp[c]; });
             Seg& sg = segs[(size_t)b * ncb + k];
-            sg.e0 = (long long)C.col.size();
             std::vector<int> wstart(nw + 1, 0), sstart(ns + 1, 0);
             std::vector<uint16_t> srow((size_t)ns * H, 0xFFFF);
             int w = 0, t = 0;
+            size_t e0 = (size_t)sg.e0;
             for (int oi = 0; oi < ns; ++oi) {
                 const int sl = order[oi];
                 while (w <= warp[sl]) wstart[w++] = oi;
                 sstart[oi] = t;
-                const size_t e0 = (size_t)C.col.size();
-                const size_t size = (size_t)steps[sl] * 32;
-                C.col.resize(e0 + size, 0);
-                C.val.resize(e0 + size, 0.0);
                 for (int rr = 0; rr < H; ++rr) {
                     const size_t pos = (size_t)sl * H + rr;
                     rem[rr].clear();
@@ -267,12 +299,11 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
                     for (int j = 0; j < len; ++j) rem[rr].push_back(bk.epos[q0 + j]);
                 }
                 cb_place_slice(C, rem, e0, steps[sl], k, cw, cols, V, ci, vx);
+                e0 += (size_t)steps[sl] * 32;
                 t += steps[sl];
             }
             sstart[ns] = t;
             while (w <= nw) wstart[w++] = ns;
-            sg.e1 = (long long)C.col.size();
-            max_e = std::max(max_e, sg.e1 - sg.e0);
             sg.words.clear();
             sg.words.push_back(ns);
             sg.words.insert(sg.words.end(), wstart.begin(), wstart.end());
@@ -281,10 +312,14 @@ static long long build_cb(int rows, int cols, const std::vector<int>& rp, const 
                 const unsigned lo = srow[i], hi = i + 1 < ns * H ? srow[i + 1] : 0xFFFFu;
                 sg.words.push_back((int)(lo | (hi << 16)));
             }
-            ms = std::max(ms, 4 + (int)sg.words.size());
         }
+    });
+    int ms = 4;
+    long long max_e = 0;
+    for (const Seg& sg : segs) {
+        ms = std::max(ms, 4 + (int)sg.words.size());
+        max_e = std::max(max_e, sg.e1 - sg.e0);
     }
-    if (C.col.size() >= (1ull << 31)) return -1;
     ms = (ms + 3) & ~3;
     C.ms = ms;
     C.meta.assign((size_t)G * ncb * ms, 0);
